@@ -1,0 +1,240 @@
+"""CPU oracle for the PeriDEM hot path -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's ``cpu_baseline``
+and reference legs may import this package.  The CUDA library never links it,
+and this package imports nothing from the library: the two share no code.
+
+``pd_oracle.c`` holds the peridynamic definitions (FP64, caller node order);
+``mlp.py`` holds the surrogate network's forward/backward/Adam in FP64 numpy.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pd_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+ERR_NONFINITE = 1
+ERR_WALL = 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                               "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64),
+                ("x", ctypes.c_void_p), ("vol", ctypes.c_void_p), ("grain", ctypes.c_void_p),
+                ("rowptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("c", ctypes.c_double), ("s0", ctypes.c_double), ("Kn", ctypes.c_double),
+                ("Rc", ctypes.c_double), ("rho", ctypes.c_double),
+                ("break_mode", ctypes.c_int), ("contact", ctypes.c_int), ("nw", ctypes.c_int),
+                ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+            L.orc_constants.argtypes = [f64, f64, f64, f64, i32, P]
+            L.orc_bond_row.argtypes = [i64, P, P, f64, i32, P, P, i64, P]
+            L.orc_bond_row.restype = i64
+            L.orc_bonds_brute.argtypes = [i64, P, P, f64, i32, P, P, P, P]
+            L.orc_bonds_brute.restype = i64
+            L.orc_bonds_cells.argtypes = [i64, P, P, f64, i32, P, P, P, P]
+            L.orc_bonds_cells.restype = i64
+            L.orc_contact_pairs.argtypes = [P, P, P, i32, P]
+            L.orc_contact_pairs.restype = i64
+            L.orc_forces.argtypes = [P, P, P, P, P, P]
+            L.orc_forces.restype = i32
+            L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P]
+            L.orc_step.restype = i32
+            L.orc_stable_dt.argtypes = [P]
+            L.orc_stable_dt.restype = f64
+            L.orc_damage.argtypes = [i64, P, P, P]
+            L.orc_energy.argtypes = [P, P, P, P]
+            L.orc_energy.restype = f64
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def constants(E, G0, delta, contact_factor=5.0, mode=0):
+    """(K, c, s0, Kn) of the material (see orc_constants)."""
+    out = np.zeros(4)
+    lib().orc_constants(E, G0, delta, contact_factor, mode, _p(out))
+    return tuple(float(v) for v in out)
+
+
+def _filters(kinds, params):
+    kinds = np.ascontiguousarray(kinds, np.int32)
+    params = np.ascontiguousarray(params, np.float64).reshape(-1, 12)
+    return len(kinds), kinds, params
+
+
+def bond_row(x, grain, delta, i, kinds=(), params=()):
+    x = np.ascontiguousarray(x, np.float64)
+    grain = np.ascontiguousarray(grain, np.int32)
+    nf, kinds, params = _filters(kinds, params)
+    out = np.zeros(x.shape[0], np.int32)
+    k = lib().orc_bond_row(x.shape[0], _p(x), _p(grain), delta, nf, _p(kinds), _p(params), i, _p(out))
+    return out[:k].copy()
+
+
+def bonds(x, grain, delta, kinds=(), params=(), brute=None):
+    """Canonical bond CSR (rowptr int64 (n+1), col int32), caller order, ascending."""
+    x = np.ascontiguousarray(x, np.float64)
+    grain = np.ascontiguousarray(grain, np.int32)
+    n = x.shape[0]
+    nf, kinds, params = _filters(kinds, params)
+    if brute is None:
+        brute = n <= 6000
+    fn = lib().orc_bonds_brute if brute else lib().orc_bonds_cells
+    rowptr = np.zeros(n + 1, np.int64)
+    B = fn(n, _p(x), _p(grain), delta, nf, _p(kinds), _p(params), _p(rowptr), None)
+    col = np.zeros(max(B, 1), np.int32)
+    fn(n, _p(x), _p(grain), delta, nf, _p(kinds), _p(params), _p(rowptr), _p(col))
+    return rowptr, col[:B].copy()
+
+
+class Model:
+    """A problem (geometry, bonds, constants, walls) plus its state, all FP64,
+    caller order.  Mirrors the library's state: u, v, a, broken (uint8 per
+    directed slot), wall positions and time."""
+
+    def __init__(self, x, vol, grain, rowptr, col, material, horizon, walls=None,
+                 body_force=(0.0, 0.0, 0.0), v0=None, contact=True):
+        self.x = np.ascontiguousarray(x, np.float64)
+        self.vol = np.ascontiguousarray(vol, np.float64)
+        self.grain = np.ascontiguousarray(grain, np.int32)
+        self.rowptr = np.ascontiguousarray(rowptr, np.int64)
+        self.col = np.ascontiguousarray(col, np.int32)
+        n = self.x.shape[0]
+        m = material
+        self.K, self.c, self.s0, self.Kn = constants(m.E, m.G0, horizon, m.contact_factor, m.constants)
+        self.walls = np.ascontiguousarray(walls if walls is not None else np.zeros((0, 9)), np.float64).reshape(-1, 9)
+        self.wall_pos = self.walls[:, 3:6].copy()
+        self.P = Problem()
+        self.P.n = n
+        self.P.x, self.P.vol, self.P.grain = _p(self.x), _p(self.vol), _p(self.grain)
+        self.P.rowptr, self.P.col = _p(self.rowptr), _p(self.col)
+        self.P.c, self.P.s0, self.P.Kn, self.P.Rc, self.P.rho = self.c, self.s0, self.Kn, m.contact_radius, m.rho
+        self.P.break_mode = m.break_mode
+        self.P.contact = 1 if contact else 0
+        self.P.nw = self.walls.shape[0]
+        self.P.walls = _p(self.walls)
+        self.P.b = (ctypes.c_double * 3)(*body_force)
+        self.body_force = np.array(body_force, np.float64)
+        self.rho = m.rho
+        self.u = np.zeros((n, 3))
+        self.v = np.zeros((n, 3)) if v0 is None else np.ascontiguousarray(v0, np.float64).copy()
+        self.broken = np.zeros(max(len(self.col), 1), np.uint8)
+        self.F = np.zeros((n, 3))
+        self.react = np.zeros((self.walls.shape[0], 3))
+        self.t = 0.0
+        self.err = 0
+        self.acc = np.zeros((n, 3))
+
+    @classmethod
+    def from_scenario(cls, sc, rowptr=None, col=None, contact=True):
+        from_sc = sc
+        if rowptr is None:
+            kinds = [k for k, _ in from_sc.filters]
+            params = [list(a) + [0.0] * (12 - len(a)) for _, a in from_sc.filters]
+            rowptr, col = bonds(sc.x, sc.grain, sc.horizon, kinds, params)
+        walls = np.array([list(w.normal) + list(w.point) + list(w.velocity) for w in sc.walls],
+                         np.float64).reshape(-1, 9)
+        return cls(sc.x, sc.vol, sc.grain, rowptr, col, sc.material, sc.horizon, walls,
+                   sc.body_force, sc.v0, contact)
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    def forces(self):
+        """F at the current state (applies breaking), sets react; returns F."""
+        self.err |= lib().orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.wall_pos),
+                                     _p(self.broken), _p(self.F), _p(self.react))
+        return self.F
+
+    def init(self):
+        """a(t) from the current state, as the first half-kick needs it."""
+        self.forces()
+        self.acc = (self.F + self.body_force) / self.rho
+        return self
+
+    def step(self, dt, nsteps=1):
+        self.err |= lib().orc_step(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.acc),
+                                   _p(self.broken), _p(self.wall_pos), dt, nsteps, _p(self.F),
+                                   _p(self.react))
+        self.t += dt * nsteps
+        return self
+
+    def stable_dt(self):
+        return float(lib().orc_stable_dt(ctypes.byref(self.P)))
+
+    def damage(self):
+        phi = np.zeros(self.n)
+        lib().orc_damage(self.n, _p(self.rowptr), _p(self.broken), _p(phi))
+        return phi
+
+    def energy(self):
+        return float(lib().orc_energy(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.broken)))
+
+    def contact_pairs(self, brute=False):
+        """(m,2) int32 ordered contact pairs at the current state, sorted."""
+        cnt = lib().orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), None)
+        pr = np.zeros((max(cnt, 1), 2), np.int32)
+        lib().orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), _p(pr))
+        return pr[:cnt].copy()
+
+    def bulk_stress(self, areas):
+        return bulk_stress(self.walls[:, 0:3], self.react, areas)
+
+
+def bulk_stress(normals, react, areas):
+    """Bulk stress (Voigt xx, yy, zz, yz, xz, xy) from wall reactions.
+
+    Reading of "bulk strength = difference of top and bottom reactions, normalised
+    by the top area" (Sec. 6.4): the wall pushes on the aggregate with -R_l over
+    area A_l, whose outward normal (of the aggregate) is m_l = -n_l; Cauchy's
+    relation sigma m = t gives, per wall, the column sigma e_k = -(R_l / A_l)(m_l . e_k)
+    for the axis k that m_l points along.  Columns are averaged over the walls
+    that face each axis and the result is symmetrised.
+    """
+    normals = np.asarray(normals, np.float64).reshape(-1, 3)
+    react = np.asarray(react, np.float64).reshape(-1, 3)
+    areas = np.asarray(areas, np.float64).reshape(-1)
+    S = np.zeros((3, 3))
+    cnt = np.zeros(3)
+    for l in range(normals.shape[0]):
+        m = -normals[l]
+        k = int(np.argmax(np.abs(m)))
+        S[:, k] += -(react[l] / areas[l]) * np.sign(m[k])
+        cnt[k] += 1
+    for k in range(3):
+        if cnt[k] > 0:
+            S[:, k] /= cnt[k]
+    S = 0.5 * (S + S.T)
+    return np.array([S[0, 0], S[1, 1], S[2, 2], S[1, 2], S[0, 2], S[0, 1]])
