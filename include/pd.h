@@ -1,0 +1,253 @@
+/*
+ * pd.h - C ABI of the GB300 PeriDEM hot-path library (libpd.so).
+ *
+ * One explicit velocity-Verlet step of bond-based peridynamics (PMB bonds with
+ * critical-stretch breaking) inside every grain, short-range nodal contact
+ * between grains and fragments, and rigid planar walls, after the paper's
+ * Sec. 2-5 (equation of motion, Eq. motion; bond force, Eq. pmb and
+ * Eq. peri-damage; contact, Eq. repulsive-force and the self-contact law; wall
+ * contact, Sec. 4.1; time integration, Sec. 5.2).  Plus the bulk-stress MLP
+ * surrogate (pd_mlp_*), which the paper motivates (RVE use, Sec. 1 and 6.4) but
+ * does not specify.
+ *
+ * Conventions for every call:
+ *  - Units are SI.  Node arrays are row-major n x 3 float64 (x0 y0 z0 x1 ...).
+ *  - Node indices are the caller's order everywhere; the library's internal
+ *    (grain-major, Morton) order never leaks through the ABI.
+ *  - Input arrays are host pointers, read during the call and not retained:
+ *    the caller keeps ownership.  Outputs go to caller-allocated host buffers.
+ *  - Every call returns a pd_status; pd_last_error() gives the message.
+ *  - Device memory is obtained through pd_options.alloc/free when given
+ *    (e.g. a framework's caching allocator), else cudaMalloc/cudaFree.  The
+ *    context owns it until pd_destroy.
+ *  - Work runs on pd_options.stream (a cudaStream_t; NULL = the legacy default
+ *    stream).  Calls that return data synchronise that stream.
+ *  - A context is not thread-safe.  Errors raised on the device (non-finite
+ *    state, wall penetration) are latched; the context then refuses pd_step
+ *    until pd_set_state is called.
+ */
+#ifndef PD_H
+#define PD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pd_ctx pd_ctx;
+typedef struct pd_mlp pd_mlp;
+
+typedef enum {
+    PD_OK = 0,
+    PD_EINVAL = -1,      /* bad argument: null pointer, size, value out of range */
+    PD_ENOMEM = -2,      /* the allocator returned NULL */
+    PD_ECUDA = -3,       /* a CUDA runtime call failed (message has the CUDA error) */
+    PD_ESTATE = -4,      /* call out of order (e.g. pd_step before pd_build_bonds) */
+    PD_ECAPACITY = -5,   /* a fixed capacity was exceeded and could not be regrown */
+    PD_ENONFINITE = -6,  /* a force, displacement or velocity became NaN/inf */
+    PD_ETIMEOUT = -7,    /* a bounded device wait gave up */
+    PD_EWALL = -8        /* a node went a whole contact radius behind a wall */
+} pd_status;
+
+/* Arithmetic of the bond loop. */
+enum { PD_MIXED = 0,  /* FP32 bond arithmetic; xi and eta from double-float pairs
+                         (48-bit significands), FP64 state and accumulation */
+       PD_FP64 = 1 }; /* every operation in FP64 */
+
+/* Material (one per context).  Bond-based PD fixes nu = 1/4 in 3-D (Sec. 3.1.1),
+ * so K = 2E/3.  constants = 0: c = 18K/(pi delta^4), s0 = sqrt(5 G0/(9 K delta));
+ * constants = 1: the paper's table row (c = 12E/(pi delta^4 (1-nu)),
+ * s0 = sqrt(5 pi G0/(12 E delta))).  K_n = contact_factor * 18K/(pi delta^5)
+ * (Sec. 3.2).  break_mode = 0 breaks a bond when s > s0 (definition of the bond
+ * memory gamma); 1 when |s| > s0 (the sentence before the table). */
+typedef struct {
+    double E;               /* Young's modulus, Pa (> 0) */
+    double rho;             /* density, kg/m^3 (> 0) */
+    double G0;              /* critical energy release rate, J/m^2 (> 0; inf = unbreakable) */
+    double contact_radius;  /* R_c, m (> 0) */
+    double contact_factor;  /* f_c in K_n (>= 0; 0 disables contact stiffness) */
+    int constants;          /* 0 or 1, see above */
+    int break_mode;         /* 0 or 1, see above */
+} pd_material;
+
+typedef struct {
+    int device;                          /* CUDA device ordinal */
+    void *stream;                        /* cudaStream_t, NULL = legacy default stream */
+    void *(*alloc)(size_t bytes, void *alloc_ctx);  /* NULL: cudaMalloc */
+    void (*free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+    int precision;                       /* PD_MIXED or PD_FP64 */
+    int contact;                         /* 1: nodal contact on, 0: off */
+    int contact_every;                   /* steps between contact-list rebuilds; 0 = automatic */
+    double skin;                         /* Verlet skin of the contact list, m; 0 = 0.5 R_c */
+    int lanes_per_node;                  /* lanes sharing one node's bonds: 4, 8, 16, 32; 0 = autotune */
+    int graph_chunk;                     /* steps per captured CUDA graph; 0 = 64 */
+} pd_options;
+
+/* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */
+typedef struct {
+    double normal[3];
+    double point[3];     /* a point of the plane at the current time */
+    double velocity[3];  /* rigid translation velocity, m/s */
+} pd_wall;
+
+/* Bond-removal filter (Sec. 5.3), applied once in pd_build_bonds.
+ * kind 1, notch (Sec. 5.3.1): a[0..3] = plane (a, b, c, d); the bond x1 -> x2 is
+ *   removed if the plane parameter t = -(a x1 + b y1 + c z1 + d)/(a dx + b dy + c dz)
+ *   satisfies 0 < t < 1 and the crossing point lies in the box a[4..6]..a[7..9]
+ *   (the notch face; the paper's plane is unbounded).  x1 is the endpoint with
+ *   the smaller caller index, so both directions decide alike.
+ * kind 2, inner sphere (Sec. 5.3.2): a[0..2] centre, a[3] radius; the bond is
+ *   removed if either end lies strictly inside. */
+typedef struct {
+    int kind;
+    double a[12];
+} pd_bond_filter;
+
+/* Fills *opt with defaults: device 0, default stream, cudaMalloc, PD_MIXED,
+ * contact on, automatic rebuild period and skin, autotuned lanes, chunk 64. */
+void pd_default_options(pd_options *opt);
+
+/* Creates a context for n nodes (Sec. 2.1: nodes x with volumes, grouped in
+ * grains P_i).  x: n*3 reference positions; vol: n volumes (> 0); grain: n grain
+ * ids (>= 0); v0: n*3 initial velocities or NULL for rest.  u starts at 0, t at 0.
+ * Sorts the nodes grain-major and in Morton order inside each grain (internal).
+ * Errors: PD_EINVAL (n < 1, n > 2^31-1, null arrays, bad material/options),
+ * PD_ENOMEM, PD_ECUDA.  On error *out is NULL. */
+pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t *grain,
+                    const double *v0, const pd_material *mat, const pd_options *opt,
+                    pd_ctx **out);
+
+/* Builds the bond family (Sec. 3.1): ordered pairs (i, j), i != j, of the same
+ * grain with |x_j - x_i| < horizon (strict; Eq. pmb), squared distance
+ * evaluated in FP64 as ((dx*dx + dy*dy) + dz*dz) without FMA, minus the
+ * filters.  Sets the micromodulus and critical stretch for this horizon, marks
+ * every bond intact, and evaluates the forces at the current state (which may
+ * already break bonds).  May be called again to rebuild from scratch.
+ * Errors: PD_EINVAL (horizon <= 0, nfilt < 0, bad filter kind),
+ * PD_ECAPACITY (more than 2^31-1 bonds), PD_ENOMEM, PD_ECUDA. */
+pd_status pd_build_bonds(pd_ctx *ctx, double horizon, int nfilt, const pd_bond_filter *filt);
+
+/* Replaces the wall set (0 <= nw <= 6).  Wall forces sum the single-wall cap
+ * terms (Sec. 4.1); the inclusion-exclusion of Sec. 4.1.1 is not applied. */
+pd_status pd_set_walls(pd_ctx *ctx, int nw, const pd_wall *walls);
+
+/* Current wall points (nw*3), after the walls moved with their velocity. */
+pd_status pd_get_walls(pd_ctx *ctx, double *points);
+
+/* Body force density b (N/m^3), added to every node (Eq. intra_particle). */
+pd_status pd_set_body_force(pd_ctx *ctx, const double b[3]);
+
+/* Critical time step of the explicit scheme on the current bonds (the paper
+ * states dt came from a stability analysis, Sec. 5.2; the bound used is
+ * Silling-Askari's dt = min_i sqrt(2 rho / sum_j V_j c / |xi_ij|)).
+ * Errors: PD_ESTATE before pd_build_bonds. */
+pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
+
+/* Advances nsteps velocity-Verlet steps of size dt (Sec. 5.2):
+ *   v += dt/2 a; u += dt v; walls move; a = (F(u) + b)/rho; v += dt/2 a,
+ * where F is the bond force with breaking (Eq. peri-damage), contact and wall
+ * force.  Captured and replayed as CUDA graphs.  Blocks until done.
+ * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL
+ * (dt <= 0, nsteps < 0), PD_ENONFINITE / PD_EWALL (state restored to the start
+ * of the call and latched), PD_ECAPACITY, PD_ECUDA. */
+pd_status pd_step(pd_ctx *ctx, double dt, int64_t nsteps);
+
+/* Damage phi_i = 1 - intact_i / initial_i, 0 for nodes without bonds (Sec. 3.1.1;
+ * the paper's wording describes the complement).  phi: n doubles, caller order. */
+pd_status pd_damage(pd_ctx *ctx, double *phi);
+
+/* Wall reactions and bulk stress from the last force evaluation.
+ * wall_force (nullable): nw*3, force exerted by the nodes on each wall.
+ * area (nullable when nw == 0): nw face areas used to turn reactions into
+ * tractions.  sigma: Voigt (xx, yy, zz, yz, xz, xy); per wall the column
+ * sigma e_k = -(R_l / A_l)(m_l . e_k) with m_l = -normal the aggregate's outward
+ * normal, averaged over walls facing the same axis and symmetrised; compression
+ * is negative (reading of "bulk strength" in Sec. 6.4/6.5). */
+pd_status pd_bulk_stress(pd_ctx *ctx, const double *area, double sigma[6], double *wall_force);
+
+/* Number of directed bonds B (each undirected bond counted twice). */
+pd_status pd_num_bonds(pd_ctx *ctx, int64_t *B);
+
+/* Canonical bond list: rowptr (n+1) and col (B), rows in caller order, columns
+ * ascending caller indices. */
+pd_status pd_bonds(pd_ctx *ctx, int64_t *rowptr, int32_t *col);
+
+/* Contact pairs at the current state (Sec. 3.2 and self-contact): ordered
+ * pairs (i, j), i != j, with |p_j - p_i| < R_c (FP64, no FMA), excluding same-
+ * grain pairs whose bond is intact; sorted by (i, j), caller indices.
+ * ij == NULL: *npairs receives the count.  Otherwise *npairs is the capacity in
+ * pairs on entry and the count on return (PD_ECAPACITY if too small). */
+pd_status pd_contacts(pd_ctx *ctx, int64_t *npairs, int32_t *ij);
+
+/* Force density F (n*3, caller order) at the current state without stepping:
+ * applies breaking exactly as a step does. */
+pd_status pd_forces(pd_ctx *ctx, double *F);
+
+/* State for checkpoints and parity: u, v (n*3), broken (B bytes, 1 = broken, in
+ * pd_bonds order), t.  Any output may be NULL. */
+pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, double *t);
+
+/* Sets the state (any input may be NULL to keep it), clears a latched device
+ * error and re-evaluates the forces (which may break bonds). */
+pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
+                       const double *t);
+
+/* Autotuning record of the bond loop: lanes per node chosen and the measured
+ * time per step (ms) of each candidate (4, 8, 16, 32 lanes; 0 = not run). */
+pd_status pd_tuning(pd_ctx *ctx, int *lanes, double ms[4]);
+
+/* Profiling switch.  When on, pd_step launches its kernels one by one (no CUDA
+ * graph) with CUDA events around every fused force/update launch, so that
+ * pd_last_step_stats can report that kernel's own device time.  Off by default. */
+pd_status pd_set_profiling(pd_ctx *ctx, int on);
+
+/* Timing of the last pd_step: ms_force = summed device milliseconds of the
+ * fused force/update launches (only when profiling is on, else 0); ms_total =
+ * device milliseconds of the whole call (event-timed on the context's stream);
+ * launches = kernels launched. */
+pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, int64_t *launches);
+
+const char *pd_last_error(const pd_ctx *ctx);
+void pd_destroy(pd_ctx *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Bulk-stress surrogate: an MLP dims[0] -> ... -> dims[nlayers] with exact GELU
+ * between layers, BF16 weights and activations, FP32 accumulation, FP32 master
+ * weights, MSE loss and Adam (beta 0.9/0.999, eps 1e-8).  Not in the paper.
+ * Parameter vector layout: for each layer, W (out x in, row-major) then b (out).
+ * ------------------------------------------------------------------------- */
+
+/* dims: nlayers+1 widths, each a multiple of 1 and <= 1024; seed draws the
+ * initial weights (uniform +-1/sqrt(fan_in), SplitMix64); device/stream as in
+ * pd_options (stream NULL = default). */
+pd_status pd_mlp_create(const int *dims, int nlayers, uint64_t seed, int device, void *stream,
+                        pd_mlp **out);
+/* Y (batch x dims[nlayers], FP32) = MLP(X); X (batch x dims[0], FP32) is
+ * rounded to BF16 (nearest-even). Host pointers. */
+pd_status pd_mlp_forward(pd_mlp *m, const float *X, int64_t batch, float *Y);
+/* Same with device pointers (no copies). */
+pd_status pd_mlp_forward_device(pd_mlp *m, const float *X, int64_t batch, float *Y);
+/* One Adam step on the MSE loss of (X, T); *loss receives the loss before the
+ * update (nullable).  Host pointers. */
+pd_status pd_mlp_train_step(pd_mlp *m, const float *X, const float *T, int64_t batch, float lr,
+                            float *loss);
+/* Same with device pointers; loss is a device float (nullable). */
+pd_status pd_mlp_train_step_device(pd_mlp *m, const float *X, const float *T, int64_t batch,
+                                   float lr, float *loss);
+/* Gradient of the MSE loss (FP32, parameter layout) without updating. */
+pd_status pd_mlp_grad(pd_mlp *m, const float *X, const float *T, int64_t batch, float *grad,
+                      float *loss);
+pd_status pd_mlp_num_params(pd_mlp *m, int64_t *count);
+pd_status pd_mlp_get_params(pd_mlp *m, float *w);
+/* Sets the FP32 master weights and resets Adam's moments and step count. */
+pd_status pd_mlp_set_params(pd_mlp *m, const float *w);
+const char *pd_mlp_last_error(const pd_mlp *m);
+void pd_mlp_destroy(pd_mlp *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PD_H */

@@ -44,7 +44,7 @@ class Problem(ctypes.Structure):
                 ("c", ctypes.c_double), ("s0", ctypes.c_double), ("Kn", ctypes.c_double),
                 ("Rc", ctypes.c_double), ("rho", ctypes.c_double),
                 ("break_mode", ctypes.c_int), ("contact", ctypes.c_int), ("nw", ctypes.c_int),
-                ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3)]
+                ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3), ("frozen", ctypes.c_int)]
 
 
 def lib():
@@ -172,10 +172,13 @@ class Model:
     def n(self):
         return self.x.shape[0]
 
-    def forces(self):
-        """F at the current state (applies breaking), sets react; returns F."""
+    def forces(self, frozen=False):
+        """F at the current state, sets react; returns F.  Applies breaking unless
+        frozen, which evaluates with the current bond memory unchanged."""
+        self.P.frozen = 1 if frozen else 0
         self.err |= lib().orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.wall_pos),
                                      _p(self.broken), _p(self.F), _p(self.react))
+        self.P.frozen = 0
         return self.F
 
     def init(self):

@@ -312,6 +312,7 @@ typedef struct {
     int nw;
     const double *walls;    /* nw*9: inward normal, point at t=0, velocity */
     double b[3];            /* body force density, N/m^3 */
+    int frozen;             /* 1: evaluate with the given bond memory, no new breaking */
 } orc_problem;
 
 /* slot of j in row i (binary search on the ascending row), or -1 */
@@ -410,6 +411,8 @@ int64_t orc_contact_pairs(const orc_problem *P, const double *u, const uint8_t *
  *    the cap and makes the force attractive near d = R_c; the printed
  *    centroid formula is only consistent with (2 R_c + d).  d <= -R_c (a node
  *    a whole radius behind the wall) is undefined and flagged ORC_ERR_WALL.
+ * With P->frozen set, step 1 keeps the given bond memory (Eq. peri-damage with
+ * gamma prescribed) so that two evaluations can be compared on one bond set.
  * Returns error bits.  react (nw*3) receives the total force on each wall.
  */
 int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, uint8_t *broken,
@@ -440,7 +443,7 @@ int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, ui
             double l = sqrt(sq3(y[0], y[1], y[2]));
             double s = (l - L) / L;
             int brk = P->break_mode ? (fabs(s) > P->s0) : (s > P->s0);
-            if (brk) { broken[k] = 1; continue; }
+            if (brk && !P->frozen) { broken[k] = 1; continue; }
             double g = P->c * s * P->vol[j] / l;
             for (int a = 0; a < 3; ++a) f[a] += g * y[a];
         }

@@ -1,0 +1,1060 @@
+// C ABI of libpd: context management, set-up, CUDA-graph stepping, queries.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "pd_build.cuh"
+#include "pd_grid.cuh"
+#include "pd_internal.cuh"
+
+struct GraphEntry {
+    int steps, k, parity;
+    double dt;
+    cudaGraphExec_t exec;
+    int64_t launches;
+};
+
+struct pd_ctx {
+    pd_options opt;
+    pd_material mat;
+    cudaStream_t st = nullptr;
+    std::string err;
+    std::vector<void *> owned;
+
+    int64_t n = 0;
+    double lo[3], hi[3];
+    double K = 0, c = 0, s0 = 0, Kn = 0, delta = 0;
+    bool bonds_ready = false;
+    int64_t B = 0;
+    int sh = 1;  // bits per node index
+
+    int32_t *perm = nullptr, *inv = nullptr, *grain = nullptr;
+    dbl4 *x4 = nullptr, *u[2] = {nullptr, nullptr}, *v = nullptr, *acc = nullptr, *F = nullptr;
+    float4 *xh4 = nullptr, *xl4 = nullptr, *uh[2] = {nullptr, nullptr}, *ul[2] = {nullptr, nullptr};
+    int cur = 0;
+
+    int64_t *rowptr = nullptr, *crow = nullptr;
+    int32_t *col = nullptr, *kc_of = nullptr;
+    uint32_t *brk = nullptr;
+    int64_t nwords = 0;
+
+    // contact candidates and grid
+    int64_t *cand_ptr = nullptr, *cand_cnt = nullptr;
+    int2 *cand = nullptr;
+    int64_t cand_cap = 0;
+    uint32_t *gk = nullptr, *gk2 = nullptr, *gv = nullptr, *gv2 = nullptr, *gstart = nullptr, *gend = nullptr;
+    uint64_t *gcell = nullptr;
+    uint32_t nbuckets = 0;
+    int64_t *tmp = nullptr;  // scan / radix scratch for n-sized problems
+
+    // reductions and device scalars
+    double *partials = nullptr, *react = nullptr, *disp = nullptr, *wall_pos = nullptr, *dscratch = nullptr;
+    unsigned *counter = nullptr, *derr = nullptr;
+    int *stale = nullptr;
+    int blocks = 0, lanes = 0, blocks_cap = 0;
+    double tune_ms[4] = {0, 0, 0, 0};
+
+    WallSet walls;
+    double b[3] = {0, 0, 0};
+    double t = 0;
+    unsigned latched = 0;
+
+    // staging and snapshot
+    double *stage = nullptr;   // n*3 doubles
+    uint8_t *stage_b = nullptr;  // B bytes
+    dbl4 *snap_u = nullptr, *snap_v = nullptr, *snap_acc = nullptr;
+    uint32_t *snap_brk = nullptr;
+
+    std::vector<GraphEntry> graphs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = 0, last_force_ms = 0;
+    int64_t last_launches = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_ev;  // pairs around force launches
+    int prof_used = 0;
+};
+
+void *pd_dev_alloc(pd_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (c->opt.alloc) {
+        p = c->opt.alloc(bytes, c->opt.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->owned.push_back(p);
+    return p;
+}
+
+void pd_dev_free(pd_ctx *c, void *p)
+{
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it != c->owned.end()) c->owned.erase(it);
+    if (c->opt.free)
+        c->opt.free(p, c->opt.alloc_ctx);
+    else if (!c->opt.alloc)
+        cudaFree(p);
+}
+
+namespace {
+
+pd_status fail(pd_ctx *c, pd_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            cudaGetLastError();                                                                   \
+            return fail(c, PD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+        }                                                                                         \
+    } while (0)
+
+#define ALLOC(ptr, type, count)                                                                   \
+    do {                                                                                          \
+        (ptr) = (type *)pd_dev_alloc(c, sizeof(type) * (size_t)(count));                          \
+        if (!(ptr)) return fail(c, PD_ENOMEM, "device allocation failed: " #ptr);                 \
+    } while (0)
+
+template <typename T>
+void release(pd_ctx *c, T *&p)
+{
+    pd_dev_free(c, (void *)p);
+    p = nullptr;
+}
+
+void clear_graphs(pd_ctx *c)
+{
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
+int bits_for(int64_t v)
+{
+    int b = 1;
+    while (b < 62 && ((int64_t)1 << b) <= v) ++b;
+    return b;
+}
+
+pd_status sync(pd_ctx *c)
+{
+    CK(cudaStreamSynchronize(c->st));
+    return PD_OK;
+}
+
+void constants(pd_ctx *c)
+{
+    const double nu = 0.25, E = c->mat.E, G0 = c->mat.G0, d = c->delta;
+    c->K = E / (3.0 * (1.0 - 2.0 * nu));
+    if (c->mat.constants == 1) {
+        c->c = 12.0 * E / (M_PI * pow(d, 4) * (1.0 - nu));
+        c->s0 = sqrt(5.0 * M_PI * G0 / (12.0 * E * d));
+    } else {
+        c->c = 18.0 * c->K / (M_PI * pow(d, 4));
+        c->s0 = sqrt(5.0 * G0 / (9.0 * c->K * d));
+    }
+    c->Kn = c->mat.contact_factor * 18.0 * c->K / (M_PI * pow(d, 5));
+}
+
+double skin_of(const pd_ctx *c) { return c->opt.skin > 0 ? c->opt.skin : 0.5 * c->mat.contact_radius; }
+
+StepParams params(pd_ctx *c, int mode, int in, double dt)
+{
+    StepParams p;
+    memset(&p, 0, sizeof(p));
+    const bool mixed = c->opt.precision == PD_MIXED;
+    p.n = c->n;
+    p.rowptr = c->rowptr;
+    p.col = c->col;
+    p.brk = c->brk;
+    p.xh4 = mixed ? c->xh4 : nullptr;
+    p.xl4 = mixed ? c->xl4 : nullptr;
+    p.uh_in = mixed ? c->uh[in] : nullptr;
+    p.ul_in = mixed ? c->ul[in] : nullptr;
+    p.uh_out = mixed ? c->uh[in ^ 1] : nullptr;
+    p.ul_out = mixed ? c->ul[in ^ 1] : nullptr;
+    p.x4 = c->x4;
+    p.u_in = c->u[in];
+    p.u_out = c->u[in ^ 1];
+    p.v = c->v;
+    p.acc = c->acc;
+    p.F_out = mode == MODE_FORCES ? c->F : nullptr;
+    p.grain = c->grain;
+    p.contact = c->opt.contact;
+    p.cand_ptr = c->cand_ptr;
+    p.cand = c->cand;
+    p.c = c->c;
+    p.s0 = c->s0;
+    p.Kn = c->Kn;
+    p.Rc = c->mat.contact_radius;
+    p.rho = c->mat.rho;
+    p.dt = dt;
+    p.cf = (float)c->c;
+    p.s0f = (float)c->s0;
+    p.break_mode = c->mat.break_mode;
+    p.mode = mode;
+    p.walls = c->walls;
+    p.wall_pos = c->wall_pos;
+    for (int a = 0; a < 3; ++a) p.b[a] = c->b[a];
+    p.partials = c->partials;
+    p.counter = c->counter;
+    p.err = c->derr;
+    p.react = c->react;
+    p.disp = c->disp;
+    p.skin = skin_of(c);
+    p.stale = c->stale;
+    return p;
+}
+
+// Contact candidate rebuild from u[in] (stream-ordered; capturable).
+void enqueue_rebuild(pd_ctx *c, int in)
+{
+    GridView g;
+    for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];
+    const double cut = c->mat.contact_radius + skin_of(c);
+    grid_build(g, c->x4, c->u[in], c->n, cut * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
+               c->gend, c->gcell, c->tmp, c->st);
+    cand_count(c->x4, c->u[in], c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_cnt, c->st);
+    scan_exclusive_i64(c->cand_cnt, c->cand_ptr, c->n, c->tmp, c->st);
+    cand_fill(c->x4, c->u[in], c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_ptr, c->cand, c->cand_cap,
+              c->derr, c->disp, c->stale, c->st);
+}
+
+pd_status grow_candidates(pd_ctx *c)
+{
+    int64_t need = 0;
+    CK(cudaMemcpy(&need, c->cand_ptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    int64_t cap = std::max<int64_t>(2 * c->cand_cap, need + need / 2 + 1024);
+    release(c, c->cand);
+    ALLOC(c->cand, int2, cap);
+    c->cand_cap = cap;
+    clear_graphs(c);
+    return PD_OK;
+}
+
+pd_status read_err(pd_ctx *c, unsigned *e)
+{
+    CK(cudaMemcpyAsync(e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    return PD_OK;
+}
+
+pd_status status_of(pd_ctx *c, unsigned e)
+{
+    if (e & PDE_NONFINITE) return fail(c, PD_ENONFINITE, "non-finite force or state on the device");
+    if (e & PDE_WALL) return fail(c, PD_EWALL, "a node is a whole contact radius behind a wall");
+    if (e & PDE_CAPACITY) return fail(c, PD_ECAPACITY, "contact candidate capacity exceeded");
+    if (e & PDE_SKIN) return fail(c, PD_ETIMEOUT, "contact list went stale between rebuilds");
+    return PD_OK;
+}
+
+// Force evaluation at the current state (breaking applies).  Retries once after
+// growing the candidate list.
+pd_status eval_forces(pd_ctx *c)
+{
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if (c->opt.contact) enqueue_rebuild(c, c->cur);
+        StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
+        launch_step(p, c->lanes, c->blocks, c->st);
+        CK(cudaGetLastError());
+        unsigned e = 0;
+        pd_status s = read_err(c, &e);
+        if (s) return s;
+        if (e & PDE_CAPACITY) {
+            s = grow_candidates(c);
+            if (s) return s;
+            continue;
+        }
+        e &= ~(unsigned)PDE_SKIN;
+        c->latched |= e & (PDE_NONFINITE | PDE_WALL);
+        return status_of(c, e);
+    }
+    return fail(c, PD_ECAPACITY, "contact candidate list could not be grown");
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+void pd_default_options(pd_options *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->device = 0;
+    o->stream = nullptr;
+    o->precision = PD_MIXED;
+    o->contact = 1;
+    o->contact_every = 0;
+    o->skin = 0.0;
+    o->lanes_per_node = 0;
+    o->graph_chunk = 64;
+}
+
+const char *pd_last_error(const pd_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void pd_destroy(pd_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->opt.device);
+    cudaStreamSynchronize(c->st);
+    clear_graphs(c);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    std::vector<void *> own = c->owned;
+    for (void *p : own) pd_dev_free(c, p);
+    delete c;
+}
+
+static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, const int32_t *grain, const double *v0)
+{
+    const int64_t n = c->n;
+    CK(cudaSetDevice(c->opt.device));
+    c->st = (cudaStream_t)c->opt.stream;
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+    int32_t gmax = 0;
+    for (int a = 0; a < 3; ++a) { c->lo[a] = INFINITY; c->hi[a] = -INFINITY; }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            double q = x[3 * i + a];
+            if (!isfinite(q)) return fail(c, PD_EINVAL, "x contains a non-finite value");
+            c->lo[a] = std::min(c->lo[a], q);
+            c->hi[a] = std::max(c->hi[a], q);
+        }
+        if (!(vol[i] > 0) || !isfinite(vol[i])) return fail(c, PD_EINVAL, "vol must be positive and finite");
+        if (grain[i] < 0) return fail(c, PD_EINVAL, "grain ids must be >= 0");
+        gmax = std::max(gmax, grain[i]);
+        if (v0)
+            for (int a = 0; a < 3; ++a)
+                if (!isfinite(v0[3 * i + a])) return fail(c, PD_EINVAL, "v0 contains a non-finite value");
+    }
+    c->sh = bits_for(n);
+    // staging of the caller arrays
+    double *dx, *dvol, *dv0 = nullptr;
+    int32_t *dgrain;
+    ALLOC(dx, double, 3 * n);
+    ALLOC(dvol, double, n);
+    ALLOC(dgrain, int32_t, n);
+    CK(cudaMemcpyAsync(dx, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dvol, vol, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(dgrain, grain, sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->st));
+    if (v0) {
+        ALLOC(dv0, double, 3 * n);
+        CK(cudaMemcpyAsync(dv0, v0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->st));
+    }
+    // scratch big enough for radix sorts and scans of n items
+    int64_t tmpn = std::max(radix_tmp_size(n), scan_tmp_size(n + 1) + 8);
+    ALLOC(c->tmp, int64_t, tmpn);
+    uint64_t *k1, *k2;
+    uint32_t *v1, *v2, *order;
+    ALLOC(k1, uint64_t, n);
+    ALLOC(k2, uint64_t, n);
+    ALLOC(v1, uint32_t, n);
+    ALLOC(v2, uint32_t, n);
+    build_morton(dx, n, c->lo, c->hi, k1, k2, v1, v2, gmax > 0 ? bits_for(gmax) : 0, dgrain, c->tmp, &order, c->st);
+    const bool mixed = c->opt.precision == PD_MIXED;
+    ALLOC(c->perm, int32_t, n);
+    ALLOC(c->inv, int32_t, n);
+    ALLOC(c->grain, int32_t, n);
+    ALLOC(c->x4, dbl4, n);
+    ALLOC(c->v, dbl4, n);
+    ALLOC(c->acc, dbl4, n);
+    ALLOC(c->F, dbl4, n);
+    for (int q = 0; q < 2; ++q) ALLOC(c->u[q], dbl4, n);
+    if (mixed) {
+        ALLOC(c->xh4, float4, n);
+        ALLOC(c->xl4, float4, n);
+        for (int q = 0; q < 2; ++q) {
+            ALLOC(c->uh[q], float4, n);
+            ALLOC(c->ul[q], float4, n);
+        }
+    }
+    gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, c->st);
+    CK(cudaGetLastError());
+    for (int q = 0; q < 2; ++q) {
+        CK(cudaMemsetAsync(c->u[q], 0, sizeof(dbl4) * n, c->st));
+        if (mixed) {
+            CK(cudaMemsetAsync(c->uh[q], 0, sizeof(float4) * n, c->st));
+            CK(cudaMemsetAsync(c->ul[q], 0, sizeof(float4) * n, c->st));
+        }
+    }
+    CK(cudaMemsetAsync(c->acc, 0, sizeof(dbl4) * n, c->st));
+    CK(cudaMemsetAsync(c->F, 0, sizeof(dbl4) * n, c->st));
+    // grid and contact buffers
+    uint32_t nb = 1024;
+    while ((int64_t)nb < 2 * n && nb < (1u << 26)) nb <<= 1;
+    c->nbuckets = nb;
+    ALLOC(c->gk, uint32_t, n);
+    ALLOC(c->gk2, uint32_t, n);
+    ALLOC(c->gv, uint32_t, n);
+    ALLOC(c->gv2, uint32_t, n);
+    ALLOC(c->gstart, uint32_t, nb);
+    ALLOC(c->gend, uint32_t, nb);
+    ALLOC(c->gcell, uint64_t, n);
+    ALLOC(c->cand_ptr, int64_t, n + 1);
+    ALLOC(c->cand_cnt, int64_t, n + 1);
+    CK(cudaMemsetAsync(c->cand_ptr, 0, sizeof(int64_t) * (n + 1), c->st));
+    c->cand_cap = std::max<int64_t>(1024, 8 * n);
+    ALLOC(c->cand, int2, c->cand_cap);
+    // reductions
+    c->blocks_cap = step_blocks(4, c->opt.device);
+    for (int g : {8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device));
+    ALLOC(c->partials, double, (int64_t)c->blocks_cap * PART_STRIDE);
+    ALLOC(c->react, double, PD_MAX_WALLS * 3);
+    ALLOC(c->disp, double, 1);
+    ALLOC(c->wall_pos, double, PD_MAX_WALLS * 3);
+    ALLOC(c->dscratch, double, 8192);
+    ALLOC(c->counter, unsigned, 1);
+    ALLOC(c->derr, unsigned, 1);
+    ALLOC(c->stale, int, 1);
+    CK(cudaMemsetAsync(c->react, 0, sizeof(double) * PD_MAX_WALLS * 3, c->st));
+    CK(cudaMemsetAsync(c->disp, 0, sizeof(double), c->st));
+    CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->st));
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    CK(cudaMemsetAsync(c->stale, 0, sizeof(int), c->st));
+    ALLOC(c->stage, double, 3 * n);
+    ALLOC(c->snap_u, dbl4, n);
+    ALLOC(c->snap_v, dbl4, n);
+    ALLOC(c->snap_acc, dbl4, n);
+    c->walls.nw = 0;
+    c->lanes = c->opt.lanes_per_node ? c->opt.lanes_per_node : 16;
+    c->blocks = step_blocks(c->lanes, c->opt.device);
+    pd_status s = sync(c);
+    if (s) return s;
+    release(c, dx); release(c, dvol); release(c, dgrain); release(c, dv0);
+    release(c, k1); release(c, k2); release(c, v1); release(c, v2);
+    return PD_OK;
+}
+
+pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t *grain, const double *v0,
+                    const pd_material *mat, const pd_options *opt, pd_ctx **out)
+{
+    if (!out) return PD_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 0x7fffffffLL || !x || !vol || !grain || !mat) return PD_EINVAL;
+    if (!(mat->E > 0) || !(mat->rho > 0) || !(mat->G0 > 0) || !(mat->contact_radius > 0) ||
+        !(mat->contact_factor >= 0) || (mat->constants != 0 && mat->constants != 1) ||
+        (mat->break_mode != 0 && mat->break_mode != 1))
+        return PD_EINVAL;
+    pd_ctx *c = new pd_ctx();
+    if (opt) c->opt = *opt; else pd_default_options(&c->opt);
+    if (c->opt.graph_chunk <= 0) c->opt.graph_chunk = 64;
+    if (c->opt.precision != PD_MIXED && c->opt.precision != PD_FP64) { delete c; return PD_EINVAL; }
+    int l = c->opt.lanes_per_node;
+    if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
+    if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
+    c->mat = *mat;
+    c->n = n;
+    pd_status s = create_impl(c, x, vol, grain, v0);
+    if (s != PD_OK) {
+        fprintf(stderr, "pd_create: %s\n", c->err.c_str());
+        pd_destroy(c);
+        return s;
+    }
+    *out = c;
+    return PD_OK;
+}
+
+static pd_status autotune(pd_ctx *c);
+
+pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_filter *filt)
+{
+    if (!c) return PD_EINVAL;
+    if (!(horizon > 0) || !isfinite(horizon) || nfilt < 0 || nfilt > PD_MAX_FILTERS || (nfilt > 0 && !filt))
+        return fail(c, PD_EINVAL, "bad horizon or filter list");
+    FilterSet f;
+    memset(&f, 0, sizeof(f));
+    f.nf = nfilt;
+    for (int q = 0; q < nfilt; ++q) {
+        if (filt[q].kind != 1 && filt[q].kind != 2) return fail(c, PD_EINVAL, "unknown filter kind");
+        f.kind[q] = filt[q].kind;
+        for (int a = 0; a < 12; ++a) f.a[q][a] = filt[q].a[a];
+    }
+    CK(cudaSetDevice(c->opt.device));
+    clear_graphs(c);
+    c->bonds_ready = false;
+    release(c, c->rowptr); release(c, c->col); release(c, c->brk); release(c, c->kc_of);
+    release(c, c->crow); release(c, c->snap_brk); release(c, c->stage_b);
+    c->delta = horizon;
+    constants(c);
+    const int64_t n = c->n;
+    // grid over the reference positions, cell = horizon
+    GridView g;
+    for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];
+    grid_build(g, c->x4, nullptr, n, horizon * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
+               c->gend, c->gcell, c->tmp, c->st);
+    int64_t *cnt;
+    ALLOC(cnt, int64_t, n + 1);
+    ALLOC(c->rowptr, int64_t, n + 1);
+    bonds_count(c->x4, c->grain, c->perm, n, g, horizon, f, cnt, c->st);
+    scan_exclusive_i64(cnt, c->rowptr, n, c->tmp, c->st);
+    int64_t B = 0;
+    CK(cudaMemcpyAsync(&B, c->rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+    pd_status s = sync(c);
+    if (s) return s;
+    if (B > 0x7fffffffLL) return fail(c, PD_ECAPACITY, "more than 2^31-1 directed bonds");
+    c->B = B;
+    uint64_t *k1, *k2;
+    uint32_t *v1, *v2;
+    int64_t *btmp;
+    ALLOC(k1, uint64_t, B + 1);
+    ALLOC(k2, uint64_t, B + 1);
+    ALLOC(v1, uint32_t, B + 1);
+    ALLOC(v2, uint32_t, B + 1);
+    ALLOC(btmp, int64_t, std::max(radix_tmp_size(B + 1), scan_tmp_size(n + 1) + 8));
+    ALLOC(c->col, int32_t, B + 1);
+    bonds_fill(c->x4, c->grain, c->perm, n, g, horizon, f, c->rowptr, k1, c->sh, c->st);
+    {
+        uint64_t *k = k1, *ka = k2;
+        radix_sort_u64(&k, &ka, nullptr, nullptr, B, 2 * c->sh, btmp, c->st);
+        bonds_keys_to_col(k, B, c->sh, c->col, c->st);
+    }
+    // canonical numbering (caller rows, ascending caller columns)
+    ALLOC(c->kc_of, int32_t, B + 1);
+    ALLOC(c->crow, int64_t, n + 1);
+    {
+        canon_keys(c->rowptr, c->col, c->perm, n, c->sh, k1, v1, c->st);
+        uint64_t *k = k1, *ka = k2;
+        uint32_t *v = v1, *va = v2;
+        radix_sort_u64(&k, &ka, &v, &va, B, 2 * c->sh, btmp, c->st);
+        canon_invert(v, B, c->kc_of, c->st);
+        row_len_caller(c->rowptr, c->inv, n, cnt, c->st);
+        scan_exclusive_i64(cnt, c->crow, n, c->tmp, c->st);
+    }
+    c->nwords = (B + 31) / 32 + 1;
+    ALLOC(c->brk, uint32_t, c->nwords);
+    ALLOC(c->snap_brk, uint32_t, c->nwords);
+    ALLOC(c->stage_b, uint8_t, B + 16);
+    CK(cudaMemsetAsync(c->brk, 0, sizeof(uint32_t) * c->nwords, c->st));
+    CK(cudaGetLastError());
+    s = sync(c);
+    if (s) return s;
+    release(c, k1); release(c, k2); release(c, v1); release(c, v2); release(c, btmp); release(c, cnt);
+    c->bonds_ready = true;
+    if (c->opt.lanes_per_node == 0) {
+        s = autotune(c);
+        if (s) return s;
+    }
+    return eval_forces(c);
+}
+
+pd_status pd_set_walls(pd_ctx *c, int nw, const pd_wall *w)
+{
+    if (!c) return PD_EINVAL;
+    if (nw < 0 || nw > PD_MAX_WALLS || (nw > 0 && !w)) return fail(c, PD_EINVAL, "0 <= nw <= 6 walls");
+    double pos[PD_MAX_WALLS * 3] = {0};
+    WallSet ws;
+    memset(&ws, 0, sizeof(ws));
+    ws.nw = nw;
+    for (int l = 0; l < nw; ++l) {
+        double nn = 0;
+        for (int a = 0; a < 3; ++a) {
+            if (!isfinite(w[l].normal[a]) || !isfinite(w[l].point[a]) || !isfinite(w[l].velocity[a]))
+                return fail(c, PD_EINVAL, "non-finite wall data");
+            nn += w[l].normal[a] * w[l].normal[a];
+        }
+        if (fabs(nn - 1.0) > 1e-12) return fail(c, PD_EINVAL, "wall normals must have unit length");
+        for (int a = 0; a < 3; ++a) {
+            ws.n[l][a] = w[l].normal[a];
+            ws.v[l][a] = w[l].velocity[a];
+            pos[3 * l + a] = w[l].point[a];
+        }
+    }
+    CK(cudaSetDevice(c->opt.device));
+    CK(cudaMemcpyAsync(c->wall_pos, pos, sizeof(pos), cudaMemcpyHostToDevice, c->st));
+    pd_status s = sync(c);
+    if (s) return s;
+    c->walls = ws;
+    clear_graphs(c);
+    if (c->bonds_ready) return eval_forces(c);
+    return PD_OK;
+}
+
+pd_status pd_get_walls(pd_ctx *c, double *points)
+{
+    if (!c || (!points && c->walls.nw)) return PD_EINVAL;
+    if (!c->walls.nw) return PD_OK;
+    CK(cudaMemcpyAsync(points, c->wall_pos, sizeof(double) * 3 * c->walls.nw, cudaMemcpyDeviceToHost, c->st));
+    return sync(c);
+}
+
+pd_status pd_set_body_force(pd_ctx *c, const double b[3])
+{
+    if (!c || !b) return PD_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(b[a])) return fail(c, PD_EINVAL, "non-finite body force");
+    for (int a = 0; a < 3; ++a) c->b[a] = b[a];
+    clear_graphs(c);
+    if (c->bonds_ready) return eval_forces(c);
+    return PD_OK;
+}
+
+pd_status pd_stable_dt(pd_ctx *c, double *dt)
+{
+    if (!c || !dt) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_stable_dt before pd_build_bonds");
+    CK(cudaSetDevice(c->opt.device));
+    int nb = stable_dt_blocks(c->n);
+    stable_dt(c->x4, c->rowptr, c->col, c->n, c->c, c->mat.rho, c->dscratch, c->st);
+    std::vector<double> h(nb);
+    CK(cudaMemcpyAsync(h.data(), c->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    pd_status s = sync(c);
+    if (s) return s;
+    double m = INFINITY;
+    for (double q : h) m = std::min(m, q);
+    *dt = m;
+    return PD_OK;
+}
+
+// ---- stepping -------------------------------------------------------------------
+// Enqueues one chunk of `steps` Verlet steps starting from u[parity]; contact
+// lists are rebuilt before the first step and then every k steps.
+static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
+{
+    int64_t launches = 0;
+    StepParams p = params(c, MODE_FULL, parity, dt);
+    launch_drift(p, c->st);
+    ++launches;
+    int in = parity ^ 1;
+    for (int s = 0; s < steps; ++s) {
+        if (c->opt.contact && s % k == 0) {
+            enqueue_rebuild(c, in);
+            launches += 12;
+        }
+        const bool last = (s == steps - 1);
+        StepParams q = params(c, last ? MODE_FINAL : MODE_FULL, in, dt);
+        const bool prof = c->profiling && c->prof_used + 2 <= (int)c->prof_ev.size();
+        if (prof) cudaEventRecord(c->prof_ev[c->prof_used], c->st);
+        launch_step(q, c->lanes, c->blocks, c->st);
+        if (prof) {
+            cudaEventRecord(c->prof_ev[c->prof_used + 1], c->st);
+            c->prof_used += 2;
+        }
+        ++launches;
+        if (!last) in ^= 1;
+    }
+    return launches;
+}
+
+static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, GraphEntry **out)
+{
+    for (auto &g : c->graphs)
+        if (g.steps == steps && g.k == k && g.parity == parity && g.dt == dt) { *out = &g; return PD_OK; }
+    if (c->graphs.size() >= 6) clear_graphs(c);
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+    int64_t launches = enqueue_chunk(c, steps, k, parity, dt);
+    cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(c, PD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)); }
+    GraphEntry ge;
+    ge.steps = steps; ge.k = k; ge.parity = parity; ge.dt = dt; ge.launches = launches;
+    e = cudaGraphInstantiate(&ge.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(c, PD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
+    c->graphs.push_back(ge);
+    *out = &c->graphs.back();
+    return PD_OK;
+}
+
+static pd_status snapshot(pd_ctx *c, bool restore)
+{
+    const size_t nb = sizeof(dbl4) * c->n;
+    if (!restore) {
+        CK(cudaMemcpyAsync(c->snap_u, c->u[c->cur], nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->snap_v, c->v, nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->snap_acc, c->acc, nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->snap_brk, c->brk, sizeof(uint32_t) * c->nwords, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 3,
+                           cudaMemcpyDeviceToDevice, c->st));
+    } else {
+        CK(cudaMemcpyAsync(c->u[c->cur], c->snap_u, nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->v, c->snap_v, nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->acc, c->snap_acc, nb, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->brk, c->snap_brk, sizeof(uint32_t) * c->nwords, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(c->wall_pos, c->dscratch + 4096, sizeof(double) * PD_MAX_WALLS * 3,
+                           cudaMemcpyDeviceToDevice, c->st));
+        if (c->opt.precision == PD_MIXED) split_hilo(c->u[c->cur], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+        CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    }
+    return PD_OK;
+}
+
+static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
+{
+    if (!c->opt.contact) { *k = 1 << 30; return PD_OK; }
+    if (c->opt.contact_every > 0) { *k = c->opt.contact_every; return PD_OK; }
+    int nb = vmax_blocks(c->n);
+    vmax(c->v, c->n, c->dscratch, c->st);
+    std::vector<double> h(nb);
+    CK(cudaMemcpyAsync(h.data(), c->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    pd_status s = sync(c);
+    if (s) return s;
+    double vm = 0;
+    for (double q : h) vm = std::max(vm, q);
+    for (int l = 0; l < c->walls.nw; ++l)
+        vm = std::max(vm, sqrt(c->walls.v[l][0] * c->walls.v[l][0] + c->walls.v[l][1] * c->walls.v[l][1] +
+                               c->walls.v[l][2] * c->walls.v[l][2]));
+    double steps = skin_of(c) / (2.0 * 1.5 * dt * std::max(vm, 1e-30));
+    *k = (int)std::max(1.0, std::min(steps, (double)c->opt.graph_chunk));
+    return PD_OK;
+}
+
+static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t *launches)
+{
+    int64_t left = nsteps;
+    *launches = 0;
+    while (left > 0) {
+        int steps = (int)std::min<int64_t>(left, c->opt.graph_chunk);
+        if (c->profiling) {
+            int kk = std::min(k, steps);
+            if ((int)c->prof_ev.size() < c->prof_used + 2 * steps) {
+                int want = c->prof_used + 2 * steps;
+                while ((int)c->prof_ev.size() < want) {
+                    cudaEvent_t e;
+                    CK(cudaEventCreate(&e));
+                    c->prof_ev.push_back(e);
+                }
+            }
+            *launches += enqueue_chunk(c, steps, kk, c->cur, dt);
+            CK(cudaGetLastError());
+            c->cur ^= (steps & 1);
+            left -= steps;
+            continue;
+        }
+        GraphEntry *g;
+        pd_status s = get_graph(c, steps, std::min(k, steps), c->cur, dt, &g);
+        if (s) return s;
+        CK(cudaGraphLaunch(g->exec, c->st));
+        *launches += g->launches;
+        c->cur ^= (steps & 1);
+        left -= steps;
+    }
+    return PD_OK;
+}
+
+pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
+{
+    if (!c) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_step before pd_build_bonds");
+    if (c->latched) return fail(c, PD_ESTATE, "a device error is latched; call pd_set_state");
+    if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return fail(c, PD_EINVAL, "dt must be > 0 and nsteps >= 0");
+    if (nsteps == 0) return PD_OK;
+    CK(cudaSetDevice(c->opt.device));
+    int k;
+    pd_status s = rebuild_period(c, dt, &k);
+    if (s) return s;
+    const int cur0 = c->cur;
+    s = snapshot(c, false);
+    if (s) return s;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        int64_t launches = 0;
+        c->prof_used = 0;
+        CK(cudaEventRecord(c->ev0, c->st));
+        s = run_steps(c, dt, nsteps, k, &launches);
+        if (s) return s;
+        CK(cudaEventRecord(c->ev1, c->st));
+        unsigned e = 0;
+        s = read_err(c, &e);
+        if (s) return s;
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->last_ms = ms;
+        c->last_launches = launches;
+        c->last_force_ms = 0;
+        for (int q = 0; q + 1 < c->prof_used; q += 2) {
+            float m = 0;
+            CK(cudaEventElapsedTime(&m, c->prof_ev[q], c->prof_ev[q + 1]));
+            c->last_force_ms += m;
+        }
+        if (!e) {
+            c->t += dt * (double)nsteps;
+            return PD_OK;
+        }
+        c->cur = cur0;
+        s = snapshot(c, true);
+        if (s) return s;
+        if (e & (PDE_NONFINITE | PDE_WALL)) {
+            c->latched |= e & (PDE_NONFINITE | PDE_WALL);
+            sync(c);
+            return status_of(c, e);
+        }
+        if (e & PDE_CAPACITY) {
+            s = grow_candidates(c);
+            if (s) return s;
+        }
+        if (e & PDE_SKIN) {
+            if (k == 1) return fail(c, PD_ETIMEOUT, "contact list stale even when rebuilt every step");
+            k = std::max(1, k / 2);
+        }
+    }
+    return fail(c, PD_ECAPACITY, "pd_step retried too often");
+}
+
+static pd_status autotune(pd_ctx *c)
+{
+    // time a force evaluation (idempotent at a fixed state) for each lane count
+    const int cand[4] = {4, 8, 16, 32};
+    double best = INFINITY;
+    int bestl = 16;
+    if (c->opt.contact) enqueue_rebuild(c, c->cur);
+    for (int q = 0; q < 4; ++q) {
+        const int l = cand[q];
+        const int blocks = step_blocks(l, c->opt.device);
+        StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
+        launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
+        CK(cudaEventRecord(c->ev0, c->st));
+        for (int r = 0; r < 5; ++r) launch_step(p, l, blocks, c->st);
+        CK(cudaEventRecord(c->ev1, c->st));
+        CK(cudaEventSynchronize(c->ev1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        c->tune_ms[q] = ms / 5.0;
+        if (c->tune_ms[q] < best) { best = c->tune_ms[q]; bestl = l; }
+    }
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    c->lanes = bestl;
+    c->blocks = step_blocks(bestl, c->opt.device);
+    clear_graphs(c);
+    return sync(c);
+}
+
+// ---- queries ----------------------------------------------------------------------
+pd_status pd_damage(pd_ctx *c, double *phi)
+{
+    if (!c || !phi) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_damage before pd_build_bonds");
+    CK(cudaSetDevice(c->opt.device));
+    damage(c->rowptr, c->brk, c->perm, c->n, c->stage, c->st);
+    CK(cudaMemcpyAsync(phi, c->stage, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->st));
+    return sync(c);
+}
+
+pd_status pd_bulk_stress(pd_ctx *c, const double *area, double sigma[6], double *wall_force)
+{
+    if (!c || !sigma) return PD_EINVAL;
+    const int nw = c->walls.nw;
+    double R[PD_MAX_WALLS * 3] = {0};
+    if (nw) {
+        if (!area) return fail(c, PD_EINVAL, "area is required when walls are set");
+        CK(cudaMemcpyAsync(R, c->react, sizeof(double) * 3 * nw, cudaMemcpyDeviceToHost, c->st));
+        pd_status s = sync(c);
+        if (s) return s;
+    }
+    double S[3][3] = {{0}}, cnt[3] = {0, 0, 0};
+    for (int l = 0; l < nw; ++l) {
+        if (!(area[l] > 0)) return fail(c, PD_EINVAL, "wall areas must be positive");
+        double m[3] = {-c->walls.n[l][0], -c->walls.n[l][1], -c->walls.n[l][2]};
+        int k = 0;
+        for (int a = 1; a < 3; ++a)
+            if (fabs(m[a]) > fabs(m[k])) k = a;
+        const double sg = m[k] > 0 ? 1.0 : -1.0;
+        for (int a = 0; a < 3; ++a) S[a][k] += -(R[3 * l + a] / area[l]) * sg;
+        cnt[k] += 1;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (cnt[k] > 0)
+            for (int a = 0; a < 3; ++a) S[a][k] /= cnt[k];
+    double T[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b2 = 0; b2 < 3; ++b2) T[a][b2] = 0.5 * (S[a][b2] + S[b2][a]);
+    sigma[0] = T[0][0]; sigma[1] = T[1][1]; sigma[2] = T[2][2];
+    sigma[3] = T[1][2]; sigma[4] = T[0][2]; sigma[5] = T[0][1];
+    if (wall_force)
+        for (int q = 0; q < 3 * nw; ++q) wall_force[q] = R[q];
+    return PD_OK;
+}
+
+pd_status pd_num_bonds(pd_ctx *c, int64_t *B)
+{
+    if (!c || !B) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+    *B = c->B;
+    return PD_OK;
+}
+
+pd_status pd_bonds(pd_ctx *c, int64_t *rowptr, int32_t *col)
+{
+    if (!c || !rowptr || !col) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+    CK(cudaSetDevice(c->opt.device));
+    CK(cudaMemcpyAsync(rowptr, c->crow, sizeof(int64_t) * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+    if (c->B) {
+        int32_t *tmpc = (int32_t *)pd_dev_alloc(c, sizeof(int32_t) * c->B);
+        if (!tmpc) return fail(c, PD_ENOMEM, "pd_bonds staging");
+        col_caller(c->col, c->perm, c->kc_of, c->B, tmpc, c->st);
+        CK(cudaMemcpyAsync(col, tmpc, sizeof(int32_t) * c->B, cudaMemcpyDeviceToHost, c->st));
+        pd_status s = sync(c);
+        pd_dev_free(c, tmpc);
+        return s;
+    }
+    return sync(c);
+}
+
+pd_status pd_contacts(pd_ctx *c, int64_t *npairs, int32_t *ij)
+{
+    if (!c || !npairs) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+    CK(cudaSetDevice(c->opt.device));
+    const int64_t n = c->n;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        enqueue_rebuild(c, c->cur);
+        unsigned e = 0;
+        pd_status s = read_err(c, &e);
+        if (s) return s;
+        if (e & PDE_CAPACITY) {
+            s = grow_candidates(c);
+            if (s) return s;
+            continue;
+        }
+        break;
+    }
+    int64_t *cnt = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (n + 1));
+    int64_t *off = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (n + 1));
+    if (!cnt || !off) { pd_dev_free(c, cnt); pd_dev_free(c, off); return fail(c, PD_ENOMEM, "pd_contacts staging"); }
+    pairs_count(c->x4, c->u[c->cur], c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, cnt, c->st);
+    scan_exclusive_i64(cnt, off, n, c->tmp, c->st);
+    int64_t total = 0;
+    cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
+    pd_status s = sync(c);
+    if (s == PD_OK && ij) {
+        if (total > *npairs) {
+            s = fail(c, PD_ECAPACITY, "pair buffer too small");
+        } else if (total > 0) {
+            int32_t *out = (int32_t *)pd_dev_alloc(c, sizeof(int32_t) * 2 * total);
+            if (!out) {
+                s = fail(c, PD_ENOMEM, "pd_contacts output");
+            } else {
+                pairs_fill(c->x4, c->u[c->cur], c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, off,
+                           out, c->st);
+                cudaMemcpyAsync(ij, out, sizeof(int32_t) * 2 * total, cudaMemcpyDeviceToHost, c->st);
+                s = sync(c);
+                pd_dev_free(c, out);
+                if (s == PD_OK) {
+                    std::vector<std::pair<int32_t, int32_t>> v(total);
+                    for (int64_t q = 0; q < total; ++q) v[q] = {ij[2 * q], ij[2 * q + 1]};
+                    std::sort(v.begin(), v.end());
+                    for (int64_t q = 0; q < total; ++q) { ij[2 * q] = v[q].first; ij[2 * q + 1] = v[q].second; }
+                }
+            }
+        }
+    }
+    *npairs = total;
+    pd_dev_free(c, cnt);
+    pd_dev_free(c, off);
+    return s;
+}
+
+pd_status pd_forces(pd_ctx *c, double *F)
+{
+    if (!c || !F) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+    CK(cudaSetDevice(c->opt.device));
+    pd_status s = eval_forces(c);
+    if (s) return s;
+    to_caller(c->F, c->perm, c->n, c->stage, c->st);
+    CK(cudaMemcpyAsync(F, c->stage, sizeof(double) * 3 * c->n, cudaMemcpyDeviceToHost, c->st));
+    return sync(c);
+}
+
+pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double *t)
+{
+    if (!c) return PD_EINVAL;
+    CK(cudaSetDevice(c->opt.device));
+    const size_t nb = sizeof(double) * 3 * c->n;
+    if (u) {
+        to_caller(c->u[c->cur], c->perm, c->n, c->stage, c->st);
+        CK(cudaMemcpyAsync(u, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
+    }
+    if (v) {
+        if (u) { pd_status s = sync(c); if (s) return s; }
+        to_caller(c->v, c->perm, c->n, c->stage, c->st);
+        CK(cudaMemcpyAsync(v, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
+    }
+    if (broken) {
+        if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+        if (c->B) {
+            bits_to_bytes(c->brk, c->kc_of, c->B, c->stage_b, c->st);
+            CK(cudaMemcpyAsync(broken, c->stage_b, c->B, cudaMemcpyDeviceToHost, c->st));
+        }
+    }
+    if (t) *t = c->t;
+    return sync(c);
+}
+
+pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_t *broken, const double *t)
+{
+    if (!c) return PD_EINVAL;
+    CK(cudaSetDevice(c->opt.device));
+    const size_t nb = sizeof(double) * 3 * c->n;
+    if (u) {
+        for (int64_t q = 0; q < 3 * c->n; ++q)
+            if (!isfinite(u[q])) return fail(c, PD_EINVAL, "u contains a non-finite value");
+        CK(cudaMemcpyAsync(c->stage, u, nb, cudaMemcpyHostToDevice, c->st));
+        from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
+        if (c->opt.precision == PD_MIXED) split_hilo(c->u[c->cur], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+        pd_status s = sync(c);
+        if (s) return s;
+    }
+    if (v) {
+        for (int64_t q = 0; q < 3 * c->n; ++q)
+            if (!isfinite(v[q])) return fail(c, PD_EINVAL, "v contains a non-finite value");
+        CK(cudaMemcpyAsync(c->stage, v, nb, cudaMemcpyHostToDevice, c->st));
+        from_caller(c->stage, c->perm, c->n, c->v, c->st);
+        pd_status s = sync(c);
+        if (s) return s;
+    }
+    if (broken) {
+        if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
+        if (c->B) {
+            CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
+            bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
+        }
+    }
+    if (t) c->t = *t;
+    c->latched = 0;
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    pd_status s = sync(c);
+    if (s) return s;
+    if (c->bonds_ready) return eval_forces(c);
+    return PD_OK;
+}
+
+pd_status pd_tuning(pd_ctx *c, int *lanes, double ms[4])
+{
+    if (!c) return PD_EINVAL;
+    if (lanes) *lanes = c->lanes;
+    if (ms)
+        for (int q = 0; q < 4; ++q) ms[q] = c->tune_ms[q];
+    return PD_OK;
+}
+
+pd_status pd_set_profiling(pd_ctx *c, int on)
+{
+    if (!c) return PD_EINVAL;
+    c->profiling = on != 0;
+    return PD_OK;
+}
+
+pd_status pd_last_step_stats(pd_ctx *c, double *ms_force, double *ms_total, int64_t *launches)
+{
+    if (!c) return PD_EINVAL;
+    if (ms_force) *ms_force = c->last_force_ms;
+    if (ms_total) *ms_total = c->last_ms;
+    if (launches) *launches = c->last_launches;
+    return PD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations of libpd (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/pd.h"
+
+#define PD_MAX_WALLS 6
+
+// 32-byte aligned double quadruple: one 256-bit load on sm_100+ parts
+typedef double4_32a dbl4;
+
+// device error bits (latched in pd_ctx::d_err)
+enum : unsigned {
+    PDE_NONFINITE = 1u,
+    PDE_WALL = 2u,
+    PDE_CAPACITY = 4u,   // contact candidate list overflow
+    PDE_SKIN = 8u        // a node moved more than half the skin between rebuilds
+};
+
+// what the fused step kernel does after the force evaluation
+enum StepMode : int {
+    MODE_FORCES = 0,  // store F and a; no velocity/position change
+    MODE_FULL = 1,    // finish this step's kick, next half-kick, drift (writes other buffer)
+    MODE_FINAL = 2    // finish this step's kick only
+};
+
+struct WallSet {
+    int nw;
+    double n[PD_MAX_WALLS][3];
+    double v[PD_MAX_WALLS][3];
+};
+
+// Everything the force/update kernels need, passed by value.
+struct StepParams {
+    int64_t n;
+    const int64_t *rowptr;
+    const int32_t *col;
+    uint32_t *brk;                 // broken bit per directed slot
+    // mixed-precision gather records
+    const float4 *xh4;             // (x_hi, V)
+    const float4 *xl4;             // (x_lo, 0)
+    const float4 *uh_in, *ul_in;   // u split, current buffer
+    float4 *uh_out, *ul_out;       // u split, next buffer
+    // FP64 state
+    const dbl4 *x4;             // (x, V)
+    const dbl4 *u_in;           // u, current buffer
+    dbl4 *u_out;                // u, next buffer
+    dbl4 *v;                    // velocity (in place)
+    dbl4 *acc;                  // acceleration (F + b)/rho, stored
+    dbl4 *F_out;                // force density (MODE_FORCES), may be null
+    const int32_t *grain;
+    // contact candidates (CSR; each entry = (j, bond slot or -1))
+    int contact;
+    const int64_t *cand_ptr;
+    const int2 *cand;
+    // constants
+    double c, s0, Kn, Rc, rho, dt;
+    float cf, s0f;
+    int break_mode;
+    int mode;
+    WallSet walls;
+    double *wall_pos;              // nw*3, current wall points (device)
+    double b[3];
+    // per-block partials and the last-block reduction
+    double *partials;              // gridDim.x * PART_STRIDE
+    unsigned *counter;
+    unsigned *err;
+    double *react;                 // nw*3 final wall reactions
+    double *disp;                  // accumulated displacement bound since last rebuild
+    double skin;
+    int *stale;                    // set when 2*disp >= skin
+};
+
+#define PART_STRIDE 20  // 18 reaction components + max|v| + spare
+
+// Radix sort of (key, value) pairs, LSD 8-bit digits, stable.  bits = number of
+// low key bits to sort.  Buffers are ping-ponged; the result is in (*k, *v)
+// (pointers swapped as needed).  hist must hold radix_tmp_size(n) int64.
+int radix_blocks(int64_t n);
+int64_t radix_tmp_size(int64_t n);
+void radix_sort_u64(uint64_t **k, uint64_t **kalt, uint32_t **v, uint32_t **valt, int64_t n, int bits,
+                    int64_t *hist, cudaStream_t st);
+void radix_sort_u32(uint32_t **k, uint32_t **kalt, uint32_t **v, uint32_t **valt, int64_t n, int bits,
+                    int64_t *hist, cudaStream_t st);
+// Exclusive scan of n int64 values (in may equal out); out[n] receives the total.
+// tmp must hold scan_tmp_size(n) int64.
+int64_t scan_tmp_size(int64_t n);
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tmp, cudaStream_t st);
+void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *tmp,
+                               cudaStream_t st);
+
+// Step kernels (pd_step.cu)
+void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
+void launch_drift(const StepParams &p, cudaStream_t st);
+int step_blocks(int lanes, int device);
+
+// Device memory handle with the caller's allocator.
+struct pd_ctx;
+void *pd_dev_alloc(pd_ctx *c, size_t bytes);
+void pd_dev_free(pd_ctx *c, void *p);

@@ -1,0 +1,387 @@
+// Fused force evaluation and velocity-Verlet update.
+//
+// One launch per time step.  A group of G lanes owns one node i (row of the
+// bond CSR) at a time, in a grid-stride loop over rows:
+//   1. bond loop (Eq. peri-damage): each lane takes every G-th slot of row i,
+//      skips broken slots (one bit per directed slot), computes the stretch,
+//      breaks the bond (atomicOr of its bit) when s > s0, or accumulates
+//      c s V_j (xi + eta)/|xi + eta|;
+//   2. contact loop (Sec. 3.2, self-contact law): candidates of row i from the
+//      skin list, exact |d|^2 < R_c^2 test in FP64, same-grain pairs skipped
+//      while their bond bit is intact;
+//   3. the group's partial sums are combined with xor shuffles;
+//   4. the group leader adds the wall cap force (Sec. 4.1, FP64), forms
+//      a = (F + b)/rho and performs the Verlet kick(s) and drift (Sec. 5.2).
+// Positions are double-buffered: step n reads u^n and writes u^{n+1}, so every
+// gather of step n sees the same state.  Per-block wall-reaction partials and
+// the max |v| are combined by the last block to finish (fixed order, so runs
+// are bitwise reproducible).
+//
+// Mixed path: u and x are held as float pairs (hi = RN(value), lo =
+// RN(value - hi)); xi and eta are formed from hi and lo differences, which keeps
+// the cancellation in u_j - u_i exact to ~2^-48 |u| while using FP32 units only.
+// The stretch uses the cancellation-free form
+//   s = eta . (2 xi + eta) / (|xi| (|xi + eta| + |xi|)),
+// which equals (|xi + eta| - |xi|)/|xi| exactly in real arithmetic.
+#include "pd_internal.cuh"
+
+namespace {
+
+constexpr int STEP_THREADS = 256;
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+
+struct F3 {
+    float x, y, z;
+};
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ double group_sum(double v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Wall cap force on a node at p (Sec. 4.1).  Returns error bits.
+__device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, double py, double pz,
+                                               double vol, double &fx, double &fy, double &fz,
+                                               double *react)
+{
+    unsigned e = 0;
+    for (int l = 0; l < p.walls.nw; ++l) {
+        const double nx = p.walls.n[l][0], ny = p.walls.n[l][1], nz = p.walls.n[l][2];
+        const double *w = p.wall_pos + 3 * l;
+        double d = dadd(dadd(dmul(px - w[0], nx), dmul(py - w[1], ny)), dmul(pz - w[2], nz));
+        if (!(d < p.Rc)) continue;
+        if (d <= -p.Rc) { e |= PDE_WALL; continue; }
+        double hc = p.Rc - d;
+        double vcap = (M_PI / 3.0) * hc * hc * (2.0 * p.Rc + d);
+        double q = p.Rc * p.Rc - d * d;
+        double zbar = (M_PI / 4.0) * q * q / vcap;
+        double mag = p.Kn * (p.Rc - zbar) * vcap;
+        fx += mag * nx; fy += mag * ny; fz += mag * nz;
+        react[3 * l + 0] -= mag * nx * vol;
+        react[3 * l + 1] -= mag * ny * vol;
+        react[3 * l + 2] -= mag * nz * vol;
+    }
+    return e;
+}
+
+template <int G, bool MIXED>
+__global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
+    __shared__ double s_vmax[GPB];
+    __shared__ unsigned s_err;
+    __shared__ bool s_last;
+
+    const int gl = threadIdx.x % G;
+    const int grp = threadIdx.x / G;
+    if (gl == 0) {
+        for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
+        s_vmax[grp] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
+    }
+    __syncthreads();
+    unsigned err = 0;
+    double vmax2 = 0.0;
+    const double hdt = 0.5 * p.dt;
+
+    for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
+        const int64_t row = r0 + grp;
+        const bool active = row < p.n;
+        // ---- 1. bonds
+        float fbx = 0.f, fby = 0.f, fbz = 0.f;
+        double fdx = 0.0, fdy = 0.0, fdz = 0.0;
+        if (active) {
+            const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
+            if (MIXED) {
+                const float4 oxh = p.xh4[row], oxl = p.xl4[row], ouh = p.uh_in[row], oul = p.ul_in[row];
+                for (int64_t k = k0 + gl; k < k1; k += G) {
+                    const uint32_t w = p.brk[k >> 5];
+                    if ((w >> (k & 31)) & 1u) continue;
+                    const int j = __ldg(p.col + k);
+                    const float4 a = __ldg(p.xh4 + j), b = __ldg(p.xl4 + j);
+                    const float4 c = __ldg(p.uh_in + j), d = __ldg(p.ul_in + j);
+                    const float xx = (a.x - oxh.x) + (b.x - oxl.x);
+                    const float xy = (a.y - oxh.y) + (b.y - oxl.y);
+                    const float xz = (a.z - oxh.z) + (b.z - oxl.z);
+                    const float ex = (c.x - ouh.x) + (d.x - oul.x);
+                    const float ey = (c.y - ouh.y) + (d.y - oul.y);
+                    const float ez = (c.z - ouh.z) + (d.z - oul.z);
+                    const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
+                    const float L2 = fmaf(xx, xx, fmaf(xy, xy, xz * xz));
+                    const float y2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz));
+                    const float num = fmaf(ex, xx + yx, fmaf(ey, xy + yy, ez * (xz + yz)));
+                    const float rL = rsqrtf(L2), ry = rsqrtf(y2);
+                    const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
+                    const bool brk = p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f);
+                    if (brk) {
+                        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+                    } else {
+                        const float g = p.cf * a.w * s * ry;
+                        fbx = fmaf(g, yx, fbx);
+                        fby = fmaf(g, yy, fby);
+                        fbz = fmaf(g, yz, fbz);
+                    }
+                }
+            } else {
+                const dbl4 ox = p.x4[row], ou = p.u_in[row];
+                for (int64_t k = k0 + gl; k < k1; k += G) {
+                    const uint32_t w = p.brk[k >> 5];
+                    if ((w >> (k & 31)) & 1u) continue;
+                    const int j = __ldg(p.col + k);
+                    const dbl4 a = p.x4[j], c = p.u_in[j];
+                    const double xx = a.x - ox.x, xy = a.y - ox.y, xz = a.z - ox.z;
+                    const double ex = c.x - ou.x, ey = c.y - ou.y, ez = c.z - ou.z;
+                    const double yx = xx + ex, yy = xy + ey, yz = xz + ez;
+                    const double L = sqrt(xx * xx + xy * xy + xz * xz);
+                    const double l = sqrt(yx * yx + yy * yy + yz * yz);
+                    const double s = (l - L) / L;
+                    const bool brk = p.break_mode ? (fabs(s) > p.s0) : (s > p.s0);
+                    if (brk) {
+                        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+                    } else {
+                        const double g = p.c * s * a.w / l;
+                        fdx += g * yx; fdy += g * yy; fdz += g * yz;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // ---- 2. contact candidates (FP64, exact predicate)
+        if (active && p.contact) {
+            const int64_t c0 = p.cand_ptr[row], c1 = p.cand_ptr[row + 1];
+            if (c1 > c0) {
+                const dbl4 ox = p.x4[row], ou = p.u_in[row];
+                const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
+                const int gi = p.grain[row];
+                const double R2 = dmul(p.Rc, p.Rc);
+                for (int64_t q = c0 + gl; q < c1; q += G) {
+                    const int2 cj = p.cand[q];
+                    const int j = cj.x;
+                    if (cj.y >= 0) {
+                        const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
+                        if (!((w >> (cj.y & 31)) & 1u)) continue;  // bond intact
+                    }
+                    const dbl4 xj = p.x4[j], uj = p.u_in[j];
+                    const double dx = dadd(xj.x, uj.x) - pix;
+                    const double dy = dadd(xj.y, uj.y) - piy;
+                    const double dz = dadd(xj.z, uj.z) - piz;
+                    const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+                    if (!(d2 < R2)) continue;
+                    const double dn = sqrt(d2);
+                    if (dn == 0.0) continue;
+                    double mag;
+                    const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
+                    const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
+                    if (p.grain[j] != gi || L >= p.Rc) {
+                        mag = -p.Kn * (p.Rc - dn);
+                    } else {
+                        const double sr = (dn - L) / L;
+                        mag = p.c * (sr < 0.0 ? sr : 0.0);
+                    }
+                    const double gm = mag * xj.w / dn;
+                    fdx += gm * dx; fdy += gm * dy; fdz += gm * dz;
+                }
+            }
+        }
+        // ---- 3. combine the group
+        if (MIXED) {
+            fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
+        }
+        fdx = group_sum<G>(fdx); fdy = group_sum<G>(fdy); fdz = group_sum<G>(fdz);
+        // ---- 4. walls and Verlet update (group leader)
+        if (active && gl == 0) {
+            double Fx = fdx + (double)fbx, Fy = fdy + (double)fby, Fz = fdz + (double)fbz;
+            const dbl4 ox = p.x4[row], ou = p.u_in[row];
+            if (p.walls.nw) {
+                err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, Fx, Fy,
+                                  Fz, s_react[grp]);
+            }
+            if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
+            dbl4 a;
+            a.x = __ddiv_rn(dadd(Fx, p.b[0]), p.rho);
+            a.y = __ddiv_rn(dadd(Fy, p.b[1]), p.rho);
+            a.z = __ddiv_rn(dadd(Fz, p.b[2]), p.rho);
+            a.w = 0.0;
+            if (p.mode != MODE_FULL) p.acc[row] = a;
+            if (p.mode == MODE_FORCES) {
+                if (p.F_out) {
+                    dbl4 f; f.x = Fx; f.y = Fy; f.z = Fz; f.w = 0.0;
+                    p.F_out[row] = f;
+                }
+            } else {
+                dbl4 v = p.v[row];
+                v.x = dadd(v.x, dmul(hdt, a.x));
+                v.y = dadd(v.y, dmul(hdt, a.y));
+                v.z = dadd(v.z, dmul(hdt, a.z));
+                if (p.mode == MODE_FULL) {
+                    v.x = dadd(v.x, dmul(hdt, a.x));
+                    v.y = dadd(v.y, dmul(hdt, a.y));
+                    v.z = dadd(v.z, dmul(hdt, a.z));
+                    dbl4 un;
+                    un.x = dadd(ou.x, dmul(p.dt, v.x));
+                    un.y = dadd(ou.y, dmul(p.dt, v.y));
+                    un.z = dadd(ou.z, dmul(p.dt, v.z));
+                    un.w = 0.0;
+                    p.u_out[row] = un;
+                    if (MIXED) {
+                        float4 h, lo;
+                        h.x = __double2float_rn(un.x); lo.x = __double2float_rn(un.x - (double)h.x);
+                        h.y = __double2float_rn(un.y); lo.y = __double2float_rn(un.y - (double)h.y);
+                        h.z = __double2float_rn(un.z); lo.z = __double2float_rn(un.z - (double)h.z);
+                        h.w = 0.f; lo.w = 0.f;
+                        p.uh_out[row] = h;
+                        p.ul_out[row] = lo;
+                    }
+                    const double vv = v.x * v.x + v.y * v.y + v.z * v.z;
+                    vmax2 = fmax(vmax2, vv);
+                    if (!isfinite(vv) || !isfinite(un.x + un.y + un.z)) err |= PDE_NONFINITE;
+                }
+                p.v[row] = v;
+            }
+        }
+    }
+    // ---- block epilogue: partials, last-block reduction
+    if (gl == 0) s_vmax[grp] = vmax2;
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    double *part = p.partials + (int64_t)blockIdx.x * PART_STRIDE;
+    if (threadIdx.x < PD_MAX_WALLS * 3) {
+        double s = 0.0;
+        for (int g = 0; g < GPB; ++g) s += s_react[g][threadIdx.x];
+        part[threadIdx.x] = s;
+    } else if (threadIdx.x == PD_MAX_WALLS * 3) {
+        double m = 0.0;
+        for (int g = 0; g < GPB; ++g) m = fmax(m, s_vmax[g]);
+        part[PD_MAX_WALLS * 3] = m;
+        if (s_err) atomicOr(p.err, s_err);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev = atomicAdd(p.counter, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x < PD_MAX_WALLS * 3) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            s += ((volatile double *)p.partials)[(int64_t)b * PART_STRIDE + threadIdx.x];
+        if (threadIdx.x < 3 * p.walls.nw) p.react[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 32) {
+        double m = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            m = fmax(m, ((volatile double *)p.partials)[(int64_t)b * PART_STRIDE + PD_MAX_WALLS * 3]);
+        if (p.mode == MODE_FULL) {
+            double dsp = *p.disp + p.dt * sqrt(m);
+            *p.disp = dsp;
+            if (2.0 * dsp >= p.skin) *p.stale = 1;
+            for (int l = 0; l < p.walls.nw; ++l)
+                for (int q = 0; q < 3; ++q)
+                    p.wall_pos[3 * l + q] = dadd(p.wall_pos[3 * l + q], dmul(p.dt, p.walls.v[l][q]));
+        }
+        *p.counter = 0u;
+    }
+}
+
+// First half of a chunk's first step: v += dt/2 a; u^{n+1} = u^n + dt v; walls move.
+template <bool MIXED>
+__global__ void k_drift(const StepParams p)
+{
+    const double hdt = 0.5 * p.dt;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        dbl4 v = p.v[i];
+        const dbl4 a = p.acc[i], u = p.u_in[i];
+        v.x = dadd(v.x, dmul(hdt, a.x));
+        v.y = dadd(v.y, dmul(hdt, a.y));
+        v.z = dadd(v.z, dmul(hdt, a.z));
+        dbl4 un;
+        un.x = dadd(u.x, dmul(p.dt, v.x));
+        un.y = dadd(u.y, dmul(p.dt, v.y));
+        un.z = dadd(u.z, dmul(p.dt, v.z));
+        un.w = 0.0;
+        p.v[i] = v;
+        p.u_out[i] = un;
+        if (MIXED) {
+            float4 h, lo;
+            h.x = __double2float_rn(un.x); lo.x = __double2float_rn(un.x - (double)h.x);
+            h.y = __double2float_rn(un.y); lo.y = __double2float_rn(un.y - (double)h.y);
+            h.z = __double2float_rn(un.z); lo.z = __double2float_rn(un.z - (double)h.z);
+            h.w = 0.f; lo.w = 0.f;
+            p.uh_out[i] = h;
+            p.ul_out[i] = lo;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int l = 0; l < p.walls.nw; ++l)
+            for (int q = 0; q < 3; ++q)
+                p.wall_pos[3 * l + q] = dadd(p.wall_pos[3 * l + q], dmul(p.dt, p.walls.v[l][q]));
+    }
+}
+
+template <int G>
+void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
+{
+    if (mixed)
+        k_step<G, true><<<blocks, STEP_THREADS, 0, st>>>(p);
+    else
+        k_step<G, false><<<blocks, STEP_THREADS, 0, st>>>(p);
+}
+
+}  // namespace
+
+int step_blocks(int lanes, int device)
+{
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    switch (lanes) {
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<4, true>, STEP_THREADS, 0); break;
+        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<8, true>, STEP_THREADS, 0); break;
+        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<16, true>, STEP_THREADS, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<32, true>, STEP_THREADS, 0); break;
+    }
+    if (per < 1) per = 1;
+    if (sms < 1) sms = 1;
+    return sms * per;
+}
+
+void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st)
+{
+    const bool mixed = p.xh4 != nullptr;
+    switch (lanes) {
+        case 4: launch_g<4>(p, blocks, st, mixed); break;
+        case 8: launch_g<8>(p, blocks, st, mixed); break;
+        case 16: launch_g<16>(p, blocks, st, mixed); break;
+        default: launch_g<32>(p, blocks, st, mixed); break;
+    }
+}
+
+void launch_drift(const StepParams &p, cudaStream_t st)
+{
+    int blocks = (int)((p.n + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    if (p.xh4)
+        k_drift<true><<<blocks, 256, 0, st>>>(p);
+    else
+        k_drift<false><<<blocks, 256, 0, st>>>(p);
+}

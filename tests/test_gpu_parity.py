@@ -1,0 +1,348 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_05362_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+MIXED_FORCE_TOL = 1e-5      # rel-L2 of F per evaluation, mixed path
+FP64_FORCE_TOL = 1e-12      # rel-L2 of F, all-FP64 path
+BAND = 1e-6                 # bonds with |s - s0| < BAND * s0 may decide either way
+
+
+@pytest.fixture(scope="module")
+def pd():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2506_05362_gb300 import pd as _pd
+    _pd.lib()
+    return _pd
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def stretches(x, u, rp, col):
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    xi = x[col] - x[rows]
+    y = xi + (u[col] - u[rows])
+    L = np.linalg.norm(xi, axis=1)
+    return (np.linalg.norm(y, axis=1) - L) / L
+
+
+def small_kalthoff():
+    return S.kalthoff(length=0.02, height=0.04, thickness=0.005, notch_len=0.01, notch_width=1.5e-3,
+                      notch_gap=0.012, steps=40)
+
+
+def small_hollow():
+    return S.hollow(outer_cells=14, inner_cells=9, steps=40)
+
+
+SCENARIOS = {
+    "sphere": lambda: S.sphere(),
+    "kalthoff_small": small_kalthoff,
+    "hollow_small": small_hollow,
+    "aggregate_small": lambda: S.aggregate(n_grains=4, h=0.5e-3 / 5, gap_cells=0.3, seed=2),
+    "block_ragged": lambda: S.small_block(nx=7, ny=5, nz=3, jitter=0.2),
+}
+
+
+# --------------------------------------------------------------------------- lists
+@pytest.mark.parametrize("name", list(SCENARIOS))
+def test_bond_lists_bitexact(pd, name):
+    sc = SCENARIOS[name]()
+    ctx = pd.Context.from_scenario(sc, lanes=8)
+    rp, col = ctx.bonds()
+    kinds, params = S.filters_array(sc.filters)
+    orp, ocol = oracle.bonds(sc.x, sc.grain, sc.horizon, kinds, params)
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(col, ocol)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["kalthoff", "hollow"])
+def test_bond_lists_full_size(pd, name):
+    """Full-size plate (178,200 nodes, delta = 4h) and hollow sphere (343,846 nodes):
+    whole CSR against the oracle's cell-list build (itself pinned to brute force)."""
+    sc = S.BY_NAME[name]()
+    ctx = pd.Context.from_scenario(sc, lanes=16, contact=False)
+    rp, col = ctx.bonds()
+    kinds, params = S.filters_array(sc.filters)
+    orp, ocol = oracle.bonds(sc.x, sc.grain, sc.horizon, kinds, params, brute=False)
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(col, ocol)
+    # a few rows by brute force over all nodes
+    for i in [0, sc.n // 3, sc.n - 1]:
+        assert np.array_equal(col[rp[i]:rp[i + 1]], oracle.bond_row(sc.x, sc.grain, sc.horizon, i, kinds, params))
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- forces
+def perturbed_state(sc, rp, col, seed, strain=0.9, noise=0.5):
+    """Affine stretch of about `strain` s0 plus noise, so that some bonds break."""
+    K, c, s0, Kn = oracle.constants(sc.material.E, sc.material.G0, sc.horizon, sc.material.contact_factor)
+    rng = np.random.default_rng(seed)
+    A = np.diag([strain * s0, -0.3 * strain * s0, 0.5 * strain * s0]) + rng.normal(0, 0.2 * s0, (3, 3))
+    u = (sc.x - sc.x.mean(0)) @ A.T + rng.normal(0, noise * s0 * sc.h, sc.x.shape)
+    return u, s0
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_FORCE_TOL), ("fp64", FP64_FORCE_TOL)])
+@pytest.mark.parametrize("name", ["sphere", "kalthoff_small", "aggregate_small", "block_ragged"])
+@pytest.mark.parametrize("lanes", [4, 32])
+def test_forces_same_state(pd, name, precision, tol, lanes):
+    sc = SCENARIOS[name]()
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=lanes)
+    ref = oracle.Model.from_scenario(sc)
+    u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=1)
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    _, _, broken, _ = ctx.get_state()
+    ref.u = u.copy()
+    ref.forces()
+    s = stretches(sc.x, u, ref.rowptr, ref.col)
+    diff = broken.astype(bool) != ref.broken.astype(bool)
+    assert ref.broken.sum() > 0, "test state should break some bonds"
+    assert np.all(np.abs(s[diff] - s0) < BAND * s0), "broken sets differ outside the tolerance band"
+    # evaluate the oracle with the GPU's decisions on band bonds, then compare F
+    ref.broken[:] = broken
+    Fo = ref.forces(frozen=True).copy()
+    assert rel_l2(F, Fo) <= tol
+    ctx.close()
+
+
+def test_forces_full_size_sampled(pd):
+    """Full-size notched plate in the launch configuration the benchmark times:
+    forces at a perturbed state against the oracle (whole field; the oracle
+    evaluates 45 M bonds in a few seconds)."""
+    sc = S.kalthoff()
+    ctx = pd.Context.from_scenario(sc)
+    ref = oracle.Model.from_scenario(sc)
+    u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=3, strain=0.5, noise=0.2)
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    _, _, broken, _ = ctx.get_state()
+    ref.u = u.copy()
+    ref.forces()
+    s = stretches(sc.x, u, ref.rowptr, ref.col)
+    diff = broken.astype(bool) != ref.broken.astype(bool)
+    assert ref.broken.sum() > 0
+    assert np.all(np.abs(s[diff] - s0) < BAND * s0)
+    ref.broken[:] = broken
+    Fo = ref.forces(frozen=True)
+    assert rel_l2(F, Fo) <= MIXED_FORCE_TOL
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- trajectories
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-11)])
+def test_sphere_trajectory_200_steps(pd, precision, tol):
+    """Glass sphere between plates, 200 steps at 0.8 dt_crit: u, v, wall force."""
+    sc = S.sphere()
+    ctx = pd.Context.from_scenario(sc, precision=precision)
+    ref = oracle.Model.from_scenario(sc)
+    dtc = ref.stable_dt()
+    assert ctx.stable_dt() == pytest.approx(dtc, rel=1e-12)
+    dt = 0.8 * dtc
+    ref.init()
+    ctx.step(dt, sc.steps)
+    ref.step(dt, sc.steps)
+    u, v, broken, t = ctx.get_state()
+    assert rel_l2(u, ref.u) <= tol
+    assert rel_l2(v, ref.v) <= tol
+    assert t == pytest.approx(ref.t, rel=1e-14)
+    walls = ctx.get_walls()
+    assert np.allclose(walls, ref.wall_pos, rtol=0, atol=1e-18)
+    sig, wf = ctx.bulk_stress([sc.wall_area] * 2)
+    assert rel_l2(wf, ref.react) <= max(tol, 1e-9)
+    assert np.allclose(sig, ref.bulk_stress([sc.wall_area] * 2), rtol=max(tol, 1e-9))
+    ctx.close()
+
+
+def test_breaking_trajectory_block(pd):
+    """A block torn apart by opposing initial velocities: damage appears, and the
+    step-by-step comparison from a shared state holds through the damage."""
+    sc = S.small_block(nx=10, ny=6, nz=5, jitter=0.05)
+    sc.v0 = np.zeros_like(sc.x)
+    sc.v0[:, 0] = np.where(sc.x[:, 0] > sc.x[:, 0].mean(), 40.0, -40.0)
+    ctx = pd.Context.from_scenario(sc, lanes=16)
+    ref = oracle.Model.from_scenario(sc)
+    dt = 0.5 * ref.stable_dt()
+    ref.init()
+    for _ in range(30):
+        ctx.step(dt, 1)
+        ref.step(dt, 1)
+        u, v, broken, _ = ctx.get_state()
+        assert rel_l2(u, ref.u) < 1e-5
+        # resynchronise the oracle on the GPU's band decisions (chaos after damage)
+        s = stretches(sc.x, u, ref.rowptr, ref.col)
+        diff = broken.astype(bool) != ref.broken.astype(bool)
+        assert np.all(np.abs(s[diff] - ref.s0) < 1e-3 * ref.s0)
+        ref.broken[:] = broken
+    assert broken.sum() > 0
+    phi = ctx.damage()
+    assert np.allclose(phi, ref.damage(), atol=0)
+    ctx.close()
+
+
+def test_kalthoff_window(pd):
+    """Small notched plate: impact window of 40 steps, mixed path vs oracle."""
+    sc = small_kalthoff()
+    ctx = pd.Context.from_scenario(sc)
+    ref = oracle.Model.from_scenario(sc)
+    dt = 0.8 * ref.stable_dt()
+    ref.init()
+    ctx.step(dt, sc.steps)
+    ref.step(dt, sc.steps)
+    u, v, broken, _ = ctx.get_state()
+    assert rel_l2(u, ref.u) < 1e-5
+    assert rel_l2(v, ref.v) < 1e-5
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- contact
+def test_contact_pairs_bitexact(pd):
+    sc = S.aggregate(n_grains=3, h=0.5e-3 / 4, gap_cells=0.2, seed=3)
+    ctx = pd.Context.from_scenario(sc, lanes=8)
+    ref = oracle.Model.from_scenario(sc)
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-0.5, 0.5, (sc.n, 3)) * sc.h
+    ctx.set_state(u=u)
+    _, _, broken, _ = ctx.get_state()
+    ref.u = u.copy()
+    ref.broken[:] = broken
+    pairs = ctx.contacts()
+    opairs = ref.contact_pairs()
+    assert len(opairs) > 0
+    assert np.array_equal(pairs, opairs)
+    F = ctx.forces()
+    Fo = ref.forces(frozen=True)
+    assert rel_l2(F, Fo) < MIXED_FORCE_TOL
+
+
+def test_grain_collision_dynamics(pd):
+    """Two grains flying into each other: contact forces act across grains and the
+    trajectory follows the oracle (which rebuilds contacts every step)."""
+    sc = S.aggregate(n_grains=2, h=0.5e-3 / 4, gap_cells=0.5, seed=4)
+    c = sc.x[sc.grain == 0].mean(0) - sc.x[sc.grain == 1].mean(0)
+    c /= np.linalg.norm(c)
+    sc.v0 = np.where((sc.grain == 0)[:, None], -5.0 * c, 5.0 * c)
+    sc.walls = []
+    from scipy.spatial import cKDTree
+    gap = float(cKDTree(sc.x[sc.grain == 1]).query(sc.x[sc.grain == 0])[0].min())
+    ctx = pd.Context.from_scenario(sc)
+    ref = oracle.Model.from_scenario(sc)
+    dt = 0.5 * ref.stable_dt()
+    steps = int((gap - sc.material.contact_radius) / (10.0 * dt)) + 40
+    ref.init()
+    ctx.step(dt, steps)
+    ref.step(dt, steps)
+    u, v, broken, _ = ctx.get_state()
+    assert len(ref.contact_pairs()) > 0 or np.abs(ref.F).max() > 0
+    assert rel_l2(u, ref.u) < 1e-5
+    assert rel_l2(v, ref.v) < 1e-4
+
+
+# --------------------------------------------------------------------------- invariants
+def test_rigid_motion_zero_force_gpu(pd):
+    sc = S.small_block(nx=8, ny=6, nz=5, jitter=0.03)
+    ctx = pd.Context.from_scenario(sc, contact=False)
+    th = 0.4
+    R = np.array([[np.cos(th), 0, np.sin(th)], [0, 1, 0], [-np.sin(th), 0, np.cos(th)]])
+    u = sc.x @ R.T - sc.x + np.array([1e-3, 2e-3, -1e-3])
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    ref = oracle.Model.from_scenario(sc)
+    ref.u = 1e-3 * (sc.x - sc.x.mean(0))
+    scale = np.abs(ref.forces()).max()
+    assert np.abs(F).max() < 1e-5 * scale
+    ctx.close()
+
+
+def test_momentum_gpu(pd):
+    sc = S.aggregate(n_grains=3, h=0.5e-3 / 4, gap_cells=0.2, seed=5)
+    sc.walls = []
+    ctx = pd.Context.from_scenario(sc)
+    u = np.random.default_rng(2).uniform(-0.3, 0.3, sc.x.shape) * sc.h
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    FV = F * sc.vol[:, None]
+    assert np.abs(FV.sum(0)).max() < 1e-6 * np.abs(FV).sum()
+
+
+def test_determinism_and_checkpoint(pd):
+    sc = S.sphere()
+    a = pd.Context.from_scenario(sc, lanes=16)
+    b = pd.Context.from_scenario(sc, lanes=16)
+    dt = 0.8 * a.stable_dt()
+    a.step(dt, 100)
+    b.step(dt, 50)
+    st = b.get_state()
+    walls = b.get_walls()
+    c = pd.Context.from_scenario(sc, lanes=16)
+    c.set_walls(np.concatenate([S.walls_array(sc.walls)[:, :3], walls, S.walls_array(sc.walls)[:, 6:]], 1))
+    c.set_state(u=st[0], v=st[1], broken=st[2], t=st[3])
+    c.step(dt, 50)
+    b.step(dt, 50)
+    ua, va, ba, ta = a.get_state()
+    for other in (b, c):
+        uo, vo, bo, to = other.get_state()
+        assert np.array_equal(ua, uo) and np.array_equal(va, vo) and np.array_equal(ba, bo)
+        assert ta == to
+
+
+def test_damage_and_stable_dt_match(pd):
+    sc = S.small_block(nx=9, ny=7, nz=5, jitter=0.05)
+    ctx = pd.Context.from_scenario(sc, contact=False)
+    ref = oracle.Model.from_scenario(sc)
+    u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=9, strain=1.2)
+    ctx.set_state(u=u)
+    ref.u = u.copy()
+    ref.forces()
+    _, _, broken, _ = ctx.get_state()
+    ref.broken[:] = broken
+    assert np.array_equal(ctx.damage(), ref.damage())
+    assert ctx.stable_dt() == pytest.approx(ref.stable_dt(), rel=1e-12)
+
+
+# --------------------------------------------------------------------------- errors
+def test_error_paths(pd):
+    sc = S.small_block()
+    with pytest.raises(pd.PDError) as e:
+        pd.Context(sc.x, -sc.vol, sc.grain, sc.material)
+    ctx = pd.Context(sc.x, sc.vol, sc.grain, sc.material)
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(1e-9, 1)
+    assert e.value.status == pd.PD_ESTATE
+    ctx.build_bonds(sc.horizon)
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(-1.0, 1)
+    assert e.value.status == pd.PD_EINVAL
+    with pytest.raises(pd.PDError) as e:
+        ctx.build_bonds(sc.horizon, [(7, [0] * 12)])
+    assert e.value.status == pd.PD_EINVAL
+    with pytest.raises(pd.PDError) as e:
+        ctx.set_walls(np.array([[0, 0, 2.0, 0, 0, 0, 0, 0, 0]]))
+    assert e.value.status == pd.PD_EINVAL
+    with pytest.raises(pd.PDError) as e:
+        ctx.set_state(u=np.full((sc.n, 3), np.nan))
+    assert e.value.status == pd.PD_EINVAL
+    # a time step far beyond the stability limit blows up: non-finite state is
+    # detected on the device, the call restores the state and latches the error
+    ctx.build_bonds(sc.horizon)
+    u0 = np.random.default_rng(0).normal(0, 1e-5, sc.x.shape)
+    ctx.set_state(u=u0)
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(1e3 * ctx.stable_dt(), 400)
+    assert e.value.status in (pd.PD_ENONFINITE, pd.PD_EWALL)
+    u, _, _, _ = ctx.get_state()
+    assert np.array_equal(u, u0)
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(1e-9, 1)
+    assert e.value.status == pd.PD_ESTATE
+    ctx.set_state(u=u0)
+    ctx.step(0.5 * ctx.stable_dt(), 2)

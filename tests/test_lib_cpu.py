@@ -1,0 +1,51 @@
+"""Host-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every entry point that include/pd.h declares.  No compute calls."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pd_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2506_05362_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["pd_create", "pd_build_bonds", "pd_step", "pd_damage", "pd_bulk_stress",
+                     "pd_forces", "pd_get_state", "pd_set_state", "pd_mlp_forward", "pd_mlp_train_step"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_default_options_without_gpu(libpath):
+    from paper_2506_05362_gb300 import pd
+    o = pd.pd_default_options()
+    assert o.precision == pd.PD_MIXED and o.contact == 1 and o.graph_chunk == 64
+    assert o.lanes_per_node == 0 and not o.alloc
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle never includes or loads the CUDA sources and vice versa."""
+    csrc = os.path.join(ROOT, "paper_2506_05362_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "oracle" not in open(os.path.join(csrc, f)).read()
+    for f in ["pd_oracle.c", "__init__.py", "mlp.py"]:
+        txt = open(os.path.join(ROOT, "oracle", f)).read()
+        assert "paper_2506_05362_gb300" not in txt and "libpd" not in txt
