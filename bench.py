@@ -158,7 +158,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=50, help="0 skips the end-to-end leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -240,13 +241,16 @@ def main():
         pd.pd_get_state(ctx.h, n, B, u_h, v_h, b_h)
     barrier()
     e2e_s = time.perf_counter() - te
-    e2e = {"value": ws * n * args.e2e_steps / e2e_s, "unit": "node-steps/s",
-           "h2d_bytes_per_step": 48 * n + B, "d2h_bytes_per_step": 48 * n + B,
-           "steps": args.e2e_steps, "path": "pd_set_state + pd_step(dt,1) + pd_get_state, pinned host buffers"}
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e = {"value": ws * n * args.e2e_steps / e2e_s, "unit": "node-steps/s",
+               "h2d_bytes_per_step": 48 * n + B, "d2h_bytes_per_step": 48 * n + B,
+               "steps": args.e2e_steps,
+               "path": "pd_set_state + pd_step(dt,1) + pd_get_state, pinned host buffers"}
 
     # ---- all-FP64 GPU path on the same workload (comparison the metric asks for)
     fp64 = None
-    if args.precision == "mixed":
+    if args.precision == "mixed" and not args.no_fp64:
         c64 = pd.Context.from_scenario(sc, precision="fp64", device=local, stream=stream)
         c64.step(dt, args.warmup)
         k64 = min(args.steps, 400)

@@ -35,6 +35,9 @@ struct pd_ctx {
     int32_t *perm = nullptr, *inv = nullptr, *grain = nullptr;
     dbl4 *x4 = nullptr, *u[2] = {nullptr, nullptr}, *v = nullptr, *acc = nullptr, *F = nullptr;
     float4 *xh4 = nullptr, *xl4 = nullptr, *uh[2] = {nullptr, nullptr}, *ul[2] = {nullptr, nullptr};
+    float4 *vh = nullptr, *vl = nullptr, *af = nullptr;  // mixed path: v pairs, a
+    float4 *snap_vh = nullptr, *snap_vl = nullptr, *snap_af = nullptr, *snap_uh = nullptr, *snap_ul = nullptr;
+    bool own_stream = false;
     int cur = 0;
 
     int64_t *rowptr = nullptr, *crow = nullptr;
@@ -183,6 +186,19 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.ul_in = mixed ? c->ul[in] : nullptr;
     p.uh_out = mixed ? c->uh[in ^ 1] : nullptr;
     p.ul_out = mixed ? c->ul[in ^ 1] : nullptr;
+    p.vh = c->vh;
+    p.vl = c->vl;
+    p.af = c->af;
+    {
+        const float dth = (float)dt, hdth = (float)(0.5 * dt);
+        p.dt_hi = dth;
+        p.dt_lo = (float)(dt - (double)dth);
+        p.hdt_hi = hdth;
+        p.hdt_lo = (float)(0.5 * dt - (double)hdth);
+        p.inv_rho_f = (float)(1.0 / c->mat.rho);
+        for (int a = 0; a < 3; ++a) p.bf[a] = (float)c->b[a];
+        p.Rc_f = (float)c->mat.contact_radius;
+    }
     p.x4 = c->x4;
     p.u_in = c->u[in];
     p.u_out = c->u[in ^ 1];
@@ -216,17 +232,28 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     return p;
 }
 
+// FP64 displacement of buffer `in` (materialised into scratch on the mixed path).
+const dbl4 *upos(pd_ctx *c, int in)
+{
+    if (c->opt.precision == PD_MIXED) {
+        materialize_df(c->uh[in], c->ul[in], c->n, c->u[0], c->st);
+        return c->u[0];
+    }
+    return c->u[in];
+}
+
 // Contact candidate rebuild from u[in] (stream-ordered; capturable).
 void enqueue_rebuild(pd_ctx *c, int in)
 {
+    const dbl4 *u = upos(c, in);
     GridView g;
     for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];
     const double cut = c->mat.contact_radius + skin_of(c);
-    grid_build(g, c->x4, c->u[in], c->n, cut * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
+    grid_build(g, c->x4, u, c->n, cut * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
                c->gend, c->gcell, c->tmp, c->st);
-    cand_count(c->x4, c->u[in], c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_cnt, c->st);
+    cand_count(c->x4, u, c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_cnt, c->st);
     scan_exclusive_i64(c->cand_cnt, c->cand_ptr, c->n, c->tmp, c->st);
-    cand_fill(c->x4, c->u[in], c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_ptr, c->cand, c->cand_cap,
+    cand_fill(c->x4, u, c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_ptr, c->cand, c->cand_cap,
               c->derr, c->disp, c->stale, c->st);
 }
 
@@ -315,6 +342,7 @@ void pd_destroy(pd_ctx *c)
     if (c->ev1) cudaEventDestroy(c->ev1);
     std::vector<void *> own = c->owned;
     for (void *p : own) pd_dev_free(c, p);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
 
@@ -323,6 +351,10 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     const int64_t n = c->n;
     CK(cudaSetDevice(c->opt.device));
     c->st = (cudaStream_t)c->opt.stream;
+    if (!c->st) {  // the legacy default stream cannot be captured into graphs
+        CK(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     int32_t gmax = 0;
@@ -381,6 +413,14 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
             ALLOC(c->uh[q], float4, n);
             ALLOC(c->ul[q], float4, n);
         }
+        ALLOC(c->vh, float4, n);
+        ALLOC(c->vl, float4, n);
+        ALLOC(c->af, float4, n);
+        ALLOC(c->snap_uh, float4, n);
+        ALLOC(c->snap_ul, float4, n);
+        ALLOC(c->snap_vh, float4, n);
+        ALLOC(c->snap_vl, float4, n);
+        ALLOC(c->snap_af, float4, n);
     }
     gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, c->st);
     CK(cudaGetLastError());
@@ -393,6 +433,10 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     }
     CK(cudaMemsetAsync(c->acc, 0, sizeof(dbl4) * n, c->st));
     CK(cudaMemsetAsync(c->F, 0, sizeof(dbl4) * n, c->st));
+    if (mixed) {
+        split_df(c->v, n, c->vh, c->vl, c->st);
+        CK(cudaMemsetAsync(c->af, 0, sizeof(float4) * n, c->st));
+    }
     // grid and contact buffers
     uint32_t nb = 1024;
     while ((int64_t)nb < 2 * n && nb < (1u << 26)) nb <<= 1;
@@ -671,24 +715,25 @@ static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, G
 
 static pd_status snapshot(pd_ctx *c, bool restore)
 {
-    const size_t nb = sizeof(dbl4) * c->n;
-    if (!restore) {
-        CK(cudaMemcpyAsync(c->snap_u, c->u[c->cur], nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->snap_v, c->v, nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->snap_acc, c->acc, nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->snap_brk, c->brk, sizeof(uint32_t) * c->nwords, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 3,
-                           cudaMemcpyDeviceToDevice, c->st));
+    const size_t nb = sizeof(dbl4) * c->n, nf = sizeof(float4) * c->n;
+    const bool mixed = c->opt.precision == PD_MIXED;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(restore ? (void *)src : dst, restore ? dst : src, bytes, cudaMemcpyDeviceToDevice, c->st);
+    };
+    if (mixed) {
+        CK(cp(c->snap_uh, c->uh[c->cur], nf));
+        CK(cp(c->snap_ul, c->ul[c->cur], nf));
+        CK(cp(c->snap_vh, c->vh, nf));
+        CK(cp(c->snap_vl, c->vl, nf));
+        CK(cp(c->snap_af, c->af, nf));
     } else {
-        CK(cudaMemcpyAsync(c->u[c->cur], c->snap_u, nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->v, c->snap_v, nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->acc, c->snap_acc, nb, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->brk, c->snap_brk, sizeof(uint32_t) * c->nwords, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(c->wall_pos, c->dscratch + 4096, sizeof(double) * PD_MAX_WALLS * 3,
-                           cudaMemcpyDeviceToDevice, c->st));
-        if (c->opt.precision == PD_MIXED) split_hilo(c->u[c->cur], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
-        CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+        CK(cp(c->snap_u, c->u[c->cur], nb));
+        CK(cp(c->snap_v, c->v, nb));
+        CK(cp(c->snap_acc, c->acc, nb));
     }
+    CK(cp(c->snap_brk, c->brk, sizeof(uint32_t) * c->nwords));
+    CK(cp(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 3));
+    if (restore) CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
     return PD_OK;
 }
 
@@ -697,6 +742,7 @@ static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
     if (!c->opt.contact) { *k = 1 << 30; return PD_OK; }
     if (c->opt.contact_every > 0) { *k = c->opt.contact_every; return PD_OK; }
     int nb = vmax_blocks(c->n);
+    if (c->opt.precision == PD_MIXED) materialize_df(c->vh, c->vl, c->n, c->v, c->st);
     vmax(c->v, c->n, c->dscratch, c->st);
     std::vector<double> h(nb);
     CK(cudaMemcpyAsync(h.data(), c->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
@@ -924,7 +970,8 @@ pd_status pd_contacts(pd_ctx *c, int64_t *npairs, int32_t *ij)
     int64_t *cnt = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (n + 1));
     int64_t *off = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (n + 1));
     if (!cnt || !off) { pd_dev_free(c, cnt); pd_dev_free(c, off); return fail(c, PD_ENOMEM, "pd_contacts staging"); }
-    pairs_count(c->x4, c->u[c->cur], c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, cnt, c->st);
+    const dbl4 *upc = upos(c, c->cur);
+    pairs_count(c->x4, upc, c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, cnt, c->st);
     scan_exclusive_i64(cnt, off, n, c->tmp, c->st);
     int64_t total = 0;
     cudaMemcpyAsync(&total, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st);
@@ -937,7 +984,7 @@ pd_status pd_contacts(pd_ctx *c, int64_t *npairs, int32_t *ij)
             if (!out) {
                 s = fail(c, PD_ENOMEM, "pd_contacts output");
             } else {
-                pairs_fill(c->x4, c->u[c->cur], c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, off,
+                pairs_fill(c->x4, upc, c->perm, c->brk, c->cand_ptr, c->cand, n, c->mat.contact_radius, off,
                            out, c->st);
                 cudaMemcpyAsync(ij, out, sizeof(int32_t) * 2 * total, cudaMemcpyDeviceToHost, c->st);
                 s = sync(c);
@@ -974,12 +1021,14 @@ pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double 
     if (!c) return PD_EINVAL;
     CK(cudaSetDevice(c->opt.device));
     const size_t nb = sizeof(double) * 3 * c->n;
+    const bool mixed = c->opt.precision == PD_MIXED;
     if (u) {
-        to_caller(c->u[c->cur], c->perm, c->n, c->stage, c->st);
+        to_caller(upos(c, c->cur), c->perm, c->n, c->stage, c->st);
         CK(cudaMemcpyAsync(u, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
     }
     if (v) {
         if (u) { pd_status s = sync(c); if (s) return s; }
+        if (mixed) materialize_df(c->vh, c->vl, c->n, c->v, c->st);
         to_caller(c->v, c->perm, c->n, c->stage, c->st);
         CK(cudaMemcpyAsync(v, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
     }
@@ -1003,8 +1052,12 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
         for (int64_t q = 0; q < 3 * c->n; ++q)
             if (!isfinite(u[q])) return fail(c, PD_EINVAL, "u contains a non-finite value");
         CK(cudaMemcpyAsync(c->stage, u, nb, cudaMemcpyHostToDevice, c->st));
-        from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
-        if (c->opt.precision == PD_MIXED) split_hilo(c->u[c->cur], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+        if (c->opt.precision == PD_MIXED) {
+            from_caller(c->stage, c->perm, c->n, c->u[0], c->st);
+            split_df(c->u[0], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+        } else {
+            from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
+        }
         pd_status s = sync(c);
         if (s) return s;
     }
@@ -1013,6 +1066,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
             if (!isfinite(v[q])) return fail(c, PD_EINVAL, "v contains a non-finite value");
         CK(cudaMemcpyAsync(c->stage, v, nb, cudaMemcpyHostToDevice, c->st));
         from_caller(c->stage, c->perm, c->n, c->v, c->st);
+        if (c->opt.precision == PD_MIXED) split_df(c->v, c->n, c->vh, c->vl, c->st);
         pd_status s = sync(c);
         if (s) return s;
     }

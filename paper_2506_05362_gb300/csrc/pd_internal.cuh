@@ -43,11 +43,14 @@ struct StepParams {
     const int64_t *rowptr;
     const int32_t *col;
     uint32_t *brk;                 // broken bit per directed slot
-    // mixed-precision gather records
+    // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
     const float4 *xh4;             // (x_hi, V)
     const float4 *xl4;             // (x_lo, 0)
-    const float4 *uh_in, *ul_in;   // u split, current buffer
-    float4 *uh_out, *ul_out;       // u split, next buffer
+    const float4 *uh_in, *ul_in;   // u, current buffer
+    float4 *uh_out, *ul_out;       // u, next buffer
+    float4 *vh, *vl;               // v (in place)
+    float4 *af;                    // a = (F + b)/rho, stored for the next drift
+    float dt_hi, dt_lo, hdt_hi, hdt_lo, inv_rho_f, bf[3], Rc_f;
     // FP64 state
     const dbl4 *x4;             // (x, V)
     const dbl4 *u_in;           // u, current buffer
@@ -99,6 +102,9 @@ void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64
 // Step kernels (pd_step.cu)
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
 void launch_drift(const StepParams &p, cudaStream_t st);
+// double-float state <-> FP64 (mixed path)
+void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st);
+void split_df(const dbl4 *in, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
 int step_blocks(int lanes, int device);
 
 // Device memory handle with the caller's allocator.

@@ -23,6 +23,7 @@
 // The stretch uses the cancellation-free form
 //   s = eta . (2 xi + eta) / (|xi| (|xi + eta| + |xi|)),
 // which equals (|xi + eta| - |xi|)/|xi| exactly in real arithmetic.
+#include "pd_df.cuh"
 #include "pd_internal.cuh"
 
 namespace {
@@ -31,10 +32,6 @@ constexpr int STEP_THREADS = 256;
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
-
-struct F3 {
-    float x, y, z;
-};
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v)
@@ -76,6 +73,92 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
     return e;
 }
 
+// u of node i in FP64: the double-float state of the mixed path, or the FP64 array
+template <bool MIXED>
+__device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
+{
+    dbl4 r;
+    if (MIXED) {
+        const float4 h = p.uh_in[i], l = p.ul_in[i];
+        r.x = df_to_double(df{h.x, l.x});
+        r.y = df_to_double(df{h.y, l.y});
+        r.z = df_to_double(df{h.z, l.z});
+        r.w = 0.0;
+    } else {
+        r = p.u_in[i];
+    }
+    return r;
+}
+
+// Mixed-path epilogue: forces to acceleration in FP32, Verlet update of the
+// double-float state.  Wall forces are evaluated in FP64 only for nodes that an
+// FP32 pre-test places near a wall.
+__device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t row, float Fx, float Fy, float Fz,
+                                                   double *react, float &vmax2)
+{
+    unsigned err = 0;
+    if (p.walls.nw) {
+        const float4 oxh = p.xh4[row], ouh = p.uh_in[row];
+        const float px = oxh.x + ouh.x, py = oxh.y + ouh.y, pz = oxh.z + ouh.z;
+        bool near = false;
+        for (int l = 0; l < p.walls.nw; ++l) {
+            const double *w = p.wall_pos + 3 * l;
+            const float wx = (float)w[0], wy = (float)w[1], wz = (float)w[2];
+            const float d = (px - wx) * (float)p.walls.n[l][0] + (py - wy) * (float)p.walls.n[l][1] +
+                            (pz - wz) * (float)p.walls.n[l][2];
+            const float margin = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(wx) + fabsf(wy) + fabsf(wz));
+            near |= d < p.Rc_f + margin;
+        }
+        if (near) {
+            const dbl4 ox = p.x4[row];
+            const dbl4 ou = load_u_t<true>(p, row);
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, fx, fy, fz, react);
+            Fx += (float)fx; Fy += (float)fy; Fz += (float)fz;
+        }
+    }
+    if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
+    float4 a;
+    a.x = (Fx + p.bf[0]) * p.inv_rho_f;
+    a.y = (Fy + p.bf[1]) * p.inv_rho_f;
+    a.z = (Fz + p.bf[2]) * p.inv_rho_f;
+    a.w = 0.f;
+    if (p.mode == MODE_FORCES) {
+        p.af[row] = a;
+        if (p.F_out) {
+            dbl4 f; f.x = Fx; f.y = Fy; f.z = Fz; f.w = 0.0;
+            p.F_out[row] = f;
+        }
+        return err;
+    }
+    const df hdt{p.hdt_hi, p.hdt_lo};
+    float4 vh = p.vh[row], vl = p.vl[row];
+    df vx{vh.x, vl.x}, vy{vh.y, vl.y}, vz{vh.z, vl.z};
+    vx = df_add(vx, df_mul_f(hdt, a.x));
+    vy = df_add(vy, df_mul_f(hdt, a.y));
+    vz = df_add(vz, df_mul_f(hdt, a.z));
+    if (p.mode == MODE_FULL) {
+        vx = df_add(vx, df_mul_f(hdt, a.x));
+        vy = df_add(vy, df_mul_f(hdt, a.y));
+        vz = df_add(vz, df_mul_f(hdt, a.z));
+        const df dt{p.dt_hi, p.dt_lo};
+        const float4 uh = p.uh_in[row], ul = p.ul_in[row];
+        const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
+        const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
+        const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
+        p.uh_out[row] = make_float4(ux.hi, uy.hi, uz.hi, 0.f);
+        p.ul_out[row] = make_float4(ux.lo, uy.lo, uz.lo, 0.f);
+        const float vv = vx.hi * vx.hi + vy.hi * vy.hi + vz.hi * vz.hi;
+        vmax2 = fmaxf(vmax2, vv);
+        if (!isfinite(vv) || !isfinite(ux.hi + uy.hi + uz.hi)) err |= PDE_NONFINITE;
+    } else {
+        p.af[row] = a;
+    }
+    p.vh[row] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
+    p.vl[row] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
+    return err;
+}
+
 template <int G, bool MIXED>
 __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
 {
@@ -98,7 +181,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
     __syncthreads();
     unsigned err = 0;
     double vmax2 = 0.0;
+    float vmax2f = 0.f;
     const double hdt = 0.5 * p.dt;
+#define load_u(P, I) load_u_t<MIXED>(P, I)
 
     for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
         const int64_t row = r0 + grp;
@@ -166,7 +251,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
         if (active && p.contact) {
             const int64_t c0 = p.cand_ptr[row], c1 = p.cand_ptr[row + 1];
             if (c1 > c0) {
-                const dbl4 ox = p.x4[row], ou = p.u_in[row];
+                const dbl4 ox = p.x4[row], ou = load_u(p, row);
                 const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
                 const int gi = p.grain[row];
                 const double R2 = dmul(p.Rc, p.Rc);
@@ -177,7 +262,7 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
                         const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
                         if (!((w >> (cj.y & 31)) & 1u)) continue;  // bond intact
                     }
-                    const dbl4 xj = p.x4[j], uj = p.u_in[j];
+                    const dbl4 xj = p.x4[j], uj = load_u(p, j);
                     const double dx = dadd(xj.x, uj.x) - pix;
                     const double dy = dadd(xj.y, uj.y) - piy;
                     const double dz = dadd(xj.z, uj.z) - piz;
@@ -205,8 +290,11 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
         }
         fdx = group_sum<G>(fdx); fdy = group_sum<G>(fdy); fdz = group_sum<G>(fdz);
         // ---- 4. walls and Verlet update (group leader)
-        if (active && gl == 0) {
-            double Fx = fdx + (double)fbx, Fy = fdy + (double)fby, Fz = fdz + (double)fbz;
+        if (MIXED && active && gl == 0) {
+            err |= epilogue_mixed(p, row, fbx + (float)fdx, fby + (float)fdy, fbz + (float)fdz, s_react[grp], vmax2f);
+        }
+        if (!MIXED && active && gl == 0) {
+            double Fx = fdx, Fy = fdy, Fz = fdz;
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
             if (p.walls.nw) {
                 err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, Fx, Fy,
@@ -239,15 +327,6 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
                     un.z = dadd(ou.z, dmul(p.dt, v.z));
                     un.w = 0.0;
                     p.u_out[row] = un;
-                    if (MIXED) {
-                        float4 h, lo;
-                        h.x = __double2float_rn(un.x); lo.x = __double2float_rn(un.x - (double)h.x);
-                        h.y = __double2float_rn(un.y); lo.y = __double2float_rn(un.y - (double)h.y);
-                        h.z = __double2float_rn(un.z); lo.z = __double2float_rn(un.z - (double)h.z);
-                        h.w = 0.f; lo.w = 0.f;
-                        p.uh_out[row] = h;
-                        p.ul_out[row] = lo;
-                    }
                     const double vv = v.x * v.x + v.y * v.y + v.z * v.z;
                     vmax2 = fmax(vmax2, vv);
                     if (!isfinite(vv) || !isfinite(un.x + un.y + un.z)) err |= PDE_NONFINITE;
@@ -256,8 +335,9 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
             }
         }
     }
+#undef load_u
     // ---- block epilogue: partials, last-block reduction
-    if (gl == 0) s_vmax[grp] = vmax2;
+    if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     double *part = p.partials + (int64_t)blockIdx.x * PART_STRIDE;
@@ -309,32 +389,62 @@ __global__ void k_drift(const StepParams p)
     const double hdt = 0.5 * p.dt;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        dbl4 v = p.v[i];
-        const dbl4 a = p.acc[i], u = p.u_in[i];
-        v.x = dadd(v.x, dmul(hdt, a.x));
-        v.y = dadd(v.y, dmul(hdt, a.y));
-        v.z = dadd(v.z, dmul(hdt, a.z));
-        dbl4 un;
-        un.x = dadd(u.x, dmul(p.dt, v.x));
-        un.y = dadd(u.y, dmul(p.dt, v.y));
-        un.z = dadd(u.z, dmul(p.dt, v.z));
-        un.w = 0.0;
-        p.v[i] = v;
-        p.u_out[i] = un;
         if (MIXED) {
-            float4 h, lo;
-            h.x = __double2float_rn(un.x); lo.x = __double2float_rn(un.x - (double)h.x);
-            h.y = __double2float_rn(un.y); lo.y = __double2float_rn(un.y - (double)h.y);
-            h.z = __double2float_rn(un.z); lo.z = __double2float_rn(un.z - (double)h.z);
-            h.w = 0.f; lo.w = 0.f;
-            p.uh_out[i] = h;
-            p.ul_out[i] = lo;
+            const float4 a = p.af[i], vh = p.vh[i], vl = p.vl[i], uh = p.uh_in[i], ul = p.ul_in[i];
+            const df h{p.hdt_hi, p.hdt_lo}, dt{p.dt_hi, p.dt_lo};
+            const df vx = df_add(df{vh.x, vl.x}, df_mul_f(h, a.x));
+            const df vy = df_add(df{vh.y, vl.y}, df_mul_f(h, a.y));
+            const df vz = df_add(df{vh.z, vl.z}, df_mul_f(h, a.z));
+            const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
+            const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
+            const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
+            p.vh[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
+            p.vl[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
+            p.uh_out[i] = make_float4(ux.hi, uy.hi, uz.hi, 0.f);
+            p.ul_out[i] = make_float4(ux.lo, uy.lo, uz.lo, 0.f);
+        } else {
+            dbl4 v = p.v[i];
+            const dbl4 a = p.acc[i], u = p.u_in[i];
+            v.x = dadd(v.x, dmul(hdt, a.x));
+            v.y = dadd(v.y, dmul(hdt, a.y));
+            v.z = dadd(v.z, dmul(hdt, a.z));
+            dbl4 un;
+            un.x = dadd(u.x, dmul(p.dt, v.x));
+            un.y = dadd(u.y, dmul(p.dt, v.y));
+            un.z = dadd(u.z, dmul(p.dt, v.z));
+            un.w = 0.0;
+            p.v[i] = v;
+            p.u_out[i] = un;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int l = 0; l < p.walls.nw; ++l)
             for (int q = 0; q < 3; ++q)
                 p.wall_pos[3 * l + q] = dadd(p.wall_pos[3 * l + q], dmul(p.dt, p.walls.v[l][q]));
+    }
+}
+
+// u (FP64) from the double-float state, for the rebuild kernels and queries
+__global__ void k_materialize(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n, dbl4 *out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 h = hi[i], l = lo[i];
+        dbl4 r;
+        r.x = df_to_double(df{h.x, l.x});
+        r.y = df_to_double(df{h.y, l.y});
+        r.z = df_to_double(df{h.z, l.z});
+        r.w = 0.0;
+        out[i] = r;
+    }
+}
+
+__global__ void k_split_df(const dbl4 *__restrict__ in, int64_t n, float4 *hi, float4 *lo)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const dbl4 a = in[i];
+        const df x = df_from_double(a.x), y = df_from_double(a.y), z = df_from_double(a.z);
+        hi[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
+        lo[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
     }
 }
 
@@ -373,6 +483,22 @@ void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st)
         case 16: launch_g<16>(p, blocks, st, mixed); break;
         default: launch_g<32>(p, blocks, st, mixed); break;
     }
+}
+
+static int small_grid(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st)
+{
+    k_materialize<<<small_grid(n), 256, 0, st>>>(hi, lo, n, out);
+}
+
+void split_df(const dbl4 *in, int64_t n, float4 *hi, float4 *lo, cudaStream_t st)
+{
+    k_split_df<<<small_grid(n), 256, 0, st>>>(in, n, hi, lo);
 }
 
 void launch_drift(const StepParams &p, cudaStream_t st)

@@ -310,8 +310,8 @@ class Context:
                                  m.break_mode)
         o = pd_default_options()
         o.device = device
-        if stream is None:
-            stream = torch.cuda.current_stream(device)
+        if stream is None:  # a stream of its own: graphs cannot capture the legacy stream
+            stream = torch.cuda.Stream(device)
         self.stream = stream
         o.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self._alloc = None
@@ -395,6 +395,86 @@ class Context:
     def close(self):
         if self.h:
             pd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- surrogate MLP
+def pd_mlp_create(dims, seed=0, device=0, stream=None):
+    d = (ctypes.c_int * len(dims))(*dims)
+    h = P()
+    st = lib().pd_mlp_create(d, len(dims) - 1, ctypes.c_uint64(seed), device, stream, ctypes.byref(h))
+    if st != PD_OK:
+        raise PDError(st, "pd_mlp_create failed")
+    return h
+
+
+def _mcheck(status, h):
+    if status != PD_OK:
+        raise PDError(status, lib().pd_mlp_last_error(h).decode() if h else "")
+
+
+class MLP:
+    """Bulk-stress surrogate network (BF16 tensor-core forward/backward, Adam)."""
+
+    def __init__(self, dims=(109, 256, 256, 256, 256, 6), seed=0, device=0, stream=None):
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.dims = tuple(dims)
+        self.h = pd_mlp_create(self.dims, seed, device, stream)
+        n = ctypes.c_int64()
+        _mcheck(lib().pd_mlp_num_params(self.h, ctypes.byref(n)), self.h)
+        self.nparams = n.value
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, self.dims[0])
+        Y = np.zeros((X.shape[0], self.dims[-1]), np.float32)
+        _mcheck(lib().pd_mlp_forward(self.h, _ptr(X), X.shape[0], _ptr(Y)), self.h)
+        return Y
+
+    def forward_device(self, X, Y):
+        """X, Y: torch CUDA float32 tensors (contiguous)."""
+        _mcheck(lib().pd_mlp_forward_device(self.h, P(X.data_ptr()), X.shape[0], P(Y.data_ptr())), self.h)
+
+    def grad(self, X, T):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, self.dims[0])
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, self.dims[-1])
+        g = np.zeros(self.nparams, np.float32)
+        loss = ctypes.c_float()
+        _mcheck(lib().pd_mlp_grad(self.h, _ptr(X), _ptr(T), X.shape[0], _ptr(g), ctypes.byref(loss)), self.h)
+        return float(loss.value), g
+
+    def train_step(self, X, T, lr):
+        X = np.ascontiguousarray(X, np.float32).reshape(-1, self.dims[0])
+        T = np.ascontiguousarray(T, np.float32).reshape(-1, self.dims[-1])
+        loss = ctypes.c_float()
+        _mcheck(lib().pd_mlp_train_step(self.h, _ptr(X), _ptr(T), X.shape[0], ctypes.c_float(lr),
+                                        ctypes.byref(loss)), self.h)
+        return float(loss.value)
+
+    def train_step_device(self, X, T, lr, loss_dev=None):
+        lp = P(loss_dev.data_ptr()) if loss_dev is not None else None
+        _mcheck(lib().pd_mlp_train_step_device(self.h, P(X.data_ptr()), P(T.data_ptr()), X.shape[0],
+                                               ctypes.c_float(lr), lp), self.h)
+
+    def get_params(self):
+        w = np.zeros(self.nparams, np.float32)
+        _mcheck(lib().pd_mlp_get_params(self.h, _ptr(w)), self.h)
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        assert w.size == self.nparams
+        _mcheck(lib().pd_mlp_set_params(self.h, _ptr(w)), self.h)
+
+    def close(self):
+        if self.h:
+            lib().pd_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):

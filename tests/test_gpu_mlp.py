@@ -1,0 +1,112 @@
+"""Surrogate MLP on the GPU (BF16 tensor-core kernels) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (109, 256, 256, 256, 256, 6)
+# Tolerances derived from BF16 storage (unit roundoff 2^-9): each of the 5
+# layers adds at most about one rounding of the activations it consumes, and a
+# rounding decision can flip where FP32 and FP64 accumulation differ by one
+# FP32 ulp; the output then differs by O(5 * 2^-9 / sqrt(fan-in)) relative.
+FWD_TOL = 4e-3
+GRAD_TOL = 3e-2   # gradients also round dZ to BF16 at each layer
+
+
+@pytest.fixture(scope="module")
+def pd():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2506_05362_gb300 import pd as _pd
+    return _pd
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def inputs(batch, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(0, 1, (batch, DIMS[0])).astype(np.float32)
+    T = rng.normal(0, 1, (batch, DIMS[-1])).astype(np.float32)
+    return X, T
+
+
+def theta(seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(len(DIMS) - 1):
+        b = scale / np.sqrt(DIMS[i])
+        parts.append(rng.uniform(-b, b, DIMS[i + 1] * DIMS[i]))
+        parts.append(rng.uniform(-0.1, 0.1, DIMS[i + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+@pytest.mark.parametrize("batch", [1, 37, 128, 1003, 4096])
+def test_forward_matches_oracle(pd, batch):
+    net = pd.MLP(DIMS)
+    th = theta(1, scale=1.7)
+    net.set_params(th)
+    X, _ = inputs(batch, 2)
+    Y = net.forward(X)
+    ref = omlp.forward(th.astype(np.float64), X, DIMS, bf16=True)
+    assert rel_l2(Y, ref) < FWD_TOL
+    net.close()
+
+
+def test_forward_full_batch_sampled(pd):
+    """Inference batch 65536 in the benchmark's configuration; rows sampled for the oracle."""
+    net = pd.MLP(DIMS)
+    th = theta(3, scale=1.7)
+    net.set_params(th)
+    X, _ = inputs(65536, 4)
+    Y = net.forward(X)
+    idx = np.random.default_rng(5).choice(65536, 2000, replace=False)
+    ref = omlp.forward(th.astype(np.float64), X[idx], DIMS, bf16=True)
+    assert rel_l2(Y[idx], ref) < FWD_TOL
+    assert np.all(np.isfinite(Y))
+
+
+@pytest.mark.parametrize("batch", [64, 999, 4096])
+def test_gradient_matches_oracle(pd, batch):
+    net = pd.MLP(DIMS)
+    th = theta(6, scale=1.7)
+    net.set_params(th)
+    X, T = inputs(batch, 7)
+    loss, g = net.grad(X, T)
+    rl, rg = omlp.loss_and_grad(th.astype(np.float64), X, T, DIMS, bf16=True)
+    assert loss == pytest.approx(rl, rel=FWD_TOL)
+    assert rel_l2(g, rg) < GRAD_TOL
+    # per layer, so a wrong layer cannot hide behind the others
+    off = 0
+    for i in range(len(DIMS) - 1):
+        nW = DIMS[i + 1] * DIMS[i]
+        assert rel_l2(g[off:off + nW], rg[off:off + nW]) < GRAD_TOL
+        off += nW + DIMS[i + 1]
+
+
+def test_adam_update_matches_oracle(pd):
+    net = pd.MLP(DIMS)
+    th = theta(8)
+    net.set_params(th)
+    X, T = inputs(512, 9)
+    _, g = net.grad(X, T)
+    net.train_step(X, T, lr=1e-3)
+    opt = omlp.Adam(th.astype(np.float64), lr=1e-3)
+    opt.step(g.astype(np.float64))
+    assert np.allclose(net.get_params(), opt.theta, rtol=1e-5, atol=1e-7)
+
+
+def test_training_reduces_loss(pd):
+    """Fit a smooth map: the loss falls by an order of magnitude."""
+    net = pd.MLP(DIMS, seed=3)
+    rng = np.random.default_rng(10)
+    X = rng.normal(0, 1, (8192, DIMS[0])).astype(np.float32)
+    A = rng.normal(0, 0.2, (DIMS[0], DIMS[-1]))
+    T = np.tanh(X @ A).astype(np.float32)
+    first = net.train_step(X, T, 1e-3)
+    for _ in range(150):
+        last = net.train_step(X, T, 1e-3)
+    assert last < 0.1 * first
