@@ -422,7 +422,9 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
         ALLOC(c->snap_vl, float4, n);
         ALLOC(c->snap_af, float4, n);
     }
-    gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, c->st);
+    const double centre[3] = {0.5 * (c->lo[0] + c->hi[0]), 0.5 * (c->lo[1] + c->hi[1]), 0.5 * (c->lo[2] + c->hi[2])};
+    gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, centre,
+                 c->st);
     CK(cudaGetLastError());
     for (int q = 0; q < 2; ++q) {
         CK(cudaMemsetAsync(c->u[q], 0, sizeof(dbl4) * n, c->st));
@@ -434,7 +436,8 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     CK(cudaMemsetAsync(c->acc, 0, sizeof(dbl4) * n, c->st));
     CK(cudaMemsetAsync(c->F, 0, sizeof(dbl4) * n, c->st));
     if (mixed) {
-        split_df(c->v, n, c->vh, c->vl, c->st);
+        split_df(c->v, nullptr, n, c->vh, c->vl, c->st);
+        for (int q = 0; q < 2; ++q) split_df(c->u[q], c->xl4, n, c->uh[q], c->ul[q], c->st);
         CK(cudaMemsetAsync(c->af, 0, sizeof(float4) * n, c->st));
     }
     // grid and contact buffers
@@ -1054,7 +1057,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
         CK(cudaMemcpyAsync(c->stage, u, nb, cudaMemcpyHostToDevice, c->st));
         if (c->opt.precision == PD_MIXED) {
             from_caller(c->stage, c->perm, c->n, c->u[0], c->st);
-            split_df(c->u[0], c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+            split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], c->st);
         } else {
             from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
         }
@@ -1066,7 +1069,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
             if (!isfinite(v[q])) return fail(c, PD_EINVAL, "v contains a non-finite value");
         CK(cudaMemcpyAsync(c->stage, v, nb, cudaMemcpyHostToDevice, c->st));
         from_caller(c->stage, c->perm, c->n, c->v, c->st);
-        if (c->opt.precision == PD_MIXED) split_df(c->v, c->n, c->vh, c->vl, c->st);
+        if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, c->st);
         pd_status s = sync(c);
         if (s) return s;
     }

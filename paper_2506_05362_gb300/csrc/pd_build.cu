@@ -48,7 +48,8 @@ __global__ void k_grain_keys(const int32_t *__restrict__ grain, const uint32_t *
 __global__ void k_gather_nodes(const uint32_t *__restrict__ perm, int64_t n, const double *__restrict__ x,
                                const double *__restrict__ vol, const int32_t *__restrict__ grain,
                                const double *__restrict__ v0, int32_t *perm_out, int32_t *inv, dbl4 *x4,
-                               int32_t *grain_out, dbl4 *v, float4 *xh4, float4 *xl4)
+                               int32_t *grain_out, dbl4 *v, float4 *xh4, float4 *xl4, double cx, double cy,
+                               double cz)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[k];
@@ -62,10 +63,12 @@ __global__ void k_gather_nodes(const uint32_t *__restrict__ perm, int64_t n, con
         vv.x = v0 ? v0[3 * i] : 0.0; vv.y = v0 ? v0[3 * i + 1] : 0.0; vv.z = v0 ? v0[3 * i + 2] : 0.0; vv.w = 0.0;
         v[k] = vv;
         if (xh4) {
+            // split of x relative to the bounding-box centre (xi is translation invariant)
+            const double rx = a.x - cx, ry = a.y - cy, rz = a.z - cz;
             float4 h, l;
-            h.x = __double2float_rn(a.x); l.x = __double2float_rn(a.x - (double)h.x);
-            h.y = __double2float_rn(a.y); l.y = __double2float_rn(a.y - (double)h.y);
-            h.z = __double2float_rn(a.z); l.z = __double2float_rn(a.z - (double)h.z);
+            h.x = __double2float_rn(rx); l.x = __double2float_rn(rx - (double)h.x);
+            h.y = __double2float_rn(ry); l.y = __double2float_rn(ry - (double)h.y);
+            h.z = __double2float_rn(rz); l.z = __double2float_rn(rz - (double)h.z);
             h.w = (float)a.w; l.w = 0.f;
             xh4[k] = h;
             xl4[k] = l;
@@ -444,9 +447,10 @@ void build_morton(const double *x_dev, int64_t n, const double lo[3], const doub
 
 void gather_nodes(const uint32_t *order, int64_t n, const double *x, const double *vol, const int32_t *grain,
                   const double *v0, int32_t *perm, int32_t *inv, dbl4 *x4, int32_t *grain_out, dbl4 *v,
-                  float4 *xh4, float4 *xl4, cudaStream_t st)
+                  float4 *xh4, float4 *xl4, const double centre[3], cudaStream_t st)
 {
-    k_gather_nodes<<<grid_of(n), 256, 0, st>>>(order, n, x, vol, grain, v0, perm, inv, x4, grain_out, v, xh4, xl4);
+    k_gather_nodes<<<grid_of(n), 256, 0, st>>>(order, n, x, vol, grain, v0, perm, inv, x4, grain_out, v, xh4, xl4,
+                                               centre[0], centre[1], centre[2]);
 }
 
 void grid_build(GridView &g, const dbl4 *x4, const dbl4 *u4, int64_t n, double cs, uint32_t nbuckets,

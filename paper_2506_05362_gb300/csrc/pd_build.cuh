@@ -17,7 +17,7 @@ void build_morton(const double *x_dev, int64_t n, const double lo[3], const doub
                   int64_t *tmp, uint32_t **order_out, cudaStream_t st);
 void gather_nodes(const uint32_t *order, int64_t n, const double *x, const double *vol, const int32_t *grain,
                   const double *v0, int32_t *perm, int32_t *inv, dbl4 *x4, int32_t *grain_out, dbl4 *v,
-                  float4 *xh4, float4 *xl4, cudaStream_t st);
+                  float4 *xh4, float4 *xl4, const double centre[3], cudaStream_t st);
 void bonds_count(const dbl4 *x4, const int32_t *grain, const int32_t *perm, int64_t n, const GridView &g,
                  double delta, const FilterSet &f, int64_t *cnt, cudaStream_t st);
 void bonds_fill(const dbl4 *x4, const int32_t *grain, const int32_t *perm, int64_t n, const GridView &g,

@@ -44,9 +44,9 @@ struct StepParams {
     const int32_t *col;
     uint32_t *brk;                 // broken bit per directed slot
     // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
-    const float4 *xh4;             // (x_hi, V)
+    const float4 *xh4;             // (x_hi, V), x relative to the bounding-box centre
     const float4 *xl4;             // (x_lo, 0)
-    const float4 *uh_in, *ul_in;   // u, current buffer
+    const float4 *uh_in, *ul_in;   // (u_hi, packed x_lo.xy), (u_lo, packed x_lo.z); current buffer
     float4 *uh_out, *ul_out;       // u, next buffer
     float4 *vh, *vl;               // v (in place)
     float4 *af;                    // a = (F + b)/rho, stored for the next drift
@@ -104,7 +104,7 @@ void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
 void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float state <-> FP64 (mixed path)
 void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st);
-void split_df(const dbl4 *in, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
+void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
 int step_blocks(int lanes, int device);
 
 // Device memory handle with the caller's allocator.

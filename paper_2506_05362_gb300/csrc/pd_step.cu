@@ -23,6 +23,8 @@
 // The stretch uses the cancellation-free form
 //   s = eta . (2 xi + eta) / (|xi| (|xi + eta| + |xi|)),
 // which equals (|xi + eta| - |xi|)/|xi| exactly in real arithmetic.
+#include <cuda_bf16.h>
+
 #include "pd_df.cuh"
 #include "pd_internal.cuh"
 
@@ -71,6 +73,48 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
         react[3 * l + 2] -= mag * nz * vol;
     }
     return e;
+}
+
+// x_lo rides in the spare lanes of the u records as BF16: R1.w = (x_lo.x, x_lo.y),
+// R2.w = (x_lo.z, 0).  BF16 keeps 8 bits of x_lo, so x is known to 2^-32 |x|
+// (x is stored relative to the centre of the bounding box).
+__device__ __forceinline__ void xl_unpack(float w1, float w2, float *xl)
+{
+    const uint32_t a = __float_as_uint(w1), b = __float_as_uint(w2);
+    xl[0] = __uint_as_float(a << 16);
+    xl[1] = __uint_as_float(a & 0xffff0000u);
+    xl[2] = __uint_as_float(b << 16);
+}
+
+// One bond of the mixed path (Eq. pmb with the bond memory of Eq. peri-damage):
+// records o* of the row's node and a* of the neighbour.
+__device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const float4 &o0, const float4 &o1,
+                                           const float4 &o2, const float *ol, const float4 &a0, const float4 &a1,
+                                           const float4 &a2, float &fbx, float &fby, float &fbz)
+{
+    float al[3];
+    xl_unpack(a1.w, a2.w, al);
+    const float xx = (a0.x - o0.x) + (al[0] - ol[0]);
+    const float xy = (a0.y - o0.y) + (al[1] - ol[1]);
+    const float xz = (a0.z - o0.z) + (al[2] - ol[2]);
+    const float ex = (a1.x - o1.x) + (a2.x - o2.x);
+    const float ey = (a1.y - o1.y) + (a2.y - o2.y);
+    const float ez = (a1.z - o1.z) + (a2.z - o2.z);
+    const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
+    const float L2 = fmaf(xx, xx, fmaf(xy, xy, xz * xz));
+    const float y2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz));
+    const float num = fmaf(ex, xx + yx, fmaf(ey, xy + yy, ez * (xz + yz)));
+    const float rL = rsqrtf(L2), ry = rsqrtf(y2);
+    const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
+    const bool brk = p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f);
+    if (brk) {
+        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+    } else {
+        const float g = p.cf * a0.w * s * ry;
+        fbx = fmaf(g, yx, fbx);
+        fby = fmaf(g, yy, fby);
+        fbz = fmaf(g, yz, fbz);
+    }
 }
 
 // u of node i in FP64: the double-float state of the mixed path, or the FP64 array
@@ -146,8 +190,8 @@ __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t 
         const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
         const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
         const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
-        p.uh_out[row] = make_float4(ux.hi, uy.hi, uz.hi, 0.f);
-        p.ul_out[row] = make_float4(ux.lo, uy.lo, uz.lo, 0.f);
+        p.uh_out[row] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
+        p.ul_out[row] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
         const float vv = vx.hi * vx.hi + vy.hi * vy.hi + vz.hi * vz.hi;
         vmax2 = fmaxf(vmax2, vv);
         if (!isfinite(vv) || !isfinite(ux.hi + uy.hi + uz.hi)) err |= PDE_NONFINITE;
@@ -160,7 +204,7 @@ __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t 
 }
 
 template <int G, bool MIXED>
-__global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
+__global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const StepParams p)
 {
     constexpr int GPB = STEP_THREADS / G;
     __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
@@ -194,34 +238,20 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(const StepParams p)
         if (active) {
             const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
             if (MIXED) {
-                const float4 oxh = p.xh4[row], oxl = p.xl4[row], ouh = p.uh_in[row], oul = p.ul_in[row];
-                for (int64_t k = k0 + gl; k < k1; k += G) {
-                    const uint32_t w = p.brk[k >> 5];
-                    if ((w >> (k & 31)) & 1u) continue;
-                    const int j = __ldg(p.col + k);
-                    const float4 a = __ldg(p.xh4 + j), b = __ldg(p.xl4 + j);
-                    const float4 c = __ldg(p.uh_in + j), d = __ldg(p.ul_in + j);
-                    const float xx = (a.x - oxh.x) + (b.x - oxl.x);
-                    const float xy = (a.y - oxh.y) + (b.y - oxl.y);
-                    const float xz = (a.z - oxh.z) + (b.z - oxl.z);
-                    const float ex = (c.x - ouh.x) + (d.x - oul.x);
-                    const float ey = (c.y - ouh.y) + (d.y - oul.y);
-                    const float ez = (c.z - ouh.z) + (d.z - oul.z);
-                    const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
-                    const float L2 = fmaf(xx, xx, fmaf(xy, xy, xz * xz));
-                    const float y2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz));
-                    const float num = fmaf(ex, xx + yx, fmaf(ey, xy + yy, ez * (xz + yz)));
-                    const float rL = rsqrtf(L2), ry = rsqrtf(y2);
-                    const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
-                    const bool brk = p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f);
-                    if (brk) {
-                        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
-                    } else {
-                        const float g = p.cf * a.w * s * ry;
-                        fbx = fmaf(g, yx, fbx);
-                        fby = fmaf(g, yy, fby);
-                        fbz = fmaf(g, yz, fbz);
-                    }
+                const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
+                float ol[3];
+                xl_unpack(o1.w, o2.w, ol);
+                for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
+                    const int64_t kb = k + G;
+                    const bool hasb = kb < k1;
+                    const uint32_t wa = __ldg(p.brk + (k >> 5));
+                    const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
+                    const int ja = __ldg(p.col + k);
+                    const int jb = hasb ? __ldg(p.col + kb) : ja;
+                    const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
+                    const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
+                    if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                    if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
                 }
             } else {
                 const dbl4 ox = p.x4[row], ou = p.u_in[row];
@@ -400,8 +430,8 @@ __global__ void k_drift(const StepParams p)
             const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
             p.vh[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
             p.vl[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
-            p.uh_out[i] = make_float4(ux.hi, uy.hi, uz.hi, 0.f);
-            p.ul_out[i] = make_float4(ux.lo, uy.lo, uz.lo, 0.f);
+            p.uh_out[i] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
+            p.ul_out[i] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
         } else {
             dbl4 v = p.v[i];
             const dbl4 a = p.acc[i], u = p.u_in[i];
@@ -438,13 +468,25 @@ __global__ void k_materialize(const float4 *__restrict__ hi, const float4 *__res
     }
 }
 
-__global__ void k_split_df(const dbl4 *__restrict__ in, int64_t n, float4 *hi, float4 *lo)
+// double -> double-float; with xl (the static x_lo) the spare lanes get the packed
+// x_lo of the u records
+__global__ void k_split_df(const dbl4 *__restrict__ in, const float4 *__restrict__ xl, int64_t n, float4 *hi,
+                           float4 *lo)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const dbl4 a = in[i];
         const df x = df_from_double(a.x), y = df_from_double(a.y), z = df_from_double(a.z);
-        hi[i] = make_float4(x.hi, y.hi, z.hi, 0.f);
-        lo[i] = make_float4(x.lo, y.lo, z.lo, 0.f);
+        float w1 = 0.f, w2 = 0.f;
+        if (xl) {
+            const float4 q = xl[i];
+            const uint32_t bx = __bfloat16_as_ushort(__float2bfloat16_rn(q.x));
+            const uint32_t by = __bfloat16_as_ushort(__float2bfloat16_rn(q.y));
+            const uint32_t bz = __bfloat16_as_ushort(__float2bfloat16_rn(q.z));
+            w1 = __uint_as_float(bx | (by << 16));
+            w2 = __uint_as_float(bz);
+        }
+        hi[i] = make_float4(x.hi, y.hi, z.hi, w1);
+        lo[i] = make_float4(x.lo, y.lo, z.lo, w2);
     }
 }
 
@@ -496,9 +538,9 @@ void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cu
     k_materialize<<<small_grid(n), 256, 0, st>>>(hi, lo, n, out);
 }
 
-void split_df(const dbl4 *in, int64_t n, float4 *hi, float4 *lo, cudaStream_t st)
+void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, cudaStream_t st)
 {
-    k_split_df<<<small_grid(n), 256, 0, st>>>(in, n, hi, lo);
+    k_split_df<<<small_grid(n), 256, 0, st>>>(in, xl, n, hi, lo);
 }
 
 void launch_drift(const StepParams &p, cudaStream_t st)
