@@ -84,6 +84,8 @@ typedef struct {
     double skin;                         /* Verlet skin of the contact list, m; 0 = 0.5 R_c */
     int lanes_per_node;                  /* lanes sharing one node's bonds: 4, 8, 16, 32; 0 = autotune */
     int graph_chunk;                     /* steps per captured CUDA graph; 0 = 64 */
+    int tiles;                           /* mixed path: shared-memory tiles 1 = on, -1 = off,
+                                            0 = chosen by the autotuner (on when lanes are fixed) */
 } pd_options;
 
 /* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */
@@ -107,7 +109,8 @@ typedef struct {
 } pd_bond_filter;
 
 /* Fills *opt with defaults: device 0, default stream, cudaMalloc, PD_MIXED,
- * contact on, automatic rebuild period and skin, autotuned lanes, chunk 64. */
+ * contact on, automatic rebuild period and skin, autotuned lanes and tiles,
+ * chunk 64. */
 void pd_default_options(pd_options *opt);
 
 /* Creates a context for n nodes (Sec. 2.1: nodes x with volumes, grouped in

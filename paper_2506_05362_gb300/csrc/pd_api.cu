@@ -60,6 +60,13 @@ struct pd_ctx {
     int *stale = nullptr;
     int blocks = 0, lanes = 0, blocks_cap = 0;
     double tune_ms[4] = {0, 0, 0, 0};
+    // shared-memory tiles of the mixed path
+    int64_t *tile_ptr = nullptr;
+    int32_t *ulist = nullptr;
+    uint16_t *lcol = nullptr, *lrow = nullptr;
+    int64_t ntiles = 0;
+    int tile_rows = 64, tile_cap = 0;
+    bool tiled = false;
 
     WallSet walls;
     double b[3] = {0, 0, 0};
@@ -229,6 +236,15 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.disp = c->disp;
     p.skin = skin_of(c);
     p.stale = c->stale;
+    if (mixed && c->tiled) {
+        p.tile_cap = c->tile_cap;
+        p.tile_rows = c->tile_rows;
+        p.ntiles = c->ntiles;
+        p.tile_ptr = c->tile_ptr;
+        p.ulist = c->ulist;
+        p.lcol = c->lcol;
+        p.lrow = c->lrow;
+    }
     return p;
 }
 
@@ -457,8 +473,8 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     c->cand_cap = std::max<int64_t>(1024, 8 * n);
     ALLOC(c->cand, int2, c->cand_cap);
     // reductions
-    c->blocks_cap = step_blocks(4, c->opt.device);
-    for (int g : {8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device));
+    c->blocks_cap = 0;
+    for (int g : {4, 8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device, mixed, false, 0));
     ALLOC(c->partials, double, (int64_t)c->blocks_cap * PART_STRIDE);
     ALLOC(c->react, double, PD_MAX_WALLS * 3);
     ALLOC(c->disp, double, 1);
@@ -478,7 +494,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->snap_acc, dbl4, n);
     c->walls.nw = 0;
     c->lanes = c->opt.lanes_per_node ? c->opt.lanes_per_node : 16;
-    c->blocks = step_blocks(c->lanes, c->opt.device);
+    c->blocks = step_blocks(c->lanes, c->opt.device, mixed, false, 0);
     pd_status s = sync(c);
     if (s) return s;
     release(c, dx); release(c, dvol); release(c, dgrain); release(c, dv0);
@@ -502,6 +518,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (c->opt.precision != PD_MIXED && c->opt.precision != PD_FP64) { delete c; return PD_EINVAL; }
     int l = c->opt.lanes_per_node;
     if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
+    if (c->opt.tiles < -1 || c->opt.tiles > 1) { delete c; return PD_EINVAL; }
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
     c->mat = *mat;
     c->n = n;
@@ -515,7 +532,44 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     return PD_OK;
 }
 
-static pd_status autotune(pd_ctx *c);
+static pd_status autotune(pd_ctx *c)
+{
+    // time a force evaluation (idempotent at a fixed state) for each lane count,
+    // with and without shared-memory tiles on the mixed path
+    const int cand[4] = {4, 8, 16, 32};
+    const bool mixed = c->opt.precision == PD_MIXED;
+    const bool can_tile = c->tiled;
+    const int tmin = (can_tile && c->opt.tiles == 1) ? 1 : 0;
+    double best = INFINITY;
+    int bestl = 16;
+    bool best_tiled = false;
+    if (c->opt.contact) enqueue_rebuild(c, c->cur);
+    for (int q = 0; q < 4; ++q) {
+        c->tune_ms[q] = 0;
+        for (int tl = tmin; tl < (can_tile ? 2 : 1); ++tl) {
+            const int l = cand[q];
+            c->tiled = tl == 1;
+            const int blocks = std::min(c->blocks_cap, step_blocks(l, c->opt.device, mixed, c->tiled, c->tile_cap));
+            StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
+            launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
+            CK(cudaEventRecord(c->ev0, c->st));
+            for (int r = 0; r < 5; ++r) launch_step(p, l, blocks, c->st);
+            CK(cudaEventRecord(c->ev1, c->st));
+            CK(cudaEventSynchronize(c->ev1));
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+            const double t = ms / 5.0;
+            if (c->tune_ms[q] == 0 || t < c->tune_ms[q]) c->tune_ms[q] = t;
+            if (t < best) { best = t; bestl = l; best_tiled = c->tiled; }
+        }
+    }
+    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    c->tiled = best_tiled;
+    c->lanes = bestl;
+    c->blocks = std::min(c->blocks_cap, step_blocks(bestl, c->opt.device, mixed, c->tiled, c->tile_cap));
+    clear_graphs(c);
+    return sync(c);
+}
 
 pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_filter *filt)
 {
@@ -581,6 +635,43 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
         row_len_caller(c->rowptr, c->inv, n, cnt, c->st);
         scan_exclusive_i64(cnt, c->crow, n, c->tmp, c->st);
     }
+    // shared-memory tiles (mixed path)
+    release(c, c->tile_ptr); release(c, c->ulist); release(c, c->lcol); release(c, c->lrow);
+    c->tiled = false;
+    if (c->opt.precision == PD_MIXED) {
+        const int64_t m = B + n;
+        c->ntiles = (n + c->tile_rows - 1) / c->tile_rows;
+        uint64_t *tk1, *tk2;
+        int64_t *flag, *pos, *ttmp;
+        int32_t *ufull;
+        ALLOC(tk1, uint64_t, m);
+        ALLOC(tk2, uint64_t, m);
+        ALLOC(flag, int64_t, m + 1);
+        ALLOC(pos, int64_t, m + 1);
+        ALLOC(ttmp, int64_t, std::max(radix_tmp_size(m), scan_tmp_size(m + 1) + 8));
+        ALLOC(ufull, int32_t, m);
+        ALLOC(c->tile_ptr, int64_t, c->ntiles + 1);
+        ALLOC(c->lcol, uint16_t, B + 1);
+        ALLOC(c->lrow, uint16_t, n);
+        // capacity: the largest list, at most what two blocks per SM can stage
+        const int cap_max = 2304;
+        build_tiles(c->rowptr, c->col, n, B, c->tile_rows, c->sh, cap_max, tk1, tk2, flag, pos, ttmp, ufull,
+                    c->tile_ptr, c->lcol, c->lrow, c->st);
+        std::vector<int64_t> tp(c->ntiles + 1);
+        CK(cudaMemcpyAsync(tp.data(), c->tile_ptr, sizeof(int64_t) * (c->ntiles + 1), cudaMemcpyDeviceToHost, c->st));
+        s = sync(c);
+        if (s) return s;
+        int64_t maxlen = 0;
+        for (int64_t t = 0; t < c->ntiles; ++t) maxlen = std::max(maxlen, tp[t + 1] - tp[t]);
+        const int64_t U = tp[c->ntiles];
+        ALLOC(c->ulist, int32_t, U);
+        CK(cudaMemcpyAsync(c->ulist, ufull, sizeof(int32_t) * U, cudaMemcpyDeviceToDevice, c->st));
+        c->tile_cap = (int)std::min<int64_t>(maxlen, cap_max);
+        s = sync(c);
+        if (s) return s;
+        release(c, tk1); release(c, tk2); release(c, flag); release(c, pos); release(c, ttmp); release(c, ufull);
+        c->tiled = c->tile_cap > 0 && c->opt.tiles >= 0;
+    }
     c->nwords = (B + 31) / 32 + 1;
     ALLOC(c->brk, uint32_t, c->nwords);
     ALLOC(c->snap_brk, uint32_t, c->nwords);
@@ -594,6 +685,9 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     if (c->opt.lanes_per_node == 0) {
         s = autotune(c);
         if (s) return s;
+    } else {
+        c->blocks = std::min(c->blocks_cap, step_blocks(c->lanes, c->opt.device, c->opt.precision == PD_MIXED,
+                                                        c->tiled, c->tile_cap));
     }
     return eval_forces(c);
 }
@@ -852,33 +946,6 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
     return fail(c, PD_ECAPACITY, "pd_step retried too often");
 }
 
-static pd_status autotune(pd_ctx *c)
-{
-    // time a force evaluation (idempotent at a fixed state) for each lane count
-    const int cand[4] = {4, 8, 16, 32};
-    double best = INFINITY;
-    int bestl = 16;
-    if (c->opt.contact) enqueue_rebuild(c, c->cur);
-    for (int q = 0; q < 4; ++q) {
-        const int l = cand[q];
-        const int blocks = step_blocks(l, c->opt.device);
-        StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
-        launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
-        CK(cudaEventRecord(c->ev0, c->st));
-        for (int r = 0; r < 5; ++r) launch_step(p, l, blocks, c->st);
-        CK(cudaEventRecord(c->ev1, c->st));
-        CK(cudaEventSynchronize(c->ev1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-        c->tune_ms[q] = ms / 5.0;
-        if (c->tune_ms[q] < best) { best = c->tune_ms[q]; bestl = l; }
-    }
-    CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
-    c->lanes = bestl;
-    c->blocks = step_blocks(bestl, c->opt.device);
-    clear_graphs(c);
-    return sync(c);
-}
 
 // ---- queries ----------------------------------------------------------------------
 pd_status pd_damage(pd_ctx *c, double *phi)

@@ -363,6 +363,63 @@ __global__ void k_bytes_to_bits(const uint8_t *__restrict__ in, const int32_t *_
     }
 }
 
+// ---- shared-memory tiles -----------------------------------------------------------
+// Tile t = rows [t*T, (t+1)*T).  Keys (t << sh | node) for every bond target and
+// for every row itself; sorted and de-duplicated they give the tile's node list.
+__global__ void k_tile_keys(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n, int T,
+                            int sh, uint64_t *keys)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t t = (uint64_t)(i / T) << sh;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) keys[k] = t | (uint64_t)(uint32_t)col[k];
+        keys[rowptr[n] + i] = t | (uint64_t)i;
+    }
+}
+
+__global__ void k_unique_flags(const uint64_t *__restrict__ keys, int64_t m, int64_t *flag)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x)
+        flag[q] = (q == 0 || keys[q] != keys[q - 1]) ? 1 : 0;
+}
+
+__global__ void k_unique_scatter(const uint64_t *__restrict__ keys, const int64_t *__restrict__ pos, int64_t m,
+                                 int sh, int64_t ntiles, int32_t *ulist, int64_t *tile_ptr)
+{
+    const uint64_t mask = (1ull << sh) - 1ull;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < m; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[q];
+        if (q == 0 || k != keys[q - 1]) ulist[pos[q]] = (int32_t)(k & mask);
+        if (q == 0 || (k >> sh) != (keys[q - 1] >> sh)) tile_ptr[k >> sh] = pos[q];
+        if (q == m - 1) tile_ptr[ntiles] = pos[m];
+    }
+}
+
+__device__ __forceinline__ int32_t lsearch(const int32_t *__restrict__ a, int32_t len, int32_t v)
+{
+    int32_t lo = 0, hi = len;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (a[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// tile-local index of every bond target and of every row (tiles above cap get 0xffff)
+__global__ void k_local_cols(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n, int T,
+                             const int32_t *__restrict__ ulist, const int64_t *__restrict__ tile_ptr, int cap,
+                             uint16_t *lcol, uint16_t *lrow)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / T;
+        const int64_t base = tile_ptr[t];
+        const int32_t len = (int32_t)(tile_ptr[t + 1] - base);
+        const bool fits = len <= cap;
+        lrow[i] = fits ? (uint16_t)lsearch(ulist + base, len, (int32_t)i) : 0xffffu;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            lcol[k] = fits ? (uint16_t)lsearch(ulist + base, len, col[k]) : 0xffffu;
+    }
+}
+
 // ---- state conversion -----------------------------------------------------------
 __global__ void k_to_caller(const dbl4 *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, double *out)
 {
@@ -587,4 +644,21 @@ int vmax_blocks(int64_t n)
 void vmax(const dbl4 *v, int64_t n, double *partial, cudaStream_t st)
 {
     k_vmax<<<vmax_blocks(n), 256, 0, st>>>(v, n, partial);
+}
+
+void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B, int T, int sh, int cap,
+                 uint64_t *keys, uint64_t *keys_alt, int64_t *flag, int64_t *pos, int64_t *tmp, int32_t *ulist,
+                 int64_t *tile_ptr, uint16_t *lcol, uint16_t *lrow, cudaStream_t st)
+{
+    const int64_t m = B + n;
+    const int64_t ntiles = (n + T - 1) / T;
+    int tbits = 1;
+    while (((int64_t)1 << tbits) <= ntiles) ++tbits;
+    k_tile_keys<<<grid_of(n, 128), 128, 0, st>>>(rowptr, col, n, T, sh, keys);
+    uint64_t *k = keys, *ka = keys_alt;
+    radix_sort_u64(&k, &ka, nullptr, nullptr, m, sh + tbits, tmp, st);
+    k_unique_flags<<<grid_of(m), 256, 0, st>>>(k, m, flag);
+    scan_exclusive_i64(flag, pos, m, tmp, st);
+    k_unique_scatter<<<grid_of(m), 256, 0, st>>>(k, pos, m, sh, ntiles, ulist, tile_ptr);
+    k_local_cols<<<grid_of(n, 128), 128, 0, st>>>(rowptr, col, n, T, ulist, tile_ptr, cap, lcol, lrow);
 }

@@ -50,3 +50,9 @@ void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cu
 void split_hilo(const dbl4 *u, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
 int vmax_blocks(int64_t n);
 void vmax(const dbl4 *v, int64_t n, double *partial, cudaStream_t st);
+// Shared-memory tiles of T consecutive rows: sorted unique node list per tile
+// (ulist, tile_ptr[ntiles+1]) and tile-local indices of bond targets (lcol) and
+// rows (lrow); 0xffff marks tiles whose list exceeds cap.  ulist must hold B + n.
+void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B, int T, int sh, int cap,
+                 uint64_t *keys, uint64_t *keys_alt, int64_t *flag, int64_t *pos, int64_t *tmp, int32_t *ulist,
+                 int64_t *tile_ptr, uint16_t *lcol, uint16_t *lrow, cudaStream_t st);

@@ -203,171 +203,181 @@ __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t 
     return err;
 }
 
+// Tile staging of the mixed path: the records of the nodes a tile touches.
+struct TileView {
+    const float4 *s0, *s1, *s2;  // shared copies of xh4, uh_in, ul_in for the tile's list
+    bool on;                     // false: gather from global memory
+};
+
+// Steps 1-4 for one row owned by a group of G lanes (all lanes call; inactive
+// groups pass active = false and still join the shuffles).
 template <int G, bool MIXED>
-__global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const StepParams p)
+__device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bool active, int gl, int lrow,
+                                            const TileView &tv, double *react, unsigned &err, float &vmax2f,
+                                            double &vmax2)
 {
-    constexpr int GPB = STEP_THREADS / G;
-    __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
-    __shared__ double s_vmax[GPB];
-    __shared__ unsigned s_err;
-    __shared__ bool s_last;
-
-    const int gl = threadIdx.x % G;
-    const int grp = threadIdx.x / G;
-    if (gl == 0) {
-        for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
-        s_vmax[grp] = 0.0;
-    }
-    if (threadIdx.x == 0) {
-        s_err = 0;
-        if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
-    }
-    __syncthreads();
-    unsigned err = 0;
-    double vmax2 = 0.0;
-    float vmax2f = 0.f;
-    const double hdt = 0.5 * p.dt;
 #define load_u(P, I) load_u_t<MIXED>(P, I)
-
-    for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
-        const int64_t row = r0 + grp;
-        const bool active = row < p.n;
-        // ---- 1. bonds
-        float fbx = 0.f, fby = 0.f, fbz = 0.f;
-        double fdx = 0.0, fdy = 0.0, fdz = 0.0;
-        if (active) {
-            const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
-            if (MIXED) {
-                const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
-                float ol[3];
-                xl_unpack(o1.w, o2.w, ol);
-                for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
-                    const int64_t kb = k + G;
-                    const bool hasb = kb < k1;
-                    const uint32_t wa = __ldg(p.brk + (k >> 5));
-                    const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
-                    const int ja = __ldg(p.col + k);
-                    const int jb = hasb ? __ldg(p.col + kb) : ja;
-                    const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
-                    const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
-                    if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                    if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
-                }
-            } else {
-                const dbl4 ox = p.x4[row], ou = p.u_in[row];
-                for (int64_t k = k0 + gl; k < k1; k += G) {
-                    const uint32_t w = p.brk[k >> 5];
-                    if ((w >> (k & 31)) & 1u) continue;
-                    const int j = __ldg(p.col + k);
-                    const dbl4 a = p.x4[j], c = p.u_in[j];
-                    const double xx = a.x - ox.x, xy = a.y - ox.y, xz = a.z - ox.z;
-                    const double ex = c.x - ou.x, ey = c.y - ou.y, ez = c.z - ou.z;
-                    const double yx = xx + ex, yy = xy + ey, yz = xz + ez;
-                    const double L = sqrt(xx * xx + xy * xy + xz * xz);
-                    const double l = sqrt(yx * yx + yy * yy + yz * yz);
-                    const double s = (l - L) / L;
-                    const bool brk = p.break_mode ? (fabs(s) > p.s0) : (s > p.s0);
-                    if (brk) {
-                        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
-                    } else {
-                        const double g = p.c * s * a.w / l;
-                        fdx += g * yx; fdy += g * yy; fdz += g * yz;
-                    }
+    // ---- 1. bonds
+    float fbx = 0.f, fby = 0.f, fbz = 0.f;
+    double fdx = 0.0, fdy = 0.0, fdz = 0.0;
+    if (active) {
+        const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
+        if (MIXED && tv.on) {
+            const float4 o0 = tv.s0[lrow], o1 = tv.s1[lrow], o2 = tv.s2[lrow];
+            float ol[3];
+            xl_unpack(o1.w, o2.w, ol);
+            for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
+                const int64_t kb = k + G;
+                const bool hasb = kb < k1;
+                const uint32_t wa = __ldg(p.brk + (k >> 5));
+                const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
+                const int la = __ldg(p.lcol + k);
+                const int lb = hasb ? __ldg(p.lcol + kb) : la;
+                const float4 a0 = tv.s0[la], a1 = tv.s1[la], a2 = tv.s2[la];
+                const float4 b0 = tv.s0[lb], b1 = tv.s1[lb], b2 = tv.s2[lb];
+                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+            }
+        } else if (MIXED) {
+            const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
+            float ol[3];
+            xl_unpack(o1.w, o2.w, ol);
+            for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
+                const int64_t kb = k + G;
+                const bool hasb = kb < k1;
+                const uint32_t wa = __ldg(p.brk + (k >> 5));
+                const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
+                const int ja = __ldg(p.col + k);
+                const int jb = hasb ? __ldg(p.col + kb) : ja;
+                const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
+                const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
+                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+            }
+        } else {
+            const dbl4 ox = p.x4[row], ou = p.u_in[row];
+            for (int64_t k = k0 + gl; k < k1; k += G) {
+                const uint32_t w = p.brk[k >> 5];
+                if ((w >> (k & 31)) & 1u) continue;
+                const int j = __ldg(p.col + k);
+                const dbl4 a = p.x4[j], c = p.u_in[j];
+                const double xx = a.x - ox.x, xy = a.y - ox.y, xz = a.z - ox.z;
+                const double ex = c.x - ou.x, ey = c.y - ou.y, ez = c.z - ou.z;
+                const double yx = xx + ex, yy = xy + ey, yz = xz + ez;
+                const double L = sqrt(xx * xx + xy * xy + xz * xz);
+                const double l = sqrt(yx * yx + yy * yy + yz * yz);
+                const double s = (l - L) / L;
+                const bool brk = p.break_mode ? (fabs(s) > p.s0) : (s > p.s0);
+                if (brk) {
+                    atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+                } else {
+                    const double g = p.c * s * a.w / l;
+                    fdx += g * yx; fdy += g * yy; fdz += g * yz;
                 }
             }
         }
-        __syncwarp();
-        // ---- 2. contact candidates (FP64, exact predicate)
-        if (active && p.contact) {
-            const int64_t c0 = p.cand_ptr[row], c1 = p.cand_ptr[row + 1];
-            if (c1 > c0) {
-                const dbl4 ox = p.x4[row], ou = load_u(p, row);
-                const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
-                const int gi = p.grain[row];
-                const double R2 = dmul(p.Rc, p.Rc);
-                for (int64_t q = c0 + gl; q < c1; q += G) {
-                    const int2 cj = p.cand[q];
-                    const int j = cj.x;
-                    if (cj.y >= 0) {
-                        const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
-                        if (!((w >> (cj.y & 31)) & 1u)) continue;  // bond intact
-                    }
-                    const dbl4 xj = p.x4[j], uj = load_u(p, j);
-                    const double dx = dadd(xj.x, uj.x) - pix;
-                    const double dy = dadd(xj.y, uj.y) - piy;
-                    const double dz = dadd(xj.z, uj.z) - piz;
-                    const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-                    if (!(d2 < R2)) continue;
-                    const double dn = sqrt(d2);
-                    if (dn == 0.0) continue;
-                    double mag;
-                    const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
-                    const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
-                    if (p.grain[j] != gi || L >= p.Rc) {
-                        mag = -p.Kn * (p.Rc - dn);
-                    } else {
-                        const double sr = (dn - L) / L;
-                        mag = p.c * (sr < 0.0 ? sr : 0.0);
-                    }
-                    const double gm = mag * xj.w / dn;
+    }
+    __syncwarp();
+    // ---- 2. contact candidates (FP64, exact predicate)
+    if (active && p.contact) {
+        const int64_t c0 = p.cand_ptr[row], c1 = p.cand_ptr[row + 1];
+        if (c1 > c0) {
+            const dbl4 ox = p.x4[row], ou = load_u(p, row);
+            const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
+            const int gi = p.grain[row];
+            const double R2 = dmul(p.Rc, p.Rc);
+            for (int64_t q = c0 + gl; q < c1; q += G) {
+                const int2 cj = p.cand[q];
+                const int j = cj.x;
+                if (cj.y >= 0) {
+                    const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
+                    if (!((w >> (cj.y & 31)) & 1u)) continue;  // bond intact
+                }
+                const dbl4 xj = p.x4[j], uj = load_u(p, j);
+                const double dx = dadd(xj.x, uj.x) - pix;
+                const double dy = dadd(xj.y, uj.y) - piy;
+                const double dz = dadd(xj.z, uj.z) - piz;
+                const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+                if (!(d2 < R2)) continue;
+                const double dn = sqrt(d2);
+                if (dn == 0.0) continue;
+                double mag;
+                const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
+                const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
+                if (p.grain[j] != gi || L >= p.Rc) {
+                    mag = -p.Kn * (p.Rc - dn);
+                } else {
+                    const double sr = (dn - L) / L;
+                    mag = p.c * (sr < 0.0 ? sr : 0.0);
+                }
+                const double gm = mag * xj.w / dn;
+                if (MIXED) {  // FP32 accumulators of the mixed path
+                    fbx += (float)(gm * dx); fby += (float)(gm * dy); fbz += (float)(gm * dz);
+                } else {
                     fdx += gm * dx; fdy += gm * dy; fdz += gm * dz;
                 }
             }
         }
-        // ---- 3. combine the group
-        if (MIXED) {
-            fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
-        }
+    }
+    // ---- 3. combine the group
+    if (MIXED) {
+        fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
+    } else {
         fdx = group_sum<G>(fdx); fdy = group_sum<G>(fdy); fdz = group_sum<G>(fdz);
-        // ---- 4. walls and Verlet update (group leader)
-        if (MIXED && active && gl == 0) {
-            err |= epilogue_mixed(p, row, fbx + (float)fdx, fby + (float)fdy, fbz + (float)fdz, s_react[grp], vmax2f);
-        }
-        if (!MIXED && active && gl == 0) {
-            double Fx = fdx, Fy = fdy, Fz = fdz;
-            const dbl4 ox = p.x4[row], ou = p.u_in[row];
-            if (p.walls.nw) {
-                err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, Fx, Fy,
-                                  Fz, s_react[grp]);
+    }
+    // ---- 4. walls and Verlet update (group leader)
+    if (MIXED && active && gl == 0) {
+        err |= epilogue_mixed(p, row, fbx, fby, fbz, react, vmax2f);
+    }
+    if (!MIXED && active && gl == 0) {
+        const double hdt = 0.5 * p.dt;
+        double Fx = fdx, Fy = fdy, Fz = fdz;
+        const dbl4 ox = p.x4[row], ou = p.u_in[row];
+        if (p.walls.nw) err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, Fx, Fy, Fz, react);
+        if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
+        dbl4 a;
+        a.x = __ddiv_rn(dadd(Fx, p.b[0]), p.rho);
+        a.y = __ddiv_rn(dadd(Fy, p.b[1]), p.rho);
+        a.z = __ddiv_rn(dadd(Fz, p.b[2]), p.rho);
+        a.w = 0.0;
+        if (p.mode != MODE_FULL) p.acc[row] = a;
+        if (p.mode == MODE_FORCES) {
+            if (p.F_out) {
+                dbl4 f; f.x = Fx; f.y = Fy; f.z = Fz; f.w = 0.0;
+                p.F_out[row] = f;
             }
-            if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
-            dbl4 a;
-            a.x = __ddiv_rn(dadd(Fx, p.b[0]), p.rho);
-            a.y = __ddiv_rn(dadd(Fy, p.b[1]), p.rho);
-            a.z = __ddiv_rn(dadd(Fz, p.b[2]), p.rho);
-            a.w = 0.0;
-            if (p.mode != MODE_FULL) p.acc[row] = a;
-            if (p.mode == MODE_FORCES) {
-                if (p.F_out) {
-                    dbl4 f; f.x = Fx; f.y = Fy; f.z = Fz; f.w = 0.0;
-                    p.F_out[row] = f;
-                }
-            } else {
-                dbl4 v = p.v[row];
+        } else {
+            dbl4 v = p.v[row];
+            v.x = dadd(v.x, dmul(hdt, a.x));
+            v.y = dadd(v.y, dmul(hdt, a.y));
+            v.z = dadd(v.z, dmul(hdt, a.z));
+            if (p.mode == MODE_FULL) {
                 v.x = dadd(v.x, dmul(hdt, a.x));
                 v.y = dadd(v.y, dmul(hdt, a.y));
                 v.z = dadd(v.z, dmul(hdt, a.z));
-                if (p.mode == MODE_FULL) {
-                    v.x = dadd(v.x, dmul(hdt, a.x));
-                    v.y = dadd(v.y, dmul(hdt, a.y));
-                    v.z = dadd(v.z, dmul(hdt, a.z));
-                    dbl4 un;
-                    un.x = dadd(ou.x, dmul(p.dt, v.x));
-                    un.y = dadd(ou.y, dmul(p.dt, v.y));
-                    un.z = dadd(ou.z, dmul(p.dt, v.z));
-                    un.w = 0.0;
-                    p.u_out[row] = un;
-                    const double vv = v.x * v.x + v.y * v.y + v.z * v.z;
-                    vmax2 = fmax(vmax2, vv);
-                    if (!isfinite(vv) || !isfinite(un.x + un.y + un.z)) err |= PDE_NONFINITE;
-                }
-                p.v[row] = v;
+                dbl4 un;
+                un.x = dadd(ou.x, dmul(p.dt, v.x));
+                un.y = dadd(ou.y, dmul(p.dt, v.y));
+                un.z = dadd(ou.z, dmul(p.dt, v.z));
+                un.w = 0.0;
+                p.u_out[row] = un;
+                const double vv = v.x * v.x + v.y * v.y + v.z * v.z;
+                vmax2 = fmax(vmax2, vv);
+                if (!isfinite(vv) || !isfinite(un.x + un.y + un.z)) err |= PDE_NONFINITE;
             }
+            p.v[row] = v;
         }
     }
 #undef load_u
-    // ---- block epilogue: partials, last-block reduction
-    if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
+}
+
+// Per-block partials (wall reactions, max |v|, errors) and the fixed-order
+// reduction by the last block to finish; the last block also advances the walls
+// and the skin bookkeeping.
+template <int GPB>
+__device__ __forceinline__ void block_finish(const StepParams &p, double (*s_react)[PD_MAX_WALLS * 3],
+                                             double *s_vmax, unsigned &s_err, bool &s_last, unsigned err)
+{
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     double *part = p.partials + (int64_t)blockIdx.x * PART_STRIDE;
@@ -410,6 +420,90 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const Step
         }
         *p.counter = 0u;
     }
+}
+
+// Rows in a grid-stride loop, neighbour records gathered from global memory
+// (FP64 path, and the mixed path without tiles).
+template <int G, bool MIXED>
+__global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const StepParams p)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
+    __shared__ double s_vmax[GPB];
+    __shared__ unsigned s_err;
+    __shared__ bool s_last;
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    if (gl == 0) {
+        for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
+    }
+    __syncthreads();
+    unsigned err = 0;
+    double vmax2 = 0.0;
+    float vmax2f = 0.f;
+    const TileView tv{nullptr, nullptr, nullptr, false};
+    for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
+        const int64_t row = r0 + grp;
+        process_row<G, MIXED>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
+    }
+    if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
+    block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
+}
+
+// Mixed path with shared-memory tiles: a block takes tile t (rows
+// [t T, (t+1) T)), copies the records of the tile's node list into shared
+// memory once, and every bond of the tile gathers from there through its
+// 16-bit tile-local index.  Tiles whose list exceeds the capacity gather from
+// global memory.
+template <int G>
+__global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams p)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    extern __shared__ float4 s_rec[];
+    __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
+    __shared__ double s_vmax[GPB];
+    __shared__ unsigned s_err;
+    __shared__ bool s_last;
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    if (gl == 0) {
+        for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        s_err = 0;
+        if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
+    }
+    __syncthreads();
+    unsigned err = 0;
+    double vmax2 = 0.0;
+    float vmax2f = 0.f;
+    TileView tv{s_rec, s_rec + p.tile_cap, s_rec + 2 * p.tile_cap, false};
+    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
+        const int64_t base = p.tile_ptr[t];
+        const int len = (int)(p.tile_ptr[t + 1] - base);
+        tv.on = len <= p.tile_cap;
+        if (tv.on) {
+            float4 *w0 = s_rec, *w1 = s_rec + p.tile_cap, *w2 = s_rec + 2 * p.tile_cap;
+            for (int q = threadIdx.x; q < len; q += STEP_THREADS) {
+                const int j = __ldg(p.ulist + base + q);
+                w0[q] = __ldg(p.xh4 + j);
+                w1[q] = __ldg(p.uh_in + j);
+                w2[q] = __ldg(p.ul_in + j);
+            }
+        }
+        __syncthreads();
+        for (int rr = grp; rr < p.tile_rows; rr += GPB) {
+            const int64_t row = t * p.tile_rows + rr;
+            const bool active = row < p.n;
+            const int lrow = (active && tv.on) ? (int)__ldg(p.lrow + row) : 0;
+            process_row<G, true>(p, row, active, gl, lrow, tv, s_react[grp], err, vmax2f, vmax2);
+        }
+        __syncthreads();
+    }
+    if (gl == 0) s_vmax[grp] = (double)vmax2f;
+    block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
 }
 
 // First half of a chunk's first step: v += dt/2 a; u^{n+1} = u^n + dt v; walls move.
@@ -493,27 +587,47 @@ __global__ void k_split_df(const dbl4 *__restrict__ in, const float4 *__restrict
 template <int G>
 void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 {
-    if (mixed)
+    if (mixed && p.tile_cap > 0) {
+        const size_t smem = (size_t)3 * p.tile_cap * sizeof(float4);
+        k_step_tiled<G><<<blocks, STEP_THREADS, smem, st>>>(p);
+    } else if (mixed) {
         k_step<G, true><<<blocks, STEP_THREADS, 0, st>>>(p);
-    else
+    } else {
         k_step<G, false><<<blocks, STEP_THREADS, 0, st>>>(p);
+    }
+}
+
+template <int G>
+int blocks_g(int sms, bool mixed, bool tiled, int tile_cap)
+{
+    int per = 0;
+    if (mixed && tiled) {
+        const size_t smem = (size_t)3 * tile_cap * sizeof(float4);
+        cudaFuncSetAttribute(k_step_tiled<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tiled<G>, STEP_THREADS, smem);
+    } else if (mixed) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, true>, STEP_THREADS, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, false>, STEP_THREADS, 0);
+    }
+    if (per < 1) per = 1;
+    return sms * per;
 }
 
 }  // namespace
 
-int step_blocks(int lanes, int device)
+// Grid of the step kernel: SMs x resident blocks per SM (persistent loops).
+int step_blocks(int lanes, int device, bool mixed, bool tiled, int tile_cap)
 {
-    int sms = 0, per = 0;
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    switch (lanes) {
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<4, true>, STEP_THREADS, 0); break;
-        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<8, true>, STEP_THREADS, 0); break;
-        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<16, true>, STEP_THREADS, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<32, true>, STEP_THREADS, 0); break;
-    }
-    if (per < 1) per = 1;
     if (sms < 1) sms = 1;
-    return sms * per;
+    switch (lanes) {
+        case 4: return blocks_g<4>(sms, mixed, tiled, tile_cap);
+        case 8: return blocks_g<8>(sms, mixed, tiled, tile_cap);
+        case 16: return blocks_g<16>(sms, mixed, tiled, tile_cap);
+        default: return blocks_g<32>(sms, mixed, tiled, tile_cap);
+    }
 }
 
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st)

