@@ -65,8 +65,10 @@ struct pd_ctx {
     int32_t *ulist = nullptr;
     uint16_t *lcol = nullptr, *lrow = nullptr;
     int64_t ntiles = 0;
-    int tile_rows = 64, tile_cap = 0;
+    int tile_rows = 64, tile_cap = 0, tile_slot_cap = 0;
+    size_t tile_smem = 0;
     bool tiled = false;
+    double centre[3] = {0, 0, 0};
 
     WallSet walls;
     double b[3] = {0, 0, 0};
@@ -236,8 +238,10 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.disp = c->disp;
     p.skin = skin_of(c);
     p.stale = c->stale;
+    for (int q = 0; q < 3; ++q) p.centre[q] = c->centre[q];
     if (mixed && c->tiled) {
         p.tile_cap = c->tile_cap;
+        p.tile_slot_cap = c->tile_slot_cap;
         p.tile_rows = c->tile_rows;
         p.ntiles = c->ntiles;
         p.tile_ptr = c->tile_ptr;
@@ -438,8 +442,8 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
         ALLOC(c->snap_vl, float4, n);
         ALLOC(c->snap_af, float4, n);
     }
-    const double centre[3] = {0.5 * (c->lo[0] + c->hi[0]), 0.5 * (c->lo[1] + c->hi[1]), 0.5 * (c->lo[2] + c->hi[2])};
-    gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, centre,
+    for (int q = 0; q < 3; ++q) c->centre[q] = 0.5 * (c->lo[q] + c->hi[q]);
+    gather_nodes(order, n, dx, dvol, dgrain, dv0, c->perm, c->inv, c->x4, c->grain, c->v, c->xh4, c->xl4, c->centre,
                  c->st);
     CK(cudaGetLastError());
     for (int q = 0; q < 2; ++q) {
@@ -549,7 +553,7 @@ static pd_status autotune(pd_ctx *c)
         for (int tl = tmin; tl < (can_tile ? 2 : 1); ++tl) {
             const int l = cand[q];
             c->tiled = tl == 1;
-            const int blocks = std::min(c->blocks_cap, step_blocks(l, c->opt.device, mixed, c->tiled, c->tile_cap));
+            const int blocks = std::min(c->blocks_cap, step_blocks(l, c->opt.device, mixed, c->tiled, c->tile_smem));
             StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
             launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
             CK(cudaEventRecord(c->ev0, c->st));
@@ -566,7 +570,7 @@ static pd_status autotune(pd_ctx *c)
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
     c->tiled = best_tiled;
     c->lanes = bestl;
-    c->blocks = std::min(c->blocks_cap, step_blocks(bestl, c->opt.device, mixed, c->tiled, c->tile_cap));
+    c->blocks = std::min(c->blocks_cap, step_blocks(bestl, c->opt.device, mixed, c->tiled, c->tile_smem));
     clear_graphs(c);
     return sync(c);
 }
@@ -635,12 +639,16 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
         row_len_caller(c->rowptr, c->inv, n, cnt, c->st);
         scan_exclusive_i64(cnt, c->crow, n, c->tmp, c->st);
     }
-    // shared-memory tiles (mixed path)
+    // shared-memory tiles (mixed path): the largest tile (64, 32 or 16 rows) whose
+    // staging fits two blocks per SM
     release(c, c->tile_ptr); release(c, c->ulist); release(c, c->lcol); release(c, c->lrow);
     c->tiled = false;
-    if (c->opt.precision == PD_MIXED) {
+    c->tile_cap = 0;
+    if (c->opt.precision == PD_MIXED && c->opt.tiles >= 0) {
         const int64_t m = B + n;
-        c->ntiles = (n + c->tile_rows - 1) / c->tile_rows;
+        const size_t smem_max = 110 * 1024;
+        std::vector<int64_t> rp(n + 1);
+        CK(cudaMemcpyAsync(rp.data(), c->rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost, c->st));
         uint64_t *tk1, *tk2;
         int64_t *flag, *pos, *ttmp;
         int32_t *ufull;
@@ -650,27 +658,49 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
         ALLOC(pos, int64_t, m + 1);
         ALLOC(ttmp, int64_t, std::max(radix_tmp_size(m), scan_tmp_size(m + 1) + 8));
         ALLOC(ufull, int32_t, m);
-        ALLOC(c->tile_ptr, int64_t, c->ntiles + 1);
-        ALLOC(c->lcol, uint16_t, B + 1);
+        ALLOC(c->lcol, uint16_t, B + 16);
         ALLOC(c->lrow, uint16_t, n);
-        // capacity: the largest list, at most what two blocks per SM can stage
-        const int cap_max = 2304;
-        build_tiles(c->rowptr, c->col, n, B, c->tile_rows, c->sh, cap_max, tk1, tk2, flag, pos, ttmp, ufull,
-                    c->tile_ptr, c->lcol, c->lrow, c->st);
-        std::vector<int64_t> tp(c->ntiles + 1);
-        CK(cudaMemcpyAsync(tp.data(), c->tile_ptr, sizeof(int64_t) * (c->ntiles + 1), cudaMemcpyDeviceToHost, c->st));
-        s = sync(c);
-        if (s) return s;
-        int64_t maxlen = 0;
-        for (int64_t t = 0; t < c->ntiles; ++t) maxlen = std::max(maxlen, tp[t + 1] - tp[t]);
-        const int64_t U = tp[c->ntiles];
-        ALLOC(c->ulist, int32_t, U);
-        CK(cudaMemcpyAsync(c->ulist, ufull, sizeof(int32_t) * U, cudaMemcpyDeviceToDevice, c->st));
-        c->tile_cap = (int)std::min<int64_t>(maxlen, cap_max);
-        s = sync(c);
-        if (s) return s;
+        for (int T : {64, 32, 16}) {
+            c->ntiles = (n + T - 1) / T;
+            release(c, c->tile_ptr);
+            ALLOC(c->tile_ptr, int64_t, c->ntiles + 1);
+            const int cap_max = 32767;
+            build_tiles(c->rowptr, c->col, n, B, T, c->sh, cap_max, tk1, tk2, flag, pos, ttmp, ufull, c->tile_ptr,
+                        c->lcol, c->lrow, c->st);
+            std::vector<int64_t> tp(c->ntiles + 1);
+            CK(cudaMemcpyAsync(tp.data(), c->tile_ptr, sizeof(int64_t) * (c->ntiles + 1), cudaMemcpyDeviceToHost,
+                               c->st));
+            s = sync(c);
+            if (s) return s;
+            // capacity: the 99th-percentile list length (larger tiles gather globally)
+            std::vector<int64_t> lens(c->ntiles);
+            int64_t slot_cap = 0;
+            for (int64_t t = 0; t < c->ntiles; ++t) {
+                lens[t] = tp[t + 1] - tp[t];
+                const int64_t r0 = t * T, r1 = std::min<int64_t>(n, r0 + T);
+                slot_cap = std::max(slot_cap, rp[r1] - rp[r0]);
+            }
+            std::vector<int64_t> sorted = lens;
+            std::sort(sorted.begin(), sorted.end());
+            const int64_t cap = sorted[(size_t)((sorted.size() - 1) * 0.99)];
+            const size_t smem = tiled_smem((int)cap, T, (int)slot_cap);
+            if (smem <= smem_max || T == 16) {
+                if (smem > smem_max) break;
+                c->tile_rows = T;
+                c->tile_cap = (int)cap;
+                c->tile_slot_cap = (int)slot_cap;
+                c->tile_smem = smem;
+                const int64_t U = tp[c->ntiles];
+                ALLOC(c->ulist, int32_t, U);
+                CK(cudaMemcpyAsync(c->ulist, ufull, sizeof(int32_t) * U, cudaMemcpyDeviceToDevice, c->st));
+                // local indices of tiles above the capacity are unused (global path)
+                s = sync(c);
+                if (s) return s;
+                c->tiled = true;
+                break;
+            }
+        }
         release(c, tk1); release(c, tk2); release(c, flag); release(c, pos); release(c, ttmp); release(c, ufull);
-        c->tiled = c->tile_cap > 0 && c->opt.tiles >= 0;
     }
     c->nwords = (B + 31) / 32 + 1;
     ALLOC(c->brk, uint32_t, c->nwords);
@@ -687,7 +717,7 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
         if (s) return s;
     } else {
         c->blocks = std::min(c->blocks_cap, step_blocks(c->lanes, c->opt.device, c->opt.precision == PD_MIXED,
-                                                        c->tiled, c->tile_cap));
+                                                        c->tiled, c->tile_smem));
     }
     return eval_forces(c);
 }
@@ -830,7 +860,10 @@ static pd_status snapshot(pd_ctx *c, bool restore)
     }
     CK(cp(c->snap_brk, c->brk, sizeof(uint32_t) * c->nwords));
     CK(cp(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 3));
-    if (restore) CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    if (restore) {
+        if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
+        CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    }
     return PD_OK;
 }
 
@@ -1145,6 +1178,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
         if (c->B) {
             CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
             bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
+            if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
         }
     }
     if (t) c->t = *t;

@@ -420,6 +420,13 @@ __global__ void k_local_cols(const int64_t *__restrict__ rowptr, const int32_t *
     }
 }
 
+// broken flag of every slot copied into bit 15 of its local index
+__global__ void k_sync_lcol_flags(const uint32_t *__restrict__ brk, int64_t B, uint16_t *lcol)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < B; k += (int64_t)gridDim.x * blockDim.x)
+        lcol[k] = (uint16_t)((lcol[k] & 0x7fffu) | (((brk[k >> 5] >> (k & 31)) & 1u) << 15));
+}
+
 // ---- state conversion -----------------------------------------------------------
 __global__ void k_to_caller(const dbl4 *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, double *out)
 {
@@ -661,4 +668,9 @@ void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B
     scan_exclusive_i64(flag, pos, m, tmp, st);
     k_unique_scatter<<<grid_of(m), 256, 0, st>>>(k, pos, m, sh, ntiles, ulist, tile_ptr);
     k_local_cols<<<grid_of(n, 128), 128, 0, st>>>(rowptr, col, n, T, ulist, tile_ptr, cap, lcol, lrow);
+}
+
+void sync_lcol_flags(const uint32_t *brk, int64_t B, uint16_t *lcol, cudaStream_t st)
+{
+    k_sync_lcol_flags<<<grid_of(B), 256, 0, st>>>(brk, B, lcol);
 }

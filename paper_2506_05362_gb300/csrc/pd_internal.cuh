@@ -80,11 +80,13 @@ struct StepParams {
     double skin;
     int *stale;                    // set when 2*disp >= skin
     // shared-memory tiles (mixed path; tile_cap = 0 disables)
-    int tile_cap, tile_rows;
+    int tile_cap, tile_rows, tile_slot_cap;
     int64_t ntiles;
+    double centre[3];              // origin of the split x (bounding-box centre)
     const int64_t *tile_ptr;
     const int32_t *ulist;
-    const uint16_t *lcol, *lrow;
+    uint16_t *lcol;                // bit 15 = broken (kept in step with brk)
+    const uint16_t *lrow;
 };
 
 #define PART_STRIDE 20  // 18 reaction components + max|v| + spare
@@ -111,7 +113,8 @@ void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float state <-> FP64 (mixed path)
 void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st);
 void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
-int step_blocks(int lanes, int device, bool mixed, bool tiled, int tile_cap);
+int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem);
+size_t tiled_smem(int tile_cap, int tile_rows, int slot_cap);
 
 // Device memory handle with the caller's allocator.
 struct pd_ctx;

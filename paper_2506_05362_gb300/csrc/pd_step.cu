@@ -88,6 +88,7 @@ __device__ __forceinline__ void xl_unpack(float w1, float w2, float *xl)
 
 // One bond of the mixed path (Eq. pmb with the bond memory of Eq. peri-damage):
 // records o* of the row's node and a* of the neighbour.
+template <bool FLAG = false>
 __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const float4 &o0, const float4 &o1,
                                            const float4 &o2, const float *ol, const float4 &a0, const float4 &a1,
                                            const float4 &a2, float &fbx, float &fby, float &fbz)
@@ -109,6 +110,8 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
     const bool brk = p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f);
     if (brk) {
         atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+        // the tiled path also carries the flag in bit 15 of the 16-bit local index
+        if (FLAG) atomicOr((unsigned int *)(p.lcol) + (k >> 1), 0x8000u << (16 * (int)(k & 1)));
     } else {
         const float g = p.cf * a0.w * s * ry;
         fbx = fmaf(g, yx, fbx);
@@ -138,26 +141,30 @@ __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
 // double-float state.  Wall forces are evaluated in FP64 only for nodes that an
 // FP32 pre-test places near a wall.
 __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t row, float Fx, float Fy, float Fz,
-                                                   double *react, float &vmax2)
+                                                   const float4 &oxh, const float4 &uh, const float4 &ul,
+                                                   const float4 &vh_in, const float4 &vl_in, double *react,
+                                                   float &vmax2)
 {
     unsigned err = 0;
     if (p.walls.nw) {
-        const float4 oxh = p.xh4[row], ouh = p.uh_in[row];
-        const float px = oxh.x + ouh.x, py = oxh.y + ouh.y, pz = oxh.z + ouh.z;
+        const float px = oxh.x + uh.x, py = oxh.y + uh.y, pz = oxh.z + uh.z;
+        const float cx = (float)p.centre[0], cy = (float)p.centre[1], cz = (float)p.centre[2];
         bool near = false;
         for (int l = 0; l < p.walls.nw; ++l) {
             const double *w = p.wall_pos + 3 * l;
-            const float wx = (float)w[0], wy = (float)w[1], wz = (float)w[2];
+            const float wx = (float)w[0] - cx, wy = (float)w[1] - cy, wz = (float)w[2] - cz;
             const float d = (px - wx) * (float)p.walls.n[l][0] + (py - wy) * (float)p.walls.n[l][1] +
                             (pz - wz) * (float)p.walls.n[l][2];
-            const float margin = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(wx) + fabsf(wy) + fabsf(wz));
+            const float margin = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(wx) + fabsf(wy) + fabsf(wz) +
+                                          fabsf(cx) + fabsf(cy) + fabsf(cz));
             near |= d < p.Rc_f + margin;
         }
         if (near) {
             const dbl4 ox = p.x4[row];
-            const dbl4 ou = load_u_t<true>(p, row);
+            const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
+                         uz = df_to_double(df{uh.z, ul.z});
             double fx = 0.0, fy = 0.0, fz = 0.0;
-            err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, fx, fy, fz, react);
+            err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, fx, fy, fz, react);
             Fx += (float)fx; Fy += (float)fy; Fz += (float)fz;
         }
     }
@@ -176,8 +183,7 @@ __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t 
         return err;
     }
     const df hdt{p.hdt_hi, p.hdt_lo};
-    float4 vh = p.vh[row], vl = p.vl[row];
-    df vx{vh.x, vl.x}, vy{vh.y, vl.y}, vz{vh.z, vl.z};
+    df vx{vh_in.x, vl_in.x}, vy{vh_in.y, vl_in.y}, vz{vh_in.z, vl_in.z};
     vx = df_add(vx, df_mul_f(hdt, a.x));
     vy = df_add(vy, df_mul_f(hdt, a.y));
     vz = df_add(vz, df_mul_f(hdt, a.z));
@@ -186,7 +192,6 @@ __device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t 
         vy = df_add(vy, df_mul_f(hdt, a.y));
         vz = df_add(vz, df_mul_f(hdt, a.z));
         const df dt{p.dt_hi, p.dt_lo};
-        const float4 uh = p.uh_in[row], ul = p.ul_in[row];
         const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
         const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
         const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
@@ -327,7 +332,8 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
     }
     // ---- 4. walls and Verlet update (group leader)
     if (MIXED && active && gl == 0) {
-        err |= epilogue_mixed(p, row, fbx, fby, fbz, react, vmax2f);
+        err |= epilogue_mixed(p, row, fbx, fby, fbz, __ldg(p.xh4 + row), __ldg(p.uh_in + row),
+                              __ldg(p.ul_in + row), p.vh[row], p.vl[row], react, vmax2f);
     }
     if (!MIXED && active && gl == 0) {
         const double hdt = 0.5 * p.dt;
@@ -453,11 +459,12 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const Step
     block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
 }
 
-// Mixed path with shared-memory tiles: a block takes tile t (rows
-// [t T, (t+1) T)), copies the records of the tile's node list into shared
-// memory once, and every bond of the tile gathers from there through its
-// 16-bit tile-local index.  Tiles whose list exceeds the capacity gather from
-// global memory.
+// Mixed path with shared-memory tiles.  A block takes tile t (rows
+// [t T, (t+1) T)) and stages in shared memory everything its rows read: row
+// pointers, the tile's slice of 16-bit local neighbour indices (bit 15 = broken),
+// the records of the tile's node list, and the rows' velocities.  The bond loop
+// then makes no global loads.  Tiles whose list exceeds the capacity take the
+// global-gather path of process_row.
 template <int G>
 __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams p)
 {
@@ -467,6 +474,11 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
     __shared__ double s_vmax[GPB];
     __shared__ unsigned s_err;
     __shared__ bool s_last;
+    const int T = p.tile_rows, cap = p.tile_cap;
+    float4 *r0s = s_rec, *r1s = r0s + cap, *r2s = r1s + cap, *vhs = r2s + cap, *vls = vhs + T;
+    int64_t *rps = (int64_t *)(vls + T), *cps = rps + T + 1;
+    uint16_t *lrs = (uint16_t *)(cps + T + 1);
+    uint16_t *lcs = lrs + ((T + 7) & ~7);
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
     if (gl == 0) {
         for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
@@ -479,26 +491,104 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
     unsigned err = 0;
     double vmax2 = 0.0;
     float vmax2f = 0.f;
-    TileView tv{s_rec, s_rec + p.tile_cap, s_rec + 2 * p.tile_cap, false};
+    const TileView off{nullptr, nullptr, nullptr, false};
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x) {
         const int64_t base = p.tile_ptr[t];
         const int len = (int)(p.tile_ptr[t + 1] - base);
-        tv.on = len <= p.tile_cap;
-        if (tv.on) {
-            float4 *w0 = s_rec, *w1 = s_rec + p.tile_cap, *w2 = s_rec + 2 * p.tile_cap;
+        const int64_t r0 = t * T;
+        const int rows = (int)min((int64_t)T, p.n - r0);
+        const bool on = len <= cap;
+        int64_t ka = 0;
+        if (on) {
+            const int64_t kbase = __ldg(p.rowptr + r0), kend = __ldg(p.rowptr + r0 + rows);
+            ka = kbase & ~(int64_t)7;  // 16-byte aligned start of the index slice
+            const int nch = (int)((kend - ka + 7) >> 3);
+            const uint4 *src = (const uint4 *)(p.lcol + ka);
+            for (int q = threadIdx.x; q < nch; q += STEP_THREADS) ((uint4 *)lcs)[q] = src[q];
+            for (int q = threadIdx.x; q <= rows; q += STEP_THREADS) {
+                rps[q] = __ldg(p.rowptr + r0 + q);
+                cps[q] = p.contact ? __ldg(p.cand_ptr + r0 + q) : 0;
+            }
+            for (int q = threadIdx.x; q < rows; q += STEP_THREADS) {
+                vhs[q] = p.vh[r0 + q];
+                vls[q] = p.vl[r0 + q];
+                lrs[q] = __ldg(p.lrow + r0 + q);
+            }
             for (int q = threadIdx.x; q < len; q += STEP_THREADS) {
                 const int j = __ldg(p.ulist + base + q);
-                w0[q] = __ldg(p.xh4 + j);
-                w1[q] = __ldg(p.uh_in + j);
-                w2[q] = __ldg(p.ul_in + j);
+                r0s[q] = __ldg(p.xh4 + j);
+                r1s[q] = __ldg(p.uh_in + j);
+                r2s[q] = __ldg(p.ul_in + j);
             }
         }
         __syncthreads();
-        for (int rr = grp; rr < p.tile_rows; rr += GPB) {
-            const int64_t row = t * p.tile_rows + rr;
-            const bool active = row < p.n;
-            const int lrow = (active && tv.on) ? (int)__ldg(p.lrow + row) : 0;
-            process_row<G, true>(p, row, active, gl, lrow, tv, s_react[grp], err, vmax2f, vmax2);
+        for (int rr = grp; rr < T; rr += GPB) {
+            const int64_t row = r0 + rr;
+            const bool active = rr < rows;
+            if (!on) {
+                process_row<G, true>(p, row, active, gl, 0, off, s_react[grp], err, vmax2f, vmax2);
+                continue;
+            }
+            float fbx = 0.f, fby = 0.f, fbz = 0.f;
+            float4 o0, o1, o2;
+            if (active) {
+                const int lr = lrs[rr];
+                o0 = r0s[lr]; o1 = r1s[lr]; o2 = r2s[lr];
+                float ol[3];
+                xl_unpack(o1.w, o2.w, ol);
+                const int64_t k0 = rps[rr], k1 = rps[rr + 1];
+                for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
+                    const int64_t kb = k + G;
+                    const uint32_t la = lcs[k - ka];
+                    const uint32_t lb = kb < k1 ? lcs[kb - ka] : 0x8000u;
+                    const uint32_t ia = la & 0x7fffu, ib = lb & 0x7fffu;
+                    const float4 a0 = r0s[ia], a1 = r1s[ia], a2 = r2s[ia];
+                    const float4 b0 = r0s[ib], b1 = r1s[ib], b2 = r2s[ib];
+                    if (!(la & 0x8000u)) bond_mixed<true>(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                    if (!(lb & 0x8000u)) bond_mixed<true>(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+                }
+            }
+            __syncwarp();
+            // contact candidates (rare; FP64 from global memory)
+            if (active && p.contact) {
+                const int64_t c0 = cps[rr], c1 = cps[rr + 1];
+                if (c1 > c0) {
+                    const dbl4 ox = p.x4[row], ou = load_u_t<true>(p, row);
+                    const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
+                    const int gi = p.grain[row];
+                    const double R2 = dmul(p.Rc, p.Rc);
+                    for (int64_t q = c0 + gl; q < c1; q += G) {
+                        const int2 cj = p.cand[q];
+                        const int j = cj.x;
+                        if (cj.y >= 0) {
+                            const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
+                            if (!((w >> (cj.y & 31)) & 1u)) continue;
+                        }
+                        const dbl4 xj = p.x4[j], uj = load_u_t<true>(p, j);
+                        const double dx = dadd(xj.x, uj.x) - pix;
+                        const double dy = dadd(xj.y, uj.y) - piy;
+                        const double dz = dadd(xj.z, uj.z) - piz;
+                        const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+                        if (!(d2 < R2)) continue;
+                        const double dn = sqrt(d2);
+                        if (dn == 0.0) continue;
+                        double mag;
+                        const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
+                        const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
+                        if (p.grain[j] != gi || L >= p.Rc) {
+                            mag = -p.Kn * (p.Rc - dn);
+                        } else {
+                            const double sr = (dn - L) / L;
+                            mag = p.c * (sr < 0.0 ? sr : 0.0);
+                        }
+                        const double gm = mag * xj.w / dn;
+                        fbx += (float)(gm * dx); fby += (float)(gm * dy); fbz += (float)(gm * dz);
+                    }
+                }
+            }
+            fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
+            if (active && gl == 0)
+                err |= epilogue_mixed(p, row, fbx, fby, fbz, o0, o1, o2, vhs[rr], vls[rr], s_react[grp], vmax2f);
         }
         __syncthreads();
     }
@@ -588,7 +678,7 @@ template <int G>
 void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 {
     if (mixed && p.tile_cap > 0) {
-        const size_t smem = (size_t)3 * p.tile_cap * sizeof(float4);
+        const size_t smem = tiled_smem(p.tile_cap, p.tile_rows, p.tile_slot_cap);
         k_step_tiled<G><<<blocks, STEP_THREADS, smem, st>>>(p);
     } else if (mixed) {
         k_step<G, true><<<blocks, STEP_THREADS, 0, st>>>(p);
@@ -598,11 +688,10 @@ void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 }
 
 template <int G>
-int blocks_g(int sms, bool mixed, bool tiled, int tile_cap)
+int blocks_g(int sms, bool mixed, bool tiled, size_t smem)
 {
     int per = 0;
     if (mixed && tiled) {
-        const size_t smem = (size_t)3 * tile_cap * sizeof(float4);
         cudaFuncSetAttribute(k_step_tiled<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tiled<G>, STEP_THREADS, smem);
     } else if (mixed) {
@@ -616,9 +705,17 @@ int blocks_g(int sms, bool mixed, bool tiled, int tile_cap)
 
 }  // namespace
 
-// Grid of the step kernel: SMs x resident blocks per SM (persistent loops).
-int step_blocks(int lanes, int device, bool mixed, bool tiled, int tile_cap)
+// bytes of dynamic shared memory of k_step_tiled
+size_t tiled_smem(int tile_cap, int tile_rows, int slot_cap)
 {
+    return (size_t)(3 * tile_cap + 2 * tile_rows) * sizeof(float4) + (size_t)2 * (tile_rows + 1) * sizeof(int64_t) +
+           (size_t)((tile_rows + 7) & ~7) * 2 + (size_t)(slot_cap + 16) * 2;
+}
+
+// Grid of the step kernel: SMs x resident blocks per SM (persistent loops).
+int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem)
+{
+    const size_t tile_cap = tile_smem;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (sms < 1) sms = 1;
