@@ -216,6 +216,30 @@ pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, in
 const char *pd_last_error(const pd_ctx *ctx);
 void pd_destroy(pd_ctx *ctx);
 
+/* Allocation-free critical time step.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they need the
+ * step, e.g. code running while a memory pool is frozen, a runtime that owns
+ * every device allocation itself, or a host callback where cudaMalloc is not
+ * allowed.  Same bound as pd_stable_dt, dt = min_i sqrt(2 rho / sum_j V_j c /
+ * |x_j - x_i|) over rows with at least one bond, computed from the caller's
+ * DEVICE arrays: x (n*3 FP64, row-major), vol (n), rowptr (n+1, int64), col
+ * (rowptr[n] int32 node indices); c is the micromodulus and rho the density.
+ * Writes the step to the caller's device double *dt_out (INFINITY when no row
+ * has a bond) on `stream` (cudaStream_t, NULL = legacy stream); does not
+ * synchronise.
+ * It allocates nothing: its scratch (per-block partial minima) is a file-scope
+ * device array of 65,536 doubles (512 KiB) that every GPU loading this library
+ * holds until the process exits.  Hence n <= 16,777,216; larger n gives
+ * PD_EINVAL.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls on a device share the array, so calls that
+ * overlap on the GPU (other streams, other threads) race; each call writes every
+ * partial it reads, so nothing needs clearing between calls.
+ * Errors: PD_EINVAL (null pointer, n < 1, n too large, c or rho <= 0),
+ * PD_ECUDA (no current device, symbol lookup or launch failed). */
+pd_status pd_stable_dt_noalloc(int64_t n, const double *x, const double *vol, const int64_t *rowptr,
+                               const int32_t *col, double c, double rho, void *stream, double *dt_out);
+
 /* ---------------------------------------------------------------------------
  * Bulk-stress surrogate: an MLP dims[0] -> ... -> dims[nlayers] with exact GELU
  * between layers, BF16 weights and activations, FP32 accumulation, FP32 master

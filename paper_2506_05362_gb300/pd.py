@@ -93,6 +93,7 @@ def lib():
                 "pd_tuning": (i32, [P, P, P]),
                 "pd_last_step_stats": (i32, [P, P, P, P]),
                 "pd_set_profiling": (i32, [P, i32]),
+                "pd_stable_dt_noalloc": (i32, [i64, P, P, P, P, f64, f64, P, P]),
                 "pd_last_error": (ctypes.c_char_p, [P]),
                 "pd_destroy": (None, [P]),
                 "pd_mlp_create": (i32, [P, i32, ctypes.c_uint64, i32, P, P]),
@@ -291,6 +292,13 @@ def pd_last_step_stats(h):
 
 def pd_set_profiling(h, on):
     _check(lib().pd_set_profiling(h, 1 if on else 0), h)
+
+
+def pd_stable_dt_noalloc(n, x_dev, vol_dev, rowptr_dev, col_dev, c, rho, stream, dt_out_dev):
+    """Critical time step from device arrays without any allocation (see pd.h).
+    Pointer arguments are integers (e.g. torch ``data_ptr()``).  Returns the status."""
+    return lib().pd_stable_dt_noalloc(int(n), P(x_dev), P(vol_dev), P(rowptr_dev), P(col_dev), float(c),
+                                      float(rho), P(stream) if stream else None, P(dt_out_dev))
 
 
 def pd_destroy(h):
