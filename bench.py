@@ -160,6 +160,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50, help="0 skips the end-to-end leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison leg")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-network leg")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per node (0 = autotune)")
+    ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -175,7 +178,12 @@ def main():
 
     sc = S.kalthoff()
     stream = torch.cuda.Stream(local)
-    ctx = pd.Context.from_scenario(sc, precision=args.precision, device=local, stream=stream)
+    ctx = pd.Context.from_scenario(sc, precision=args.precision, device=local, stream=stream,
+                                   lanes=args.lanes, tiles={"auto": 0, "on": 1, "off": -1}[args.tiles])
+    lanes, tiled, tms = ctx.tuning()
+    tuning = {"lanes_per_node": lanes, "tiled": tiled,
+              "ms_global_4_8_16_32": [round(float(t), 4) for t in tms[:4]],
+              "ms_tiled_4_8_16_32": [round(float(t), 4) for t in tms[4:]]}
     dt = 0.8 * ctx.stable_dt()
     n, B = sc.n, ctx.B
     # warm-up (captures the graphs)
@@ -264,6 +272,7 @@ def main():
                 "ms_per_step": m64 / k64, "bond_updates_per_s": B * k64 / (m64 * 1e-3)}
         c64.close()
 
+    surrogate = None if args.no_surrogate else bench_surrogate(local, stream)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(sc)
@@ -276,10 +285,57 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "bond_updates_per_s": ws * B * args.steps / (ms * 1e-3),
             "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches), "fp64_gpu_path": fp64,
-            "lanes_per_node": ctx.tuning()[0]}
+            "gpu_launches": int(launches), "fp64_gpu_path": fp64, "surrogate": surrogate,
+            "tuning": tuning}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def bench_surrogate(local, stream, reps=20):
+    """MLP 109-256-256-256-256-6 at inference batch 65536 and one Adam training
+    step at the same batch: device time with CUDA events, FLOP rate against the
+    measured BF16 tensor peak."""
+    import torch
+    from paper_2506_05362_gb300 import pd
+    dims = (109, 256, 256, 256, 256, 6)
+    B = 65536
+    net = pd.MLP(dims, seed=0, device=local, stream=stream)
+    g = torch.Generator(device=f"cuda:{local}").manual_seed(0)
+    X = torch.randn(B, dims[0], device=f"cuda:{local}", generator=g)
+    T = torch.randn(B, dims[-1], device=f"cuda:{local}", generator=g)
+    Y = torch.empty(B, dims[-1], device=f"cuda:{local}")
+    flop_fwd = 2.0 * B * sum(dims[i] * dims[i + 1] for i in range(len(dims) - 1))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            net.forward_device(X, Y)
+            net.train_step_device(X, T, 1e-4)
+        stream.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            net.forward_device(X, Y)
+        ev1.record(stream)
+        stream.synchronize()
+        fwd_ms = ev0.elapsed_time(ev1) / reps
+        ev0.record(stream)
+        for _ in range(reps):
+            net.train_step_device(X, T, 1e-4)
+        ev1.record(stream)
+        stream.synchronize()
+        train_ms = ev0.elapsed_time(ev1) / reps
+    net.close()
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        kind = "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    fwd_tf = flop_fwd / (fwd_ms * 1e-3) / 1e12
+    train_tf = 3 * flop_fwd / (train_ms * 1e-3) / 1e12
+    return {"dims": list(dims), "batch": B, "forward_ms": fwd_ms, "forward_samples_per_s": B / (fwd_ms * 1e-3),
+            "train_step_ms": train_ms,
+            "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
+                         "frac": fwd_tf / peak, "peak_kind": kind, "kernel": "k_gemm (forward, all layers)"},
+            "train_tflops": train_tf}
 
 
 def kernel_hash():

@@ -198,9 +198,11 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
 
-/* Autotuning record of the bond loop: lanes per node chosen and the measured
- * time per step (ms) of each candidate (4, 8, 16, 32 lanes; 0 = not run). */
-pd_status pd_tuning(pd_ctx *ctx, int *lanes, double ms[4]);
+/* Autotuning record of the bond loop: lanes per node chosen, whether the
+ * shared-memory tiles were chosen, and the measured time (ms) of one force
+ * evaluation per candidate: ms[0..3] global gathers with 4, 8, 16, 32 lanes,
+ * ms[4..7] tiles with 4, 8, 16, 32 lanes (0 = not run).  Any pointer may be NULL. */
+pd_status pd_tuning(pd_ctx *ctx, int *lanes, int *tiled, double ms[8]);
 
 /* Profiling switch.  When on, pd_step launches its kernels one by one (no CUDA
  * graph) with CUDA events around every fused force/update launch, so that

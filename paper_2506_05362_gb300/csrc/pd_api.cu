@@ -59,7 +59,7 @@ struct pd_ctx {
     unsigned *counter = nullptr, *derr = nullptr;
     int *stale = nullptr;
     int blocks = 0, lanes = 0, blocks_cap = 0;
-    double tune_ms[4] = {0, 0, 0, 0};
+    double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // shared-memory tiles of the mixed path
     int64_t *tile_ptr = nullptr;
     int32_t *ulist = nullptr;
@@ -550,6 +550,7 @@ static pd_status autotune(pd_ctx *c)
     if (c->opt.contact) enqueue_rebuild(c, c->cur);
     for (int q = 0; q < 4; ++q) {
         c->tune_ms[q] = 0;
+        c->tune_ms[4 + q] = 0;
         for (int tl = tmin; tl < (can_tile ? 2 : 1); ++tl) {
             const int l = cand[q];
             c->tiled = tl == 1;
@@ -563,7 +564,7 @@ static pd_status autotune(pd_ctx *c)
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
             const double t = ms / 5.0;
-            if (c->tune_ms[q] == 0 || t < c->tune_ms[q]) c->tune_ms[q] = t;
+            c->tune_ms[4 * tl + q] = t;
             if (t < best) { best = t; bestl = l; best_tiled = c->tiled; }
         }
     }
@@ -1190,12 +1191,13 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
     return PD_OK;
 }
 
-pd_status pd_tuning(pd_ctx *c, int *lanes, double ms[4])
+pd_status pd_tuning(pd_ctx *c, int *lanes, int *tiled, double ms[8])
 {
     if (!c) return PD_EINVAL;
     if (lanes) *lanes = c->lanes;
+    if (tiled) *tiled = c->tiled ? 1 : 0;
     if (ms)
-        for (int q = 0; q < 4; ++q) ms[q] = c->tune_ms[q];
+        for (int q = 0; q < 8; ++q) ms[q] = c->tune_ms[q];
     return PD_OK;
 }
 

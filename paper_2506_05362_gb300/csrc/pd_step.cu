@@ -120,6 +120,64 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
     }
 }
 
+// Two bonds of one row at once (slots ka, kb) with Blackwell's packed FP32x2
+// adds, multiplies and FMAs: each pair instruction performs the scalar
+// operation of bond_mixed on both bonds, with the same rounding.  ma, mb mark
+// live (unbroken, existing) bonds; broken ones contribute nothing.
+template <bool FLAG>
+__device__ __forceinline__ void bond_pair(const StepParams &p, int ka, int kb, bool ma, bool mb, const float2 *no,
+                                          const float2 *nol, const float4 &a0, const float4 &a1, const float4 &a2,
+                                          const float4 &b0, const float4 &b1, const float4 &b2, float2 &fx,
+                                          float2 &fy, float2 &fz)
+{
+    float al[3], bl[3];
+    xl_unpack(a1.w, a2.w, al);
+    xl_unpack(b1.w, b2.w, bl);
+    // xi = (x_hi_j - x_hi_i) + (x_lo_j - x_lo_i); eta likewise from u; no/nol hold -own
+    const float2 xx = __fadd2_rn(__fadd2_rn(make_float2(a0.x, b0.x), no[0]), __fadd2_rn(make_float2(al[0], bl[0]), nol[0]));
+    const float2 xy = __fadd2_rn(__fadd2_rn(make_float2(a0.y, b0.y), no[1]), __fadd2_rn(make_float2(al[1], bl[1]), nol[1]));
+    const float2 xz = __fadd2_rn(__fadd2_rn(make_float2(a0.z, b0.z), no[2]), __fadd2_rn(make_float2(al[2], bl[2]), nol[2]));
+    const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(a1.x, b1.x), no[3]), __fadd2_rn(make_float2(a2.x, b2.x), no[6]));
+    const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(a1.y, b1.y), no[4]), __fadd2_rn(make_float2(a2.y, b2.y), no[7]));
+    const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(a1.z, b1.z), no[5]), __fadd2_rn(make_float2(a2.z, b2.z), no[8]));
+    const float2 yx = __fadd2_rn(xx, ex), yy = __fadd2_rn(xy, ey), yz = __fadd2_rn(xz, ez);
+    const float2 L2 = __ffma2_rn(xx, xx, __ffma2_rn(xy, xy, __fmul2_rn(xz, xz)));
+    const float2 y2 = __ffma2_rn(yx, yx, __ffma2_rn(yy, yy, __fmul2_rn(yz, yz)));
+    const float2 num = __ffma2_rn(ex, __fadd2_rn(xx, yx), __ffma2_rn(ey, __fadd2_rn(xy, yy), __fmul2_rn(ez, __fadd2_rn(xz, yz))));
+    const float2 rL = make_float2(rsqrtf(L2.x), rsqrtf(L2.y)), ry = make_float2(rsqrtf(y2.x), rsqrtf(y2.y));
+    const float2 nr = __fmul2_rn(num, rL);
+    const float2 den = __ffma2_rn(y2, ry, __fmul2_rn(L2, rL));
+    const float2 s = make_float2(__fdividef(nr.x, den.x), __fdividef(nr.y, den.y));
+    const bool ba = ma && (p.break_mode ? (fabsf(s.x) > p.s0f) : (s.x > p.s0f));
+    const bool bb = mb && (p.break_mode ? (fabsf(s.y) > p.s0f) : (s.y > p.s0f));
+    if (ba) {
+        atomicOr(p.brk + (ka >> 5), 1u << (ka & 31));
+        if (FLAG) atomicOr((unsigned int *)(p.lcol) + (ka >> 1), 0x8000u << (16 * (ka & 1)));
+    }
+    if (bb) {
+        atomicOr(p.brk + (kb >> 5), 1u << (kb & 31));
+        if (FLAG) atomicOr((unsigned int *)(p.lcol) + (kb >> 1), 0x8000u << (16 * (kb & 1)));
+    }
+    const float2 cv = __fmul2_rn(make_float2(p.cf, p.cf), make_float2(a0.w, b0.w));
+    float2 g = __fmul2_rn(__fmul2_rn(cv, s), ry);
+    g.x = (ma && !ba) ? g.x : 0.f;
+    g.y = (mb && !bb) ? g.y : 0.f;
+    fx = __ffma2_rn(g, yx, fx);
+    fy = __ffma2_rn(g, yy, fy);
+    fz = __ffma2_rn(g, yz, fz);
+}
+
+// negated own record for bond_pair: -x_hi (0..2), -u_hi (3..5), -u_lo (6..8); -x_lo
+__device__ __forceinline__ void own_neg(const float4 &o0, const float4 &o1, const float4 &o2, float2 *no, float2 *nol)
+{
+    float ol[3];
+    xl_unpack(o1.w, o2.w, ol);
+    no[0] = make_float2(-o0.x, -o0.x); no[1] = make_float2(-o0.y, -o0.y); no[2] = make_float2(-o0.z, -o0.z);
+    no[3] = make_float2(-o1.x, -o1.x); no[4] = make_float2(-o1.y, -o1.y); no[5] = make_float2(-o1.z, -o1.z);
+    no[6] = make_float2(-o2.x, -o2.x); no[7] = make_float2(-o2.y, -o2.y); no[8] = make_float2(-o2.z, -o2.z);
+    nol[0] = make_float2(-ol[0], -ol[0]); nol[1] = make_float2(-ol[1], -ol[1]); nol[2] = make_float2(-ol[2], -ol[2]);
+}
+
 // u of node i in FP64: the double-float state of the mixed path, or the FP64 array
 template <bool MIXED>
 __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
@@ -245,20 +303,23 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             }
         } else if (MIXED) {
             const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
-            float ol[3];
-            xl_unpack(o1.w, o2.w, ol);
-            for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
-                const int64_t kb = k + G;
-                const bool hasb = kb < k1;
+            float2 no[9], nol[3];
+            own_neg(o0, o1, o2, no, nol);
+            float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+            const int i0 = (int)k0, i1 = (int)k1;
+            for (int k = i0 + gl; k < i1; k += 2 * G) {
+                const int kb = k + G;
+                const bool hasb = kb < i1;
                 const uint32_t wa = __ldg(p.brk + (k >> 5));
                 const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
                 const int ja = __ldg(p.col + k);
                 const int jb = hasb ? __ldg(p.col + kb) : ja;
                 const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
                 const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
-                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+                bond_pair<false>(p, k, kb, !((wa >> (k & 31)) & 1u), hasb && !((wb >> (kb & 31)) & 1u), no, nol, a0,
+                                 a1, a2, b0, b1, b2, px, py, pz);
             }
+            fbx = px.x + px.y; fby = py.x + py.y; fbz = pz.x + pz.y;
         } else {
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
             for (int64_t k = k0 + gl; k < k1; k += G) {
@@ -534,19 +595,21 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
             if (active) {
                 const int lr = lrs[rr];
                 o0 = r0s[lr]; o1 = r1s[lr]; o2 = r2s[lr];
-                float ol[3];
-                xl_unpack(o1.w, o2.w, ol);
-                const int64_t k0 = rps[rr], k1 = rps[rr + 1];
-                for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
-                    const int64_t kb = k + G;
-                    const uint32_t la = lcs[k - ka];
-                    const uint32_t lb = kb < k1 ? lcs[kb - ka] : 0x8000u;
+                float2 no[9], nol[3];
+                own_neg(o0, o1, o2, no, nol);
+                float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+                const int i0 = (int)rps[rr], i1 = (int)rps[rr + 1], kofs = (int)ka;
+                for (int k = i0 + gl; k < i1; k += 2 * G) {
+                    const int kb = k + G;
+                    const uint32_t la = lcs[k - kofs];
+                    const uint32_t lb = kb < i1 ? lcs[kb - kofs] : 0x8000u;
                     const uint32_t ia = la & 0x7fffu, ib = lb & 0x7fffu;
                     const float4 a0 = r0s[ia], a1 = r1s[ia], a2 = r2s[ia];
                     const float4 b0 = r0s[ib], b1 = r1s[ib], b2 = r2s[ib];
-                    if (!(la & 0x8000u)) bond_mixed<true>(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                    if (!(lb & 0x8000u)) bond_mixed<true>(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+                    bond_pair<true>(p, k, kb, !(la & 0x8000u), !(lb & 0x8000u), no, nol, a0, a1, a2, b0, b1, b2, px,
+                                    py, pz);
                 }
+                fbx = px.x + px.y; fby = py.x + py.y; fbz = pz.x + pz.y;
             }
             __syncwarp();
             // contact candidates (rare; FP64 from global memory)

@@ -90,7 +90,7 @@ def lib():
                 "pd_forces": (i32, [P, P]),
                 "pd_get_state": (i32, [P, P, P, P, P]),
                 "pd_set_state": (i32, [P, P, P, P, P]),
-                "pd_tuning": (i32, [P, P, P]),
+                "pd_tuning": (i32, [P, P, P, P]),
                 "pd_last_step_stats": (i32, [P, P, P, P]),
                 "pd_set_profiling": (i32, [P, i32]),
                 "pd_stable_dt_noalloc": (i32, [i64, P, P, P, P, f64, f64, P, P]),
@@ -278,10 +278,10 @@ def pd_set_state(h, u=None, v=None, broken=None, t=None):
 
 
 def pd_tuning(h):
-    lanes = ctypes.c_int()
-    ms = np.zeros(4)
-    _check(lib().pd_tuning(h, ctypes.byref(lanes), _ptr(ms)), h)
-    return lanes.value, ms
+    lanes, tiled = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(8)
+    _check(lib().pd_tuning(h, ctypes.byref(lanes), ctypes.byref(tiled), _ptr(ms)), h)
+    return lanes.value, bool(tiled.value), ms
 
 
 def pd_last_step_stats(h):
@@ -393,9 +393,8 @@ class Context:
         pd_set_state(self.h, u, v, broken, t)
 
     def tuning(self):
-        """(lanes per node, tiles on?, ms per candidate lane count)."""
-        lanes, ms = pd_tuning(self.h)
-        return lanes, ms
+        """(lanes per node, tiles chosen, ms per candidate: 4 global then 4 tiled)."""
+        return pd_tuning(self.h)
 
     def set_profiling(self, on):
         pd_set_profiling(self.h, on)
