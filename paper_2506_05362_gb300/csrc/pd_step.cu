@@ -120,64 +120,6 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
     }
 }
 
-// Two bonds of one row at once (slots ka, kb) with Blackwell's packed FP32x2
-// adds, multiplies and FMAs: each pair instruction performs the scalar
-// operation of bond_mixed on both bonds, with the same rounding.  ma, mb mark
-// live (unbroken, existing) bonds; broken ones contribute nothing.
-template <bool FLAG>
-__device__ __forceinline__ void bond_pair(const StepParams &p, int ka, int kb, bool ma, bool mb, const float2 *no,
-                                          const float2 *nol, const float4 &a0, const float4 &a1, const float4 &a2,
-                                          const float4 &b0, const float4 &b1, const float4 &b2, float2 &fx,
-                                          float2 &fy, float2 &fz)
-{
-    float al[3], bl[3];
-    xl_unpack(a1.w, a2.w, al);
-    xl_unpack(b1.w, b2.w, bl);
-    // xi = (x_hi_j - x_hi_i) + (x_lo_j - x_lo_i); eta likewise from u; no/nol hold -own
-    const float2 xx = __fadd2_rn(__fadd2_rn(make_float2(a0.x, b0.x), no[0]), __fadd2_rn(make_float2(al[0], bl[0]), nol[0]));
-    const float2 xy = __fadd2_rn(__fadd2_rn(make_float2(a0.y, b0.y), no[1]), __fadd2_rn(make_float2(al[1], bl[1]), nol[1]));
-    const float2 xz = __fadd2_rn(__fadd2_rn(make_float2(a0.z, b0.z), no[2]), __fadd2_rn(make_float2(al[2], bl[2]), nol[2]));
-    const float2 ex = __fadd2_rn(__fadd2_rn(make_float2(a1.x, b1.x), no[3]), __fadd2_rn(make_float2(a2.x, b2.x), no[6]));
-    const float2 ey = __fadd2_rn(__fadd2_rn(make_float2(a1.y, b1.y), no[4]), __fadd2_rn(make_float2(a2.y, b2.y), no[7]));
-    const float2 ez = __fadd2_rn(__fadd2_rn(make_float2(a1.z, b1.z), no[5]), __fadd2_rn(make_float2(a2.z, b2.z), no[8]));
-    const float2 yx = __fadd2_rn(xx, ex), yy = __fadd2_rn(xy, ey), yz = __fadd2_rn(xz, ez);
-    const float2 L2 = __ffma2_rn(xx, xx, __ffma2_rn(xy, xy, __fmul2_rn(xz, xz)));
-    const float2 y2 = __ffma2_rn(yx, yx, __ffma2_rn(yy, yy, __fmul2_rn(yz, yz)));
-    const float2 num = __ffma2_rn(ex, __fadd2_rn(xx, yx), __ffma2_rn(ey, __fadd2_rn(xy, yy), __fmul2_rn(ez, __fadd2_rn(xz, yz))));
-    const float2 rL = make_float2(rsqrtf(L2.x), rsqrtf(L2.y)), ry = make_float2(rsqrtf(y2.x), rsqrtf(y2.y));
-    const float2 nr = __fmul2_rn(num, rL);
-    const float2 den = __ffma2_rn(y2, ry, __fmul2_rn(L2, rL));
-    const float2 s = make_float2(__fdividef(nr.x, den.x), __fdividef(nr.y, den.y));
-    const bool ba = ma && (p.break_mode ? (fabsf(s.x) > p.s0f) : (s.x > p.s0f));
-    const bool bb = mb && (p.break_mode ? (fabsf(s.y) > p.s0f) : (s.y > p.s0f));
-    if (ba) {
-        atomicOr(p.brk + (ka >> 5), 1u << (ka & 31));
-        if (FLAG) atomicOr((unsigned int *)(p.lcol) + (ka >> 1), 0x8000u << (16 * (ka & 1)));
-    }
-    if (bb) {
-        atomicOr(p.brk + (kb >> 5), 1u << (kb & 31));
-        if (FLAG) atomicOr((unsigned int *)(p.lcol) + (kb >> 1), 0x8000u << (16 * (kb & 1)));
-    }
-    const float2 cv = __fmul2_rn(make_float2(p.cf, p.cf), make_float2(a0.w, b0.w));
-    float2 g = __fmul2_rn(__fmul2_rn(cv, s), ry);
-    g.x = (ma && !ba) ? g.x : 0.f;
-    g.y = (mb && !bb) ? g.y : 0.f;
-    fx = __ffma2_rn(g, yx, fx);
-    fy = __ffma2_rn(g, yy, fy);
-    fz = __ffma2_rn(g, yz, fz);
-}
-
-// negated own record for bond_pair: -x_hi (0..2), -u_hi (3..5), -u_lo (6..8); -x_lo
-__device__ __forceinline__ void own_neg(const float4 &o0, const float4 &o1, const float4 &o2, float2 *no, float2 *nol)
-{
-    float ol[3];
-    xl_unpack(o1.w, o2.w, ol);
-    no[0] = make_float2(-o0.x, -o0.x); no[1] = make_float2(-o0.y, -o0.y); no[2] = make_float2(-o0.z, -o0.z);
-    no[3] = make_float2(-o1.x, -o1.x); no[4] = make_float2(-o1.y, -o1.y); no[5] = make_float2(-o1.z, -o1.z);
-    no[6] = make_float2(-o2.x, -o2.x); no[7] = make_float2(-o2.y, -o2.y); no[8] = make_float2(-o2.z, -o2.z);
-    nol[0] = make_float2(-ol[0], -ol[0]); nol[1] = make_float2(-ol[1], -ol[1]); nol[2] = make_float2(-ol[2], -ol[2]);
-}
-
 // u of node i in FP64: the double-float state of the mixed path, or the FP64 array
 template <bool MIXED>
 __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
@@ -195,74 +137,80 @@ __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
     return r;
 }
 
-// Mixed-path epilogue: forces to acceleration in FP32, Verlet update of the
-// double-float state.  Wall forces are evaluated in FP64 only for nodes that an
-// FP32 pre-test places near a wall.
-__device__ __forceinline__ unsigned epilogue_mixed(const StepParams &p, int64_t row, float Fx, float Fy, float Fz,
-                                                   const float4 &oxh, const float4 &uh, const float4 &ul,
-                                                   const float4 &vh_in, const float4 &vl_in, double *react,
-                                                   float &vmax2)
+// Mixed-path epilogue spread over the group: lane c (0, 1, 2) updates component
+// c of the node's acceleration, velocity and displacement (same arithmetic as
+// epilogue_mixed).  Every lane of the warp calls it (inactive rows included) so
+// that the shuffles that broadcast a wall force are uniform.
+template <int G>
+__device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t row, bool active, int gl, float Fx,
+                                                   float Fy, float Fz, const float4 &oxh, const float4 &uh,
+                                                   const float4 &ul, const float4 &vh, const float4 &vl,
+                                                   double *react, float &vmax2)
 {
     unsigned err = 0;
-    if (p.walls.nw) {
-        const float px = oxh.x + uh.x, py = oxh.y + uh.y, pz = oxh.z + uh.z;
-        const float cx = (float)p.centre[0], cy = (float)p.centre[1], cz = (float)p.centre[2];
-        bool near = false;
-        for (int l = 0; l < p.walls.nw; ++l) {
-            const double *w = p.wall_pos + 3 * l;
-            const float wx = (float)w[0] - cx, wy = (float)w[1] - cy, wz = (float)w[2] - cz;
-            const float d = (px - wx) * (float)p.walls.n[l][0] + (py - wy) * (float)p.walls.n[l][1] +
-                            (pz - wz) * (float)p.walls.n[l][2];
-            const float margin = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(wx) + fabsf(wy) + fabsf(wz) +
-                                          fabsf(cx) + fabsf(cy) + fabsf(cz));
-            near |= d < p.Rc_f + margin;
+    if (p.walls.nw) {  // uniform: a kernel parameter
+        float wx = 0.f, wy = 0.f, wz = 0.f;
+        if (active && gl == 0) {
+            const float px = oxh.x + uh.x, py = oxh.y + uh.y, pz = oxh.z + uh.z;
+            const float cx = (float)p.centre[0], cy = (float)p.centre[1], cz = (float)p.centre[2];
+            bool near = false;
+            for (int l = 0; l < p.walls.nw; ++l) {
+                const double *w = p.wall_pos + 3 * l;
+                const float qx = (float)w[0] - cx, qy = (float)w[1] - cy, qz = (float)w[2] - cz;
+                const float d = (px - qx) * (float)p.walls.n[l][0] + (py - qy) * (float)p.walls.n[l][1] +
+                                (pz - qz) * (float)p.walls.n[l][2];
+                const float margin = 1e-6f * (fabsf(px) + fabsf(py) + fabsf(pz) + fabsf(qx) + fabsf(qy) +
+                                              fabsf(qz) + fabsf(cx) + fabsf(cy) + fabsf(cz));
+                near |= d < p.Rc_f + margin;
+            }
+            if (near) {
+                const dbl4 ox = p.x4[row];
+                const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
+                             uz = df_to_double(df{uh.z, ul.z});
+                double fx = 0.0, fy = 0.0, fz = 0.0;
+                err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, fx, fy, fz, react);
+                wx = (float)fx; wy = (float)fy; wz = (float)fz;
+            }
         }
-        if (near) {
-            const dbl4 ox = p.x4[row];
-            const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
-                         uz = df_to_double(df{uh.z, ul.z});
-            double fx = 0.0, fy = 0.0, fz = 0.0;
-            err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, fx, fy, fz, react);
-            Fx += (float)fx; Fy += (float)fy; Fz += (float)fz;
-        }
+        const int leader = (int)(threadIdx.x & 31) & ~(G - 1);
+        Fx += __shfl_sync(0xffffffffu, wx, leader);
+        Fy += __shfl_sync(0xffffffffu, wy, leader);
+        Fz += __shfl_sync(0xffffffffu, wz, leader);
     }
-    if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
-    float4 a;
-    a.x = (Fx + p.bf[0]) * p.inv_rho_f;
-    a.y = (Fy + p.bf[1]) * p.inv_rho_f;
-    a.z = (Fz + p.bf[2]) * p.inv_rho_f;
-    a.w = 0.f;
+    if (!active || gl >= 3) return err;
+    const int c = gl;
+    const float F = c == 0 ? Fx : (c == 1 ? Fy : Fz);
+    if (!isfinite(F)) err |= PDE_NONFINITE;
+    const float a = (F + p.bf[c]) * p.inv_rho_f;
+    float *afc = (float *)(p.af + row) + c;
     if (p.mode == MODE_FORCES) {
-        p.af[row] = a;
-        if (p.F_out) {
-            dbl4 f; f.x = Fx; f.y = Fy; f.z = Fz; f.w = 0.0;
-            p.F_out[row] = f;
-        }
+        *afc = a;
+        if (p.F_out) ((double *)(p.F_out + row))[c] = (double)F;
         return err;
     }
     const df hdt{p.hdt_hi, p.hdt_lo};
-    df vx{vh_in.x, vl_in.x}, vy{vh_in.y, vl_in.y}, vz{vh_in.z, vl_in.z};
-    vx = df_add(vx, df_mul_f(hdt, a.x));
-    vy = df_add(vy, df_mul_f(hdt, a.y));
-    vz = df_add(vz, df_mul_f(hdt, a.z));
+    const float vhc = c == 0 ? vh.x : (c == 1 ? vh.y : vh.z);
+    const float vlc = c == 0 ? vl.x : (c == 1 ? vl.y : vl.z);
+    df v = df_add(df{vhc, vlc}, df_mul_f(hdt, a));
     if (p.mode == MODE_FULL) {
-        vx = df_add(vx, df_mul_f(hdt, a.x));
-        vy = df_add(vy, df_mul_f(hdt, a.y));
-        vz = df_add(vz, df_mul_f(hdt, a.z));
-        const df dt{p.dt_hi, p.dt_lo};
-        const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
-        const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
-        const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
-        p.uh_out[row] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
-        p.ul_out[row] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
-        const float vv = vx.hi * vx.hi + vy.hi * vy.hi + vz.hi * vz.hi;
-        vmax2 = fmaxf(vmax2, vv);
-        if (!isfinite(vv) || !isfinite(ux.hi + uy.hi + uz.hi)) err |= PDE_NONFINITE;
+        v = df_add(v, df_mul_f(hdt, a));
+        const float uhc = c == 0 ? uh.x : (c == 1 ? uh.y : uh.z);
+        const float ulc = c == 0 ? ul.x : (c == 1 ? ul.y : ul.z);
+        const df u = df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v));
+        ((float *)(p.uh_out + row))[c] = u.hi;
+        ((float *)(p.ul_out + row))[c] = u.lo;
+        if (c == 0) {  // packed x_lo travels with the record
+            ((float *)(p.uh_out + row))[3] = uh.w;
+            ((float *)(p.ul_out + row))[3] = ul.w;
+        }
+        // |v|^2 <= 3 max_c v_c^2: a bound is all the skin bookkeeping needs
+        vmax2 = fmaxf(vmax2, 3.f * v.hi * v.hi);
+        if (!isfinite(v.hi) || !isfinite(u.hi)) err |= PDE_NONFINITE;
     } else {
-        p.af[row] = a;
+        *afc = a;
     }
-    p.vh[row] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
-    p.vl[row] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
+    ((float *)(p.vh + row))[c] = v.hi;
+    ((float *)(p.vl + row))[c] = v.lo;
     return err;
 }
 
@@ -285,27 +233,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
     double fdx = 0.0, fdy = 0.0, fdz = 0.0;
     if (active) {
         const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
-        if (MIXED && tv.on) {
-            const float4 o0 = tv.s0[lrow], o1 = tv.s1[lrow], o2 = tv.s2[lrow];
+        if (MIXED) {
+            const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
-            for (int64_t k = k0 + gl; k < k1; k += 2 * G) {
-                const int64_t kb = k + G;
-                const bool hasb = kb < k1;
-                const uint32_t wa = __ldg(p.brk + (k >> 5));
-                const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
-                const int la = __ldg(p.lcol + k);
-                const int lb = hasb ? __ldg(p.lcol + kb) : la;
-                const float4 a0 = tv.s0[la], a1 = tv.s1[la], a2 = tv.s2[la];
-                const float4 b0 = tv.s0[lb], b1 = tv.s1[lb], b2 = tv.s2[lb];
-                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
-            }
-        } else if (MIXED) {
-            const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
-            float2 no[9], nol[3];
-            own_neg(o0, o1, o2, no, nol);
-            float2 px = make_float2(0.f, 0.f), py = px, pz = px;
             const int i0 = (int)k0, i1 = (int)k1;
             for (int k = i0 + gl; k < i1; k += 2 * G) {
                 const int kb = k + G;
@@ -316,10 +247,9 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
                 const int jb = hasb ? __ldg(p.col + kb) : ja;
                 const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
                 const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
-                bond_pair<false>(p, k, kb, !((wa >> (k & 31)) & 1u), hasb && !((wb >> (kb & 31)) & 1u), no, nol, a0,
-                                 a1, a2, b0, b1, b2, px, py, pz);
+                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
             }
-            fbx = px.x + px.y; fby = py.x + py.y; fbz = pz.x + pz.y;
         } else {
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
             for (int64_t k = k0 + gl; k < k1; k += G) {
@@ -392,9 +322,13 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
         fdx = group_sum<G>(fdx); fdy = group_sum<G>(fdy); fdz = group_sum<G>(fdz);
     }
     // ---- 4. walls and Verlet update (group leader)
-    if (MIXED && active && gl == 0) {
-        err |= epilogue_mixed(p, row, fbx, fby, fbz, __ldg(p.xh4 + row), __ldg(p.uh_in + row),
-                              __ldg(p.ul_in + row), p.vh[row], p.vl[row], react, vmax2f);
+    if (MIXED) {
+        float4 oxh = make_float4(0.f, 0.f, 0.f, 0.f), ouh = oxh, oul = oxh, ovh = oxh, ovl = oxh;
+        if (active && gl < 3) {
+            oxh = __ldg(p.xh4 + row); ouh = __ldg(p.uh_in + row); oul = __ldg(p.ul_in + row);
+            ovh = p.vh[row]; ovl = p.vl[row];
+        }
+        err |= epilogue_lanes<G>(p, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
     }
     if (!MIXED && active && gl == 0) {
         const double hdt = 0.5 * p.dt;
@@ -595,9 +529,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
             if (active) {
                 const int lr = lrs[rr];
                 o0 = r0s[lr]; o1 = r1s[lr]; o2 = r2s[lr];
-                float2 no[9], nol[3];
-                own_neg(o0, o1, o2, no, nol);
-                float2 px = make_float2(0.f, 0.f), py = px, pz = px;
+                float ol[3];
+                xl_unpack(o1.w, o2.w, ol);
                 const int i0 = (int)rps[rr], i1 = (int)rps[rr + 1], kofs = (int)ka;
                 for (int k = i0 + gl; k < i1; k += 2 * G) {
                     const int kb = k + G;
@@ -606,10 +539,9 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
                     const uint32_t ia = la & 0x7fffu, ib = lb & 0x7fffu;
                     const float4 a0 = r0s[ia], a1 = r1s[ia], a2 = r2s[ia];
                     const float4 b0 = r0s[ib], b1 = r1s[ib], b2 = r2s[ib];
-                    bond_pair<true>(p, k, kb, !(la & 0x8000u), !(lb & 0x8000u), no, nol, a0, a1, a2, b0, b1, b2, px,
-                                    py, pz);
+                    if (!(la & 0x8000u)) bond_mixed<true>(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
+                    if (!(lb & 0x8000u)) bond_mixed<true>(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
                 }
-                fbx = px.x + px.y; fby = py.x + py.y; fbz = pz.x + pz.y;
             }
             __syncwarp();
             // contact candidates (rare; FP64 from global memory)
@@ -650,8 +582,10 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
                 }
             }
             fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
-            if (active && gl == 0)
-                err |= epilogue_mixed(p, row, fbx, fby, fbz, o0, o1, o2, vhs[rr], vls[rr], s_react[grp], vmax2f);
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            err |= epilogue_lanes<G>(p, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
+                                     active ? o2 : z4, active ? vhs[rr] : z4, active ? vls[rr] : z4, s_react[grp],
+                                     vmax2f);
         }
         __syncthreads();
     }

@@ -1,0 +1,261 @@
+"""Bulk-stress surrogate of a representative volume (RVE) of grains.
+
+The paper motivates RVEs (the force per area of crushed aggregates converges
+with grain count, Sec. 6.4, pointing to multiscale use) but builds none.  Here
+an MLP learns the bulk stress of small star-grain aggregates from their recent
+strain history and descriptors, from data that the peridynamic hot path itself
+generates, and is judged against a fresh full PD run.
+
+Data: an aggregate in a box of six rigid walls is strained at a constant rate
+along one of 8 loading paths (wall velocities per axis); every ``stride`` steps
+the macroscopic strain (from wall positions) and bulk stress (pd_bulk_stress)
+are recorded.  A sample is a window of 16 strain records (6 Voigt components,
+the shear ones are zero for axis-aligned walls) plus 13 descriptors at the
+window end (109 inputs); the target is the stress (6) at the window end.
+Inputs and targets are standardised with the training set's statistics.
+
+All simulation runs in libpd (pd_step), all network arithmetic in the BF16
+tensor-core kernels (pd_mlp_*); this module only arranges arrays.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import scenarios as S
+
+# strain-rate multipliers per axis (compression positive)
+LOADING_PATHS = {
+    "uniaxial_x": (1.0, 0.0, 0.0),
+    "uniaxial_y": (0.0, 1.0, 0.0),
+    "uniaxial_z": (0.0, 0.0, 1.0),
+    "biaxial_xy": (1.0, 1.0, 0.0),
+    "biaxial_yz": (0.0, 1.0, 1.0),
+    "biaxial_zx": (1.0, 0.0, 1.0),
+    "isotropic": (1.0, 1.0, 1.0),
+    "z_lateral_release": (-0.25, -0.25, 1.0),
+}
+WINDOW = 16
+N_DESC = 13
+N_IN = 6 * WINDOW + N_DESC   # 109
+N_OUT = 6
+
+
+@dataclass
+class Run:
+    path: str
+    n_grains: int
+    seed: int
+    strain: np.ndarray      # (T, 6)
+    stress: np.ndarray      # (T, 6) Pa
+    desc: np.ndarray        # (T, 13)
+    pd_seconds: float       # device+host time of the PD steps
+    steps: int
+    nodes: int
+
+
+def grain_shape_stats(x, grain, vol):
+    """Equivalent radius, sphericity proxy (r_eq / r_max) and aspect ratio
+    (sqrt of the extreme covariance eigenvalues) of every grain."""
+    req, sph, asp = [], [], []
+    for g in np.unique(grain):
+        pts = x[grain == g]
+        V = vol[grain == g].sum()
+        r_eq = (3.0 * V / (4.0 * math.pi)) ** (1.0 / 3.0)
+        c = pts.mean(0)
+        r_max = np.linalg.norm(pts - c, axis=1).max() + 1e-30
+        ev = np.linalg.eigvalsh(np.cov((pts - c).T) + 1e-30 * np.eye(3))
+        req.append(r_eq)
+        sph.append(min(1.0, r_eq / r_max))
+        asp.append(math.sqrt(max(ev[-1], 1e-30) / max(ev[0], 1e-30)))
+    return np.array(req), np.array(sph), np.array(asp)
+
+
+def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.03,
+            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None) -> Run:
+    """One compression run of an aggregate along ``path`` at strain rate ``rate``
+    (1/s) up to ``strain_end`` on the dominant axis, recorded ``records`` times."""
+    from . import pd
+    sc = S.aggregate(n_grains=n_grains, seed=seed, h=h, gap_cells=0.5)
+    mult = np.array(LOADING_PATHS[path])
+    walls = S.walls_array(sc.walls)
+    lo = np.array([walls[0, 3], walls[2, 4], walls[4, 5]])
+    hi = np.array([walls[1, 3], walls[3, 4], walls[5, 5]])
+    L0 = hi - lo
+    # wall order from the generator: -x, +x, -y, +y, -z, +z (normals into the box)
+    for k in range(3):
+        vk = 0.5 * mult[k] * rate * L0[k]
+        walls[2 * k, 6:9] = 0.0
+        walls[2 * k + 1, 6:9] = 0.0
+        walls[2 * k, 6 + k] = vk        # lower wall moves up
+        walls[2 * k + 1, 6 + k] = -vk   # upper wall moves down
+    sc.walls = [S.Wall(tuple(w[0:3]), tuple(w[3:6]), tuple(w[6:9])) for w in walls]
+    ctx = pd.Context.from_scenario(sc, device=device, stream=stream)
+    dt = 0.8 * ctx.stable_dt()
+    t_end = strain_end / (rate * max(abs(mult).max(), 1e-9))
+    steps_total = max(records, int(math.ceil(t_end / dt)))
+    stride = max(1, steps_total // records)
+    req, sph, asp = grain_shape_stats(sc.x, sc.grain, sc.vol)
+    static = [req.mean(), req.std(), sph.mean(), sph.std(), math.log(n_grains), asp.mean(), asp.std()]
+    strain = np.zeros((records, 6))
+    stress = np.zeros((records, 6))
+    desc = np.zeros((records, N_DESC))
+    vol_sum = sc.vol.sum()
+    B = max(ctx.B, 1)
+    t0 = time.perf_counter()
+    for r in range(records):
+        ctx.step(dt, stride)
+        pos = ctx.get_walls()
+        lo_t = np.array([pos[0, 0], pos[2, 1], pos[4, 2]])
+        hi_t = np.array([pos[1, 0], pos[3, 1], pos[5, 2]])
+        L = hi_t - lo_t
+        areas = np.array([L[1] * L[2]] * 2 + [L[0] * L[2]] * 2 + [L[0] * L[1]] * 2)
+        sig, _ = ctx.bulk_stress(areas)
+        strain[r, :3] = (L - L0) / L0
+        stress[r] = sig
+        phi = ctx.damage()
+        _, _, broken, _ = ctx.get_state()
+        ncont = len(ctx.contacts())
+        desc[r] = [vol_sum / np.prod(L), static[0], static[1], static[2], static[3], phi.mean(),
+                   broken.sum() / B, static[4], ncont / n_grains, static[5], static[6], L.max() / L.min(),
+                   rate * abs(mult).max()]
+    pd_seconds = time.perf_counter() - t0
+    ctx.close()
+    return Run(path, n_grains, seed, strain, stress, desc, pd_seconds, stride * records, sc.n)
+
+
+def windows(run: Run):
+    """(X (m, 109), Y (m, 6)) samples of one run."""
+    T = run.strain.shape[0]
+    X, Y = [], []
+    for t in range(WINDOW - 1, T):
+        X.append(np.concatenate([run.strain[t - WINDOW + 1:t + 1].ravel(), run.desc[t]]))
+        Y.append(run.stress[t])
+    return np.array(X), np.array(Y)
+
+
+class Scaler:
+    def __init__(self, A):
+        self.mu = A.mean(0)
+        sd = A.std(0)
+        self.sd = np.where(sd > 1e-12 * (np.abs(self.mu) + 1e-30), sd, 1.0)
+
+    def fwd(self, A):
+        return (A - self.mu) / self.sd
+
+    def inv(self, A):
+        return A * self.sd + self.mu
+
+
+def train(runs, epochs=300, batch=4096, lr=1e-3, seed=0, device=0, stream=None):
+    """Trains the MLP on all windows of ``runs`` on the GPU; returns (net,
+    x_scaler, y_scaler, losses)."""
+    import torch
+    from . import pd
+    X = np.concatenate([windows(r)[0] for r in runs])
+    Y = np.concatenate([windows(r)[1] for r in runs])
+    xs, ys = Scaler(X), Scaler(Y)
+    dev = torch.device("cuda", device)
+    Xd = torch.tensor(xs.fwd(X), dtype=torch.float32, device=dev)
+    Yd = torch.tensor(ys.fwd(Y), dtype=torch.float32, device=dev)
+    net = pd.MLP((N_IN, 256, 256, 256, 256, N_OUT), seed=seed, device=device, stream=stream)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    losses = []
+    m = Xd.shape[0]
+    for ep in range(epochs):
+        perm = torch.randperm(m, generator=g).to(dev)
+        lr_ep = lr * (0.5 * (1 + math.cos(math.pi * ep / epochs)) * 0.9 + 0.1)
+        for b0 in range(0, m, batch):
+            idx = perm[b0:b0 + batch]
+            xb = Xd.index_select(0, idx).contiguous()
+            yb = Yd.index_select(0, idx).contiguous()
+            net.train_step_device(xb, yb, lr_ep, loss)
+        if ep % 10 == 0 or ep == epochs - 1:
+            torch.cuda.synchronize(dev)
+            losses.append(float(loss.item()))
+    return net, xs, ys, losses
+
+
+def judge(net, xs, ys, run: Run, device=0):
+    """Error of the surrogate on one run, judged against the PD result:
+    RMS over windows of |sigma_pred - sigma_PD| / max over the run of |sigma_PD|;
+    and the time the network needs for the run's windows."""
+    import torch
+    X, Y = windows(run)
+    dev = torch.device("cuda", device)
+    Xd = torch.tensor(xs.fwd(X), dtype=torch.float32, device=dev)
+    Yd = torch.empty((X.shape[0], N_OUT), dtype=torch.float32, device=dev)
+    net.forward_device(Xd, Yd)  # warm
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    net.forward_device(Xd, Yd)
+    torch.cuda.synchronize(dev)
+    t_net = time.perf_counter() - t0
+    pred = ys.inv(Yd.cpu().numpy().astype(np.float64))
+    err = np.linalg.norm(pred - Y, axis=1)
+    scale = np.linalg.norm(run.stress, axis=1).max() + 1e-30
+    return float(np.sqrt((err ** 2).mean()) / scale), t_net
+
+
+def baseline_error(train_runs, run: Run):
+    """Error of the method without a surrogate of the history: the mean stress of
+    the training runs at the same record index (what is known before running)."""
+    S_mean = np.mean([r.stress for r in train_runs], axis=0)
+    X, Y = windows(run)
+    pred = S_mean[WINDOW - 1:]
+    err = np.linalg.norm(pred - Y, axis=1)
+    scale = np.linalg.norm(run.stress, axis=1).max() + 1e-30
+    return float(np.sqrt((err ** 2).mean()) / scale)
+
+
+def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate: float = 2.0e3,
+          records: int = 64, seed: int = 0, device: int = 0, log=print):
+    """Generates runs_per_path runs per loading path (grain counts cycling through
+    grain_counts, seeds distinct), holds out the last run of every path, trains on
+    the rest and judges the held-out runs against their PD results."""
+    # the network runs on torch's current stream (its tensors are made there);
+    # every PD context makes its own capturable stream and synchronises on return
+    stream = None
+    runs = []
+    t0 = time.perf_counter()
+    for pi, path in enumerate(LOADING_PATHS):
+        for r in range(runs_per_path):
+            ng = grain_counts[r % len(grain_counts)]
+            runs.append(rve_run(path, n_grains=ng, seed=seed + 1000 * pi + r, rate=rate, records=records,
+                                device=device, stream=stream))
+    t_data = time.perf_counter() - t0
+    held = [runs[(pi + 1) * runs_per_path - 1] for pi in range(len(LOADING_PATHS))]
+    train_runs = [r for r in runs if r not in held]
+    t0 = time.perf_counter()
+    net, xs, ys, losses = train(train_runs, epochs=epochs, seed=seed, device=device, stream=stream)
+    t_train = time.perf_counter() - t0
+    rows = []
+    for r in held:
+        err, t_net = judge(net, xs, ys, r, device=device)
+        rows.append({"path": r.path, "grains": r.n_grains, "nodes": r.nodes, "steps": r.steps,
+                     "err": err, "err_mean_history": baseline_error(train_runs, r),
+                     "pd_seconds": r.pd_seconds, "net_seconds": t_net, "speedup": r.pd_seconds / max(t_net, 1e-9)})
+    net.close()
+    errs = np.array([q["err"] for q in rows])
+    return {"runs": len(runs), "train_runs": len(train_runs), "held_out": len(held),
+            "samples": int(sum(windows(r)[0].shape[0] for r in train_runs)),
+            "data_seconds": t_data, "train_seconds": t_train, "final_loss": losses[-1],
+            "err_median": float(np.median(errs)), "err_max": float(errs.max()),
+            "frac_within_5pct": float((errs <= 0.05).mean()),
+            "speedup_median": float(np.median([q["speedup"] for q in rows])), "held": rows}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="RVE bulk-stress surrogate study on one GPU")
+    ap.add_argument("--runs-per-path", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--records", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    print(json.dumps(study(a.runs_per_path, epochs=a.epochs, records=a.records, seed=a.seed)))
