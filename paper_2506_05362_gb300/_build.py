@@ -30,9 +30,14 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, defines=(), lib_path: str = None, obj_dir: str = None) -> str:
+    """Compiles csrc/*.cu into libpd.so.  defines: extra -D macros (tuning
+    knobs); lib_path/obj_dir: build a variant elsewhere."""
+    global OBJ, LIB
+    OBJ = obj_dir or os.path.join(HERE, "_build")
+    LIB = lib_path or os.path.join(LIB_DIR, "libpd.so")
     os.makedirs(OBJ, exist_ok=True)
-    os.makedirs(LIB_DIR, exist_ok=True)
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
     cu = sorted(glob.glob(os.path.join(SRC, "*.cu")))
     headers = glob.glob(os.path.join(SRC, "*.cuh")) + [os.path.join(HERE, "..", "include", "pd.h")]
     nv = nvcc()
@@ -44,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def run(fo):
         f, o = fo
-        cmd = [nv, *ARCH, *CFLAGS, "-c", f, "-o", o]
+        cmd = [nv, *ARCH, *CFLAGS, *[f"-D{d}" for d in defines], "-c", f, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(f)}:\n{r.stderr}")

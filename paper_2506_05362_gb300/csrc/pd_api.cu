@@ -56,7 +56,7 @@ struct pd_ctx {
 
     // reductions and device scalars
     double *partials = nullptr, *react = nullptr, *disp = nullptr, *wall_pos = nullptr, *dscratch = nullptr;
-    unsigned *counter = nullptr, *derr = nullptr;
+    unsigned *counter = nullptr, *derr = nullptr, *vmax_bits = nullptr;
     int *stale = nullptr;
     int blocks = 0, lanes = 0, blocks_cap = 0;
     double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -233,6 +233,7 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     for (int a = 0; a < 3; ++a) p.b[a] = c->b[a];
     p.partials = c->partials;
     p.counter = c->counter;
+    p.vmax_bits = c->vmax_bits;
     p.err = c->derr;
     p.react = c->react;
     p.disp = c->disp;
@@ -485,6 +486,8 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->wall_pos, double, PD_MAX_WALLS * 3);
     ALLOC(c->dscratch, double, 8192);
     ALLOC(c->counter, unsigned, 1);
+    ALLOC(c->vmax_bits, unsigned, 1);
+    CK(cudaMemsetAsync(c->vmax_bits, 0, sizeof(unsigned), c->st));
     ALLOC(c->derr, unsigned, 1);
     ALLOC(c->stale, int, 1);
     CK(cudaMemsetAsync(c->react, 0, sizeof(double) * PD_MAX_WALLS * 3, c->st));

@@ -74,6 +74,7 @@ struct StepParams {
     // per-block partials and the last-block reduction
     double *partials;              // gridDim.x * PART_STRIDE
     unsigned *counter;
+    unsigned *vmax_bits;           // max |v|^2 of the step as FP32 bits (atomicMax)
     unsigned *err;
     double *react;                 // nw*3 final wall reactions
     double *disp;                  // accumulated displacement bound since last rebuild

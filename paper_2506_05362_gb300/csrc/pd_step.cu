@@ -31,6 +31,17 @@
 namespace {
 
 constexpr int STEP_THREADS = 256;
+// bonds each lane keeps in flight per loop iteration, and the minimum resident
+// blocks per SM the compiler must allow (register budget)
+#ifndef PD_INFLIGHT
+#define PD_INFLIGHT 2
+#endif
+#ifndef PD_MINB_GLOBAL
+#define PD_MINB_GLOBAL 4
+#endif
+#ifndef PD_MINB_TILED
+#define PD_MINB_TILED 2
+#endif
 
 __device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
@@ -238,17 +249,27 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
             const int i0 = (int)k0, i1 = (int)k1;
-            for (int k = i0 + gl; k < i1; k += 2 * G) {
-                const int kb = k + G;
-                const bool hasb = kb < i1;
-                const uint32_t wa = __ldg(p.brk + (k >> 5));
-                const uint32_t wb = hasb ? __ldg(p.brk + (kb >> 5)) : 0xffffffffu;
-                const int ja = __ldg(p.col + k);
-                const int jb = hasb ? __ldg(p.col + kb) : ja;
-                const float4 a0 = __ldg(p.xh4 + ja), a1 = __ldg(p.uh_in + ja), a2 = __ldg(p.ul_in + ja);
-                const float4 b0 = __ldg(p.xh4 + jb), b1 = __ldg(p.uh_in + jb), b2 = __ldg(p.ul_in + jb);
-                if (!((wa >> (k & 31)) & 1u)) bond_mixed(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                if (!((wb >> (kb & 31)) & 1u)) bond_mixed(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+            for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
+                int kk[PD_INFLIGHT], jj[PD_INFLIGHT];
+                uint32_t ww[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    kk[q] = k + q * G;
+                    const bool has = kk[q] < i1;
+                    ww[q] = has ? __ldg(p.brk + (kk[q] >> 5)) : 0xffffffffu;
+                    jj[q] = has ? __ldg(p.col + kk[q]) : jj[0];
+                }
+                float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    a0[q] = __ldg(p.xh4 + jj[q]);
+                    a1[q] = __ldg(p.uh_in + jj[q]);
+                    a2[q] = __ldg(p.ul_in + jj[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q)
+                    if (!((ww[q] >> (kk[q] & 31)) & 1u))
+                        bond_mixed(p, kk[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
             }
         } else {
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
@@ -372,47 +393,51 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
 #undef load_u
 }
 
-// Per-block partials (wall reactions, max |v|, errors) and the fixed-order
-// reduction by the last block to finish; the last block also advances the walls
-// and the skin bookkeeping.
+// Per-block partials and the finish of the step by the last block.  The max |v|
+// bound goes through one atomicMax per block (a max does not depend on order);
+// wall reactions are summed per block in group order, then by the last block
+// with one warp per component, lanes striding over the blocks and a fixed xor
+// butterfly, so the result is bitwise reproducible.  The last block also
+// advances the walls and the skin bookkeeping.
 template <int GPB>
 __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_react)[PD_MAX_WALLS * 3],
                                              double *s_vmax, unsigned &s_err, bool &s_last, unsigned err)
 {
     if (err) atomicOr(&s_err, err);
     __syncthreads();
+    const int ncomp = 3 * p.walls.nw;
     double *part = p.partials + (int64_t)blockIdx.x * PART_STRIDE;
-    if (threadIdx.x < PD_MAX_WALLS * 3) {
+    if ((int)threadIdx.x < ncomp) {
         double s = 0.0;
         for (int g = 0; g < GPB; ++g) s += s_react[g][threadIdx.x];
         part[threadIdx.x] = s;
-    } else if (threadIdx.x == PD_MAX_WALLS * 3) {
+    } else if (threadIdx.x == 32) {
         double m = 0.0;
         for (int g = 0; g < GPB; ++g) m = fmax(m, s_vmax[g]);
-        part[PD_MAX_WALLS * 3] = m;
+        if (m > 0.0) atomicMax(p.vmax_bits, __float_as_uint(__double2float_ru(m)));
         if (s_err) atomicOr(p.err, s_err);
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned prev = atomicAdd(p.counter, 1u);
+        const unsigned prev = atomicAdd(p.counter, 1u);
         s_last = (prev == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (threadIdx.x < PD_MAX_WALLS * 3) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < ncomp; c += STEP_THREADS / 32) {
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            s += ((volatile double *)p.partials)[(int64_t)b * PART_STRIDE + threadIdx.x];
-        if (threadIdx.x < 3 * p.walls.nw) p.react[threadIdx.x] = s;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(p.partials + (int64_t)b * PART_STRIDE + c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) p.react[c] = s;
     }
-    if (threadIdx.x == 32) {
-        double m = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            m = fmax(m, ((volatile double *)p.partials)[(int64_t)b * PART_STRIDE + PD_MAX_WALLS * 3]);
+    if (threadIdx.x == 0) {
+        const double vm = (double)__uint_as_float(atomicExch(p.vmax_bits, 0u));  // max |v|^2, reset
         if (p.mode == MODE_FULL) {
-            double dsp = *p.disp + p.dt * sqrt(m);
+            const double dsp = *p.disp + p.dt * sqrt(vm);
             *p.disp = dsp;
             if (2.0 * dsp >= p.skin) *p.stale = 1;
             for (int l = 0; l < p.walls.nw; ++l)
@@ -426,7 +451,7 @@ __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_rea
 // Rows in a grid-stride loop, neighbour records gathered from global memory
 // (FP64 path, and the mixed path without tiles).
 template <int G, bool MIXED>
-__global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const StepParams p)
+__global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_step(const StepParams p)
 {
     constexpr int GPB = STEP_THREADS / G;
     __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
@@ -461,7 +486,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? 4 : 2) k_step(const Step
 // then makes no global loads.  Tiles whose list exceeds the capacity take the
 // global-gather path of process_row.
 template <int G>
-__global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams p)
+__global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(const StepParams p)
 {
     constexpr int GPB = STEP_THREADS / G;
     extern __shared__ float4 s_rec[];
@@ -532,15 +557,23 @@ __global__ void __launch_bounds__(STEP_THREADS, 2) k_step_tiled(const StepParams
                 float ol[3];
                 xl_unpack(o1.w, o2.w, ol);
                 const int i0 = (int)rps[rr], i1 = (int)rps[rr + 1], kofs = (int)ka;
-                for (int k = i0 + gl; k < i1; k += 2 * G) {
-                    const int kb = k + G;
-                    const uint32_t la = lcs[k - kofs];
-                    const uint32_t lb = kb < i1 ? lcs[kb - kofs] : 0x8000u;
-                    const uint32_t ia = la & 0x7fffu, ib = lb & 0x7fffu;
-                    const float4 a0 = r0s[ia], a1 = r1s[ia], a2 = r2s[ia];
-                    const float4 b0 = r0s[ib], b1 = r1s[ib], b2 = r2s[ib];
-                    if (!(la & 0x8000u)) bond_mixed<true>(p, k, o0, o1, o2, ol, a0, a1, a2, fbx, fby, fbz);
-                    if (!(lb & 0x8000u)) bond_mixed<true>(p, kb, o0, o1, o2, ol, b0, b1, b2, fbx, fby, fbz);
+                for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
+                    uint32_t ll[PD_INFLIGHT];
+#pragma unroll
+                    for (int q = 0; q < PD_INFLIGHT; ++q) {
+                        const int kq = k + q * G;
+                        ll[q] = kq < i1 ? lcs[kq - kofs] : 0x8000u;
+                    }
+                    float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
+#pragma unroll
+                    for (int q = 0; q < PD_INFLIGHT; ++q) {
+                        const uint32_t iq = ll[q] & 0x7fffu;
+                        a0[q] = r0s[iq]; a1[q] = r1s[iq]; a2[q] = r2s[iq];
+                    }
+#pragma unroll
+                    for (int q = 0; q < PD_INFLIGHT; ++q)
+                        if (!(ll[q] & 0x8000u))
+                            bond_mixed<true>(p, k + q * G, o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
                 }
             }
             __syncwarp();
