@@ -257,8 +257,16 @@ pd_status pd_mlp_create(const int *dims, int nlayers, uint64_t seed, int device,
 /* Y (batch x dims[nlayers], FP32) = MLP(X); X (batch x dims[0], FP32) is
  * rounded to BF16 (nearest-even). Host pointers. */
 pd_status pd_mlp_forward(pd_mlp *m, const float *X, int64_t batch, float *Y);
-/* Same with device pointers (no copies). */
+/* Same with device pointers (no copies, no synchronisation; a tensor-core
+ * wait that gave up is reported by the next pd_mlp_forward). */
 pd_status pd_mlp_forward_device(pd_mlp *m, const float *X, int64_t batch, float *Y);
+/* Forward kernels: 0 (default) = the fused tcgen05 kernel (TMA-fed weights,
+ * TMEM accumulators, activations kept in shared memory across layers) when
+ * every layer is at most 256 wide on an sm_100+ GPU, else mma.sync GEMMs;
+ * 1 = mma.sync GEMMs only; 2 = the tcgen05 kernel only (a forward that it
+ * cannot run returns PD_EINVAL).  Training always uses the mma.sync kernels.
+ * PD_EINVAL for any other value. */
+pd_status pd_mlp_set_forward_path(pd_mlp *m, int path);
 /* One Adam step on the MSE loss of (X, T); *loss receives the loss before the
  * update (nullable).  Host pointers. */
 pd_status pd_mlp_train_step(pd_mlp *m, const float *X, const float *T, int64_t batch, float lr,

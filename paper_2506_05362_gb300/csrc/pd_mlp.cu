@@ -388,8 +388,13 @@ struct pd_mlp {
     float *part = nullptr;    // split-K partials
     int64_t part_cap = 0;
     float *lpart = nullptr, *dloss = nullptr;
+    unsigned *tc_err = nullptr;  // error word of the tcgen05 forward
+    int path = 0;                // 0: tcgen05 forward when the shapes allow; 1: mma.sync only
     std::vector<void *> owned;
 };
+
+int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
+                   int64_t rows, float *Y, unsigned *err, int device, cudaStream_t st);
 
 namespace {
 
@@ -482,6 +487,14 @@ pd_status ensure_cap(pd_mlp *m, int64_t rows, bool train)
 
 pd_status forward_dev(pd_mlp *m, const float *X, int64_t rows, float *Y, bool keepZ)
 {
+    if (!keepZ && m->path != 1) {
+        void *W[8];
+        const float *b[8];
+        for (int l = 0; l < m->L; ++l) { W[l] = m->Wb[l]; b[l] = m->bias[l]; }
+        if (mlp_forward_tc(m->L, m->dims, m->pad, W, b, X, rows, Y, m->tc_err, m->device, m->st) == 0)
+            return PD_OK;
+        if (m->path == 2) return mfail(m, PD_EINVAL, "the tcgen05 forward cannot run this network or GPU");
+    }
     k_to_bf16_pad<<<grid1(rows * m->pad[0]), 256, 0, m->st>>>(X, rows, m->dims[0], m->pad[0], m->H[0]);
     for (int l = 0; l < m->L; ++l) {
         GemmArgs g;
@@ -587,7 +600,7 @@ pd_status pd_mlp_create(const int *dims, int nlayers, uint64_t seed, int device,
     pd_status s = PD_OK;
     if (cudaSetDevice(device) != cudaSuccess) { cudaGetLastError(); delete m; return PD_ECUDA; }
     if ((s = malloc_(m, &m->master, off)) || (s = malloc_(m, &m->m, off)) || (s = malloc_(m, &m->v, off)) ||
-        (s = malloc_(m, &m->grad, off)) || (s = malloc_(m, &m->dloss, 4))) {
+        (s = malloc_(m, &m->grad, off)) || (s = malloc_(m, &m->dloss, 4)) || (s = malloc_(m, &m->tc_err, 1))) {
         pd_mlp_destroy(m);
         return s;
     }
@@ -597,6 +610,11 @@ pd_status pd_mlp_create(const int *dims, int nlayers, uint64_t seed, int device,
             pd_mlp_destroy(m);
             return s;
         }
+    }
+    if (cudaMemsetAsync(m->tc_err, 0, sizeof(unsigned), m->st) != cudaSuccess) {
+        cudaGetLastError();
+        pd_mlp_destroy(m);
+        return PD_ECUDA;
     }
     // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases, SplitMix64
     std::vector<float> h(off, 0.f);
@@ -676,7 +694,20 @@ pd_status pd_mlp_forward(pd_mlp *m, const float *X, int64_t batch, float *Y)
     s = forward_dev(m, m->Xf, batch, m->Y, false);
     if (s) return s;
     MCK(cudaMemcpyAsync(Y, m->Y, sizeof(float) * batch * m->dims[m->L], cudaMemcpyDeviceToHost, m->st));
+    unsigned e = 0;
+    MCK(cudaMemcpyAsync(&e, m->tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st));
     MCK(cudaStreamSynchronize(m->st));
+    if (e) {
+        cudaMemsetAsync(m->tc_err, 0, sizeof(unsigned), m->st);
+        return mfail(m, PD_ETIMEOUT, "a bounded wait of the tensor-core forward gave up");
+    }
+    return PD_OK;
+}
+
+pd_status pd_mlp_set_forward_path(pd_mlp *m, int path)
+{
+    if (!m || path < 0 || path > 2) return PD_EINVAL;
+    m->path = path;
     return PD_OK;
 }
 

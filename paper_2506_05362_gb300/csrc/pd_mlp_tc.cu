@@ -1,0 +1,415 @@
+// Fused MLP forward on the 5th-generation tensor cores (tcgen05, sm_100+).
+//
+// One persistent CTA works on 128-row tiles of the batch and keeps the tile's
+// activations in shared memory through every layer:
+//   warp 0      TMA producer: streams each layer's weights W_l [N x K] (BF16,
+//               K-major) in 64-column chunks into a 3-stage ring, 128-byte
+//               swizzle, completion counted on mbarriers;
+//   warp 1      MMA issuer: one elected thread issues tcgen05.mma (M = 128,
+//               N = layer width, K = 16 per instruction) from the activation
+//               tile A and the weight stage into a TMEM accumulator, and
+//               tcgen05.commit's to release stages and to signal the epilogue;
+//   warps 2-5   epilogue: tcgen05.ld the accumulator (one TMEM lane quarter per
+//               warp = 32 rows), add the bias, exact-erf GELU, round to BF16 and
+//               write the next layer's A tile in the swizzled layout; the last
+//               layer writes FP32 outputs.  They also stage the input tile.
+// Every mbarrier wait is bounded; on timeout the kernel records an error word,
+// stops issuing, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <string.h>
+
+#include "pd_internal.cuh"
+
+namespace tc {
+
+constexpr int TILE_M = 128;
+constexpr int KCHUNK = 64;                    // BF16 columns per 128-byte swizzle atom
+constexpr int STAGES = 3;
+constexpr int MAX_N = 256;
+constexpr int MAX_K = 256;
+constexpr int A_BYTES = TILE_M * MAX_K * 2;   // 64 KiB: 4 atoms of 128 rows x 128 B
+constexpr int W_STAGE_BYTES = MAX_N * KCHUNK * 2;  // 32 KiB
+constexpr int THREADS = 192;
+constexpr int MAX_LAYERS = 8;
+constexpr unsigned long long WAIT_NS = 1000000000ull;  // a wait gives up after 1 s
+
+struct Layer {
+    int K;        // padded input width (multiple of 16)
+    int N;        // padded output width (multiple of 16, <= 256)
+    int kchunks;  // ceil(K / 64)
+    const float *bias;  // N_pad floats
+};
+
+struct Params {
+    int L;
+    Layer layer[MAX_LAYERS];
+    const float *X;   // [rows x in_cols] FP32
+    int in_cols;
+    float *Y;         // [rows x out_cols] FP32
+    int out_cols;
+    int64_t rows;
+    unsigned *err;    // error word (1 = a wait timed out)
+};
+
+// ---- PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false once WAIT_NS of wall time have passed without the phase
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > WAIT_NS) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row groups
+// 1024 bytes apart (SBO), Blackwell descriptor version 1, layout SWIZZLE_128B
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(1u) << 16;                    // LBO (unused for swizzled K-major)
+    d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;  // SBO
+    d |= (uint64_t)1 << 46;                       // descriptor version
+    d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
+    return d;
+}
+
+// instruction descriptor: D = F32, A = B = BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+        "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+// byte offset of element (m, k) of a 128-row K-major BF16 tile in the 128-byte
+// swizzled layout: atoms of 64 columns (16 KiB), 8-row groups of 1024 bytes,
+// 16-byte chunk index XOR-ed with the row within its group
+__device__ __forceinline__ uint32_t sw128_offset(int m, int k)
+{
+    const int atom = k >> 6, c = (k & 63) >> 3, r = m & 7, g = m >> 3;
+    return (uint32_t)(atom * (TILE_M * 128) + g * 1024 + r * 128 + ((c ^ r) << 4) + ((k & 7) << 1));
+}
+
+}  // namespace tc
+
+namespace {
+
+using namespace tc;
+
+struct Maps {
+    CUtensorMap m[MAX_LAYERS];
+};
+
+__global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant__ Maps maps, const Params P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzle atoms
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;                                 // activations (A operand)
+    unsigned char *sW = base + A_BYTES;                       // weight stages
+    float *sBias = (float *)(sW + STAGES * W_STAGE_BYTES);    // MAX_N floats
+    uint64_t *full = (uint64_t *)(sBias + MAX_N);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *a_ready = acc_full + 1;
+    uint64_t *done = a_ready + 1;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(a_ready, 128);
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {  // TMEM: 256 columns x 128 lanes of FP32 accumulator
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(MAX_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int64_t ntiles = (P.rows + TILE_M - 1) / TILE_M;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int last_ph[STAGES];
+            for (int q = 0; q < STAGES; ++q) last_ph[q] = -1;
+            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x)
+                for (int l = 0; l < P.L && !s_abort; ++l)
+                    for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
+                        if (!mbar_wait(empty + s, ph ^ 1)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                        mbar_expect_tx(full + s, (uint32_t)(P.layer[l].N * KCHUNK * 2));
+                        tma_load_2d(sW + s * W_STAGE_BYTES, &maps.m[l], full + s, kc * KCHUNK, 0);
+                        last_ph[s] = (int)ph;
+                        if (++s == STAGES) { s = 0; ph ^= 1; }
+                    }
+            // no copy may still be landing in shared memory when the CTA exits
+            for (int q = 0; q < STAGES; ++q)
+                if (last_ph[q] >= 0 && !mbar_wait(full + q, (uint32_t)last_ph[q])) atomicOr(P.err, 1u);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0, aph = 0;
+            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x)
+                for (int l = 0; l < P.L && !s_abort; ++l) {
+                    if (!mbar_wait(a_ready, aph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                    aph ^= 1;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t idesc = idesc_bf16(TILE_M, P.layer[l].N);
+                    for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
+                        if (!mbar_wait(full + s, ph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a0 = smem_u32(sA + kc * (TILE_M * 128));
+                        const uint32_t b0 = smem_u32(sW + s * W_STAGE_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < KCHUNK / 16; ++kk)
+                            mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                     (kc | kk) != 0);
+                        mma_commit(empty + s);  // stage free once these MMAs completed
+                        if (++s == STAGES) { s = 0; ph ^= 1; }
+                    }
+                    mma_commit(acc_full);  // accumulator complete
+                }
+            // every MMA issued by this thread has completed before TMEM is freed
+            mma_commit(done);
+            if (!mbar_wait(done, 0)) atomicOr(P.err, 1u);
+        }
+    } else {
+        // ---------------- epilogue warps 2..5: TMEM lane quarter = warp % 4
+        const int q = warp & 3;
+        const int m = q * 32 + lane;  // row of the tile owned by this thread
+        uint32_t accph = 0;
+        bool stopped = false;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int64_t row = t * TILE_M + m;
+            // stage the input tile: BF16, zero beyond the input width and the batch
+            {
+                const int K0 = P.layer[0].K;
+                for (int k0 = 0; k0 < P.layer[0].kchunks * KCHUNK; k0 += 8) {
+                    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int k = k0 + e;
+                        const float xv = (row < P.rows && k < P.in_cols && k < K0) ? P.X[row * P.in_cols + k] : 0.f;
+                        h[e] = __float2bfloat16_rn(xv);
+                    }
+                    *(uint4 *)(sA + sw128_offset(m, k0)) = *(const uint4 *)h;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(a_ready);
+            for (int l = 0; l < P.L; ++l) {
+                const Layer &Ly = P.layer[l];
+                // the decision to stop is warp-uniform, so that no lane is left
+                // waiting in a warp-collective instruction
+                __syncwarp();
+                const bool ok = mbar_wait(acc_full, accph);
+                if (!ok) { atomicOr(P.err, 1u); s_abort = 1; }
+                accph ^= 1;
+                if (__any_sync(0xffffffffu, !ok || s_abort)) { stopped = true; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const bool last = (l == P.L - 1);
+                for (int c0 = 0; c0 < Ly.N; c0 += 32) {
+                    float v[32];
+                    __syncwarp();  // tcgen05.ld is warp-collective
+                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                    if (!last) {
+#pragma unroll
+                        for (int c8 = 0; c8 < 32; c8 += 8) {
+                            __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(gelu(v[c8 + e] + __ldg(Ly.bias + c0 + c8 + e)));
+                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = *(const uint4 *)h;
+                        }
+                    } else if (row < P.rows) {
+                        for (int e = 0; e < 32 && c0 + e < P.out_cols; ++e)
+                            P.Y[row * P.out_cols + c0 + e] = v[e] + __ldg(Ly.bias + c0 + e);
+                    }
+                }
+                if (!last) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(a_ready);
+                }
+            }
+            if (stopped) break;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    __syncwarp();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MAX_N));
+}
+
+typedef CUresult (*encode_fn_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+encode_fn_t encoder()
+{
+    static encode_fn_t fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (encode_fn_t)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t mlp_tc_smem() { return 1024 + A_BYTES + STAGES * W_STAGE_BYTES + MAX_N * 4 + 256; }
+
+// Forward of an MLP whose layers all fit the fused kernel (K, N <= 256).
+// W[l]: padded BF16 weights [pad_out x pad_in] row-major; bias[l]: pad_out
+// floats.  Returns 0 on success, -1 if the shape is unsupported or the tensor
+// maps cannot be made (the caller then uses the mma.sync kernels).
+int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
+                   int64_t rows, float *Y, unsigned *err, int device, cudaStream_t st)
+{
+    if (L < 1 || L > MAX_LAYERS || rows < 1) return -1;
+    for (int l = 0; l < L; ++l)
+        if (pad[l] > MAX_K || pad[l + 1] > MAX_N || pad[l + 1] % 16 != 0) return -1;
+    int major = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    if (major < 10) return -1;
+    encode_fn_t enc = encoder();
+    if (!enc) return -1;
+    Maps maps;
+    memset(&maps, 0, sizeof(maps));
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.L = L;
+    for (int l = 0; l < L; ++l) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)pad[l], (cuuint64_t)pad[l + 1]};
+        const cuuint64_t gstride[1] = {(cuuint64_t)pad[l] * 2};
+        const cuuint32_t box[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)pad[l + 1]};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&maps.m[l], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, W[l], gdim, gstride, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -1;
+        P.layer[l].K = pad[l];
+        P.layer[l].N = pad[l + 1];
+        P.layer[l].kchunks = (pad[l] + KCHUNK - 1) / KCHUNK;
+        P.layer[l].bias = bias[l];
+    }
+    P.X = X;
+    P.in_cols = dims[0];
+    P.Y = Y;
+    P.out_cols = dims[L];
+    P.rows = rows;
+    P.err = err;
+    const size_t smem = mlp_tc_smem();
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured = true;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int64_t ntiles = (rows + TILE_M - 1) / TILE_M;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)sms);
+    k_mlp_fwd_tc<<<grid, THREADS, smem, st>>>(maps, P);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}

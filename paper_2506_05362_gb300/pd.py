@@ -108,6 +108,7 @@ def lib():
                 "pd_mlp_set_params": (i32, [P, P]),
                 "pd_mlp_last_error": (ctypes.c_char_p, [P]),
                 "pd_mlp_destroy": (None, [P]),
+                "pd_mlp_set_forward_path": (i32, [P, i32]),
             }
             for name, (res, args) in sig.items():
                 if not hasattr(L, name):
@@ -472,6 +473,10 @@ class MLP:
         lp = P(loss_dev.data_ptr()) if loss_dev is not None else None
         _mcheck(lib().pd_mlp_train_step_device(self.h, P(X.data_ptr()), P(T.data_ptr()), X.shape[0],
                                                ctypes.c_float(lr), lp), self.h)
+
+    def set_forward_path(self, path):
+        """0: fused tcgen05 forward when possible; 1: mma.sync GEMMs only."""
+        _mcheck(lib().pd_mlp_set_forward_path(self.h, int(path)), self.h)
 
     def get_params(self):
         w = np.zeros(self.nparams, np.float32)

@@ -75,9 +75,12 @@ def grain_shape_stats(x, grain, vol):
 
 
 def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.03,
-            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None) -> Run:
+            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8) -> Run:
     """One compression run of an aggregate along ``path`` at strain rate ``rate``
-    (1/s) up to ``strain_end`` on the dominant axis, recorded ``records`` times."""
+    (1/s) up to ``strain_end`` on the dominant axis, recorded ``records`` times.
+    The step kernel's configuration is fixed (``lanes`` per node, no tiles) so
+    that a run is reproducible: the autotuner's choice would change the order of
+    the force sums, and a granular packing amplifies rounding differences."""
     from . import pd
     sc = S.aggregate(n_grains=n_grains, seed=seed, h=h, gap_cells=0.5)
     mult = np.array(LOADING_PATHS[path])
@@ -93,7 +96,7 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
         walls[2 * k, 6 + k] = vk        # lower wall moves up
         walls[2 * k + 1, 6 + k] = -vk   # upper wall moves down
     sc.walls = [S.Wall(tuple(w[0:3]), tuple(w[3:6]), tuple(w[6:9])) for w in walls]
-    ctx = pd.Context.from_scenario(sc, device=device, stream=stream)
+    ctx = pd.Context.from_scenario(sc, device=device, stream=stream, lanes=lanes, tiles=-1)
     dt = 0.8 * ctx.stable_dt()
     t_end = strain_end / (rate * max(abs(mult).max(), 1e-9))
     steps_total = max(records, int(math.ceil(t_end / dt)))

@@ -44,9 +44,12 @@ def theta(seed, scale=1.0):
     return np.concatenate(parts).astype(np.float32)
 
 
+@pytest.mark.parametrize("path", [2, 1])
 @pytest.mark.parametrize("batch", [1, 37, 128, 1003, 4096])
-def test_forward_matches_oracle(pd, batch):
+def test_forward_matches_oracle(pd, batch, path):
+    """path 2: fused tcgen05 kernel (required); path 1: mma.sync GEMMs."""
     net = pd.MLP(DIMS)
+    net.set_forward_path(path)
     th = theta(1, scale=1.7)
     net.set_params(th)
     X, _ = inputs(batch, 2)
@@ -56,9 +59,11 @@ def test_forward_matches_oracle(pd, batch):
     net.close()
 
 
-def test_forward_full_batch_sampled(pd):
+@pytest.mark.parametrize("path", [2, 1])
+def test_forward_full_batch_sampled(pd, path):
     """Inference batch 65536 in the benchmark's configuration; rows sampled for the oracle."""
     net = pd.MLP(DIMS)
+    net.set_forward_path(path)
     th = theta(3, scale=1.7)
     net.set_params(th)
     X, _ = inputs(65536, 4)
