@@ -152,10 +152,14 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
 /* Advances nsteps velocity-Verlet steps of size dt (Sec. 5.2):
  *   v += dt/2 a; u += dt v; walls move; a = (F(u) + b)/rho; v += dt/2 a,
  * where F is the bond force with breaking (Eq. peri-damage), contact and wall
- * force.  Captured and replayed as CUDA graphs.  Blocks until done.
+ * force.  Captured and replayed as CUDA graphs.  Blocks until done.  The
+ * steps run in segments of 8 graph chunks (512 steps by default); a segment
+ * whose contact list went stale or overflowed is rolled back to its own start
+ * and rerun with a shorter rebuild period or larger lists.
  * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL
  * (dt <= 0, nsteps < 0), PD_ENONFINITE / PD_EWALL (state restored to the start
- * of the call and latched), PD_ECAPACITY, PD_ECUDA. */
+ * of the segment in which it happened, so t tells how far the call got, and
+ * latched), PD_ECAPACITY, PD_ECUDA. */
 pd_status pd_step(pd_ctx *ctx, double dt, int64_t nsteps);
 
 /* Damage phi_i = 1 - intact_i / initial_i, 0 for nodes without bonds (Sec. 3.1.1;
@@ -211,8 +215,9 @@ pd_status pd_set_profiling(pd_ctx *ctx, int on);
 
 /* Timing of the last pd_step: ms_force = summed device milliseconds of the
  * fused force/update launches (only when profiling is on, else 0); ms_total =
- * device milliseconds of the whole call (event-timed on the context's stream);
- * launches = kernels launched. */
+ * device milliseconds of the call's segments (event-timed on the context's
+ * stream; attempts that were rolled back are not counted); launches = kernels
+ * launched by those segments. */
 pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, int64_t *launches);
 
 const char *pd_last_error(const pd_ctx *ctx);

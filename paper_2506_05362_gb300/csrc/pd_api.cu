@@ -844,6 +844,8 @@ static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, G
     return PD_OK;
 }
 
+#define PD_SEGMENT_CHUNKS 8  // graph chunks per rollback segment of pd_step
+
 static pd_status snapshot(pd_ctx *c, bool restore)
 {
     const size_t nb = sizeof(dbl4) * c->n, nf = sizeof(float4) * c->n;
@@ -925,14 +927,13 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
     return PD_OK;
 }
 
-pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
+// Steps [t, t + m) as one segment: a rebuild period from the current speeds, a
+// snapshot, the graph chunks, one error check.  A segment whose contact list
+// went stale or outgrew its capacity is rolled back to its own start and run
+// again (shorter rebuild period, larger lists).
+static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches, double *ms_out,
+                             double *force_ms_out)
 {
-    if (!c) return PD_EINVAL;
-    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_step before pd_build_bonds");
-    if (c->latched) return fail(c, PD_ESTATE, "a device error is latched; call pd_set_state");
-    if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return fail(c, PD_EINVAL, "dt must be > 0 and nsteps >= 0");
-    if (nsteps == 0) return PD_OK;
-    CK(cudaSetDevice(c->opt.device));
     int k;
     pd_status s = rebuild_period(c, dt, &k);
     if (s) return s;
@@ -940,10 +941,9 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
     s = snapshot(c, false);
     if (s) return s;
     for (int attempt = 0; attempt < 8; ++attempt) {
-        int64_t launches = 0;
         c->prof_used = 0;
         CK(cudaEventRecord(c->ev0, c->st));
-        s = run_steps(c, dt, nsteps, k, &launches);
+        s = run_steps(c, dt, m, k, launches);
         if (s) return s;
         CK(cudaEventRecord(c->ev1, c->st));
         unsigned e = 0;
@@ -951,16 +951,16 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
         if (s) return s;
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
-        c->last_ms = ms;
-        c->last_launches = launches;
-        c->last_force_ms = 0;
-        for (int q = 0; q + 1 < c->prof_used; q += 2) {
-            float m = 0;
-            CK(cudaEventElapsedTime(&m, c->prof_ev[q], c->prof_ev[q + 1]));
-            c->last_force_ms += m;
-        }
         if (!e) {
-            c->t += dt * (double)nsteps;
+            double fm = 0;
+            for (int q = 0; q + 1 < c->prof_used; q += 2) {
+                float x = 0;
+                CK(cudaEventElapsedTime(&x, c->prof_ev[q], c->prof_ev[q + 1]));
+                fm += x;
+            }
+            *ms_out = ms;
+            *force_ms_out = fm;
+            c->t += dt * (double)m;
             return PD_OK;
         }
         c->cur = cur0;
@@ -981,6 +981,33 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
         }
     }
     return fail(c, PD_ECAPACITY, "pd_step retried too often");
+}
+
+pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
+{
+    if (!c) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_step before pd_build_bonds");
+    if (c->latched) return fail(c, PD_ESTATE, "a device error is latched; call pd_set_state");
+    if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return fail(c, PD_EINVAL, "dt must be > 0 and nsteps >= 0");
+    if (nsteps == 0) return PD_OK;
+    CK(cudaSetDevice(c->opt.device));
+    // a rollback costs at most one segment of work
+    const int64_t seg = (int64_t)PD_SEGMENT_CHUNKS * c->opt.graph_chunk;
+    c->last_ms = 0;
+    c->last_force_ms = 0;
+    c->last_launches = 0;
+    for (int64_t done = 0; done < nsteps;) {
+        const int64_t m = std::min(seg, nsteps - done);
+        int64_t launches = 0;
+        double ms = 0, fm = 0;
+        pd_status s = run_segment(c, dt, m, &launches, &ms, &fm);
+        if (s) return s;
+        c->last_ms += ms;
+        c->last_force_ms += fm;
+        c->last_launches += launches;
+        done += m;
+    }
+    return PD_OK;
 }
 
 

@@ -148,10 +148,50 @@ __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
     return r;
 }
 
+// Component c = gl of the mixed-path Verlet update of one row.
+__device__ __forceinline__ unsigned epilogue_component(const StepParams &p, int64_t row, int c, float Fx, float Fy,
+                                                       float Fz, const float4 &uh, const float4 &ul,
+                                                       const float4 &vh, const float4 &vl, float &vc2)
+{
+    unsigned err = 0;
+    const float F = c == 0 ? Fx : (c == 1 ? Fy : Fz);
+    if (!isfinite(F)) err |= PDE_NONFINITE;
+    const float a = (F + p.bf[c]) * p.inv_rho_f;
+    float *afc = (float *)(p.af + row) + c;
+    if (p.mode == MODE_FORCES) {
+        *afc = a;
+        if (p.F_out) ((double *)(p.F_out + row))[c] = (double)F;
+        return err;
+    }
+    const df hdt{p.hdt_hi, p.hdt_lo};
+    const float vhc = c == 0 ? vh.x : (c == 1 ? vh.y : vh.z);
+    const float vlc = c == 0 ? vl.x : (c == 1 ? vl.y : vl.z);
+    df v = df_add(df{vhc, vlc}, df_mul_f(hdt, a));
+    if (p.mode == MODE_FULL) {
+        v = df_add(v, df_mul_f(hdt, a));
+        const float uhc = c == 0 ? uh.x : (c == 1 ? uh.y : uh.z);
+        const float ulc = c == 0 ? ul.x : (c == 1 ? ul.y : ul.z);
+        const df u = df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v));
+        ((float *)(p.uh_out + row))[c] = u.hi;
+        ((float *)(p.ul_out + row))[c] = u.lo;
+        if (c == 0) {  // packed x_lo travels with the record
+            ((float *)(p.uh_out + row))[3] = uh.w;
+            ((float *)(p.ul_out + row))[3] = ul.w;
+        }
+        vc2 = v.hi * v.hi;
+        if (!isfinite(v.hi) || !isfinite(u.hi)) err |= PDE_NONFINITE;
+    } else {
+        *afc = a;
+    }
+    ((float *)(p.vh + row))[c] = v.hi;
+    ((float *)(p.vl + row))[c] = v.lo;
+    return err;
+}
+
 // Mixed-path epilogue spread over the group: lane c (0, 1, 2) updates component
-// c of the node's acceleration, velocity and displacement (same arithmetic as
-// epilogue_mixed).  Every lane of the warp calls it (inactive rows included) so
-// that the shuffles that broadcast a wall force are uniform.
+// c of the node's acceleration, velocity and displacement.  Every lane of the
+// warp calls it (inactive rows included) so that the shuffles that broadcast a
+// wall force and sum |v|^2 are uniform.
 template <int G>
 __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t row, bool active, int gl, float Fx,
                                                    float Fy, float Fz, const float4 &oxh, const float4 &uh,
@@ -188,40 +228,12 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
         Fy += __shfl_sync(0xffffffffu, wy, leader);
         Fz += __shfl_sync(0xffffffffu, wz, leader);
     }
-    if (!active || gl >= 3) return err;
-    const int c = gl;
-    const float F = c == 0 ? Fx : (c == 1 ? Fy : Fz);
-    if (!isfinite(F)) err |= PDE_NONFINITE;
-    const float a = (F + p.bf[c]) * p.inv_rho_f;
-    float *afc = (float *)(p.af + row) + c;
-    if (p.mode == MODE_FORCES) {
-        *afc = a;
-        if (p.F_out) ((double *)(p.F_out + row))[c] = (double)F;
-        return err;
-    }
-    const df hdt{p.hdt_hi, p.hdt_lo};
-    const float vhc = c == 0 ? vh.x : (c == 1 ? vh.y : vh.z);
-    const float vlc = c == 0 ? vl.x : (c == 1 ? vl.y : vl.z);
-    df v = df_add(df{vhc, vlc}, df_mul_f(hdt, a));
-    if (p.mode == MODE_FULL) {
-        v = df_add(v, df_mul_f(hdt, a));
-        const float uhc = c == 0 ? uh.x : (c == 1 ? uh.y : uh.z);
-        const float ulc = c == 0 ? ul.x : (c == 1 ? ul.y : ul.z);
-        const df u = df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v));
-        ((float *)(p.uh_out + row))[c] = u.hi;
-        ((float *)(p.ul_out + row))[c] = u.lo;
-        if (c == 0) {  // packed x_lo travels with the record
-            ((float *)(p.uh_out + row))[3] = uh.w;
-            ((float *)(p.ul_out + row))[3] = ul.w;
-        }
-        // |v|^2 <= 3 max_c v_c^2: a bound is all the skin bookkeeping needs
-        vmax2 = fmaxf(vmax2, 3.f * v.hi * v.hi);
-        if (!isfinite(v.hi) || !isfinite(u.hi)) err |= PDE_NONFINITE;
-    } else {
-        *afc = a;
-    }
-    ((float *)(p.vh + row))[c] = v.hi;
-    ((float *)(p.vl + row))[c] = v.lo;
+    float vc2 = 0.f;  // v_c^2 of this lane's component (0 on lanes 3.. and inactive rows)
+    if (active && gl < 3) err |= epilogue_component(p, row, gl, Fx, Fy, Fz, uh, ul, vh, vl, vc2);
+    // |v|^2 of the row: lanes 0..3 of the group form an aligned quad (G >= 4)
+    float v2 = vc2 + __shfl_xor_sync(0xffffffffu, vc2, 1);
+    v2 += __shfl_xor_sync(0xffffffffu, v2, 2);
+    vmax2 = fmaxf(vmax2, v2);
     return err;
 }
 
