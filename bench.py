@@ -1,7 +1,7 @@
 """Benchmark of the PeriDEM hot path on one GB300 (replicas per GPU under torchrun).
 
 A step is one velocity-Verlet step of the notched steel plate (Kalthoff-Winkler
-geometry, 200 x 100 x 9 mm, h = 1 mm, 178,200 nodes, delta = 4h, ~45 M directed
+geometry, 200 x 100 x 9 mm, h = 1 mm, 178,200 nodes, delta = 4h, 36.4 M directed
 bonds): bond force with breaking, contact search and force, kick/drift.  Inputs
 are resident in HBM when the timed region starts; the working set (~0.3 GB)
 exceeds L2.  Prints one JSON line.
