@@ -175,6 +175,17 @@ pd_status pd_damage(pd_ctx *ctx, double *phi);
  * is negative (reading of "bulk strength" in Sec. 6.4/6.5). */
 pd_status pd_bulk_stress(pd_ctx *ctx, const double *area, double sigma[6], double *wall_force);
 
+/* The same stress from the wall forces averaged over time: every step adds
+ * dt * R_l (the reaction of its force evaluation) to an impulse J_l; this call
+ * returns sigma of the mean forces J_l / T, the mean forces themselves
+ * (wall_force, nullable, nw*3) and T, the time covered (span, nullable), then
+ * zeroes J and T.  pd_create, pd_set_walls and pd_set_state also zero them.
+ * The paper reports wall forces over time (Sec. 6.4); the average over a
+ * window is the macroscopic stress of a representative volume without the
+ * contact chatter of single steps.  All zeros while T = 0. */
+pd_status pd_bulk_stress_mean(pd_ctx *ctx, const double *area, double sigma[6], double *wall_force,
+                              double *span);
+
 /* Number of directed bonds B (each undirected bond counted twice). */
 pd_status pd_num_bonds(pd_ctx *ctx, int64_t *B);
 

@@ -65,7 +65,7 @@ def lib():
             L.orc_contact_pairs.restype = i64
             L.orc_forces.argtypes = [P, P, P, P, P, P]
             L.orc_forces.restype = i32
-            L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P]
+            L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P, P]
             L.orc_step.restype = i32
             L.orc_stable_dt.argtypes = [P]
             L.orc_stable_dt.restype = f64
@@ -152,6 +152,8 @@ class Model:
         self.broken = np.zeros(max(len(self.col), 1), np.uint8)
         self.F = np.zeros((n, 3))
         self.react = np.zeros((self.walls.shape[0], 3))
+        self.impulse = np.zeros((self.walls.shape[0], 3))   # sum of dt * react over steps
+        self.impulse_span = 0.0
         self.t = 0.0
         self.err = 0
         self.acc = np.zeros((n, 3))
@@ -190,8 +192,9 @@ class Model:
     def step(self, dt, nsteps=1):
         self.err |= lib().orc_step(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.acc),
                                    _p(self.broken), _p(self.wall_pos), dt, nsteps, _p(self.F),
-                                   _p(self.react))
+                                   _p(self.react), _p(self.impulse))
         self.t += dt * nsteps
+        self.impulse_span += dt * nsteps
         return self
 
     def stable_dt(self):
@@ -214,6 +217,16 @@ class Model:
 
     def bulk_stress(self, areas):
         return bulk_stress(self.walls[:, 0:3], self.react, areas)
+
+    def bulk_stress_mean(self, areas, reset=True):
+        """Bulk stress from the wall forces averaged over the steps since the last
+        reset (impulse / span), the mean wall forces and the span; then resets."""
+        mean = self.impulse / self.impulse_span if self.impulse_span > 0 else np.zeros_like(self.impulse)
+        out = (bulk_stress(self.walls[:, 0:3], mean, areas), mean.copy(), self.impulse_span)
+        if reset:
+            self.impulse[:] = 0.0
+            self.impulse_span = 0.0
+        return out
 
 
 def bulk_stress(normals, react, areas):

@@ -511,10 +511,12 @@ int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, ui
  *   v <- v + (dt/2) a;  u <- u + dt v;  walls advance w <- w + dt v_wall;
  *   a <- (F(u) + b) / rho;  v <- v + (dt/2) a.
  * Returns the OR of the force error bits; react holds the wall forces of the
- * last evaluation.
+ * last evaluation.  impulse (nw*3, nullable) accumulates dt * react after every
+ * step's force evaluation: the wall impulse over the steps, rectangle rule on
+ * the evaluations at the ends of the steps.
  */
 int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *broken,
-             double *wall_pos, double dt, int64_t nsteps, double *F, double *react)
+             double *wall_pos, double dt, int64_t nsteps, double *F, double *react, double *impulse)
 {
     int64_t n = P->n;
     int err = 0;
@@ -528,6 +530,8 @@ int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *b
             for (int a = 0; a < 3; ++a)
                 wall_pos[3 * l + a] = wall_pos[3 * l + a] + dt * P->walls[9 * l + 6 + a];
         err |= orc_forces(P, u, wall_pos, broken, F, react);
+        if (impulse)
+            for (int l = 0; l < 3 * P->nw; ++l) impulse[l] += dt * react[l];
         for (int64_t i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) {
                 acc[3 * i + a] = (F[3 * i + a] + P->b[a]) / P->rho;

@@ -64,6 +64,7 @@ struct pd_ctx {
     int64_t *tile_ptr = nullptr;
     int32_t *ulist = nullptr;
     uint16_t *lcol = nullptr, *lrow = nullptr;
+    int32_t *colf = nullptr;  // col with the broken flag in bit 31 (mixed path; bitset is the master)
     int64_t ntiles = 0;
     int tile_rows = 64, tile_cap = 0, tile_slot_cap = 0;
     size_t tile_smem = 0;
@@ -83,6 +84,7 @@ struct pd_ctx {
 
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double impulse_span = 0;       // time covered by the wall impulses since their reset
     double last_ms = 0, last_force_ms = 0;
     int64_t last_launches = 0;
     bool profiling = false;
@@ -189,6 +191,7 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.rowptr = c->rowptr;
     p.col = c->col;
     p.brk = c->brk;
+    p.colf = c->colf;
     p.xh4 = mixed ? c->xh4 : nullptr;
     p.xl4 = mixed ? c->xl4 : nullptr;
     p.uh_in = mixed ? c->uh[in] : nullptr;
@@ -236,6 +239,7 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.vmax_bits = c->vmax_bits;
     p.err = c->derr;
     p.react = c->react;
+    p.impulse = c->wall_pos + PD_MAX_WALLS * 3;
     p.disp = c->disp;
     p.skin = skin_of(c);
     p.stale = c->stale;
@@ -309,6 +313,13 @@ pd_status status_of(pd_ctx *c, unsigned e)
 
 // Force evaluation at the current state (breaking applies).  Retries once after
 // growing the candidate list.
+// zero the wall impulses and the time they cover
+cudaError_t reset_impulse(pd_ctx *c)
+{
+    c->impulse_span = 0;
+    return cudaMemsetAsync(c->wall_pos + PD_MAX_WALLS * 3, 0, sizeof(double) * PD_MAX_WALLS * 3, c->st);
+}
+
 pd_status eval_forces(pd_ctx *c)
 {
     for (int attempt = 0; attempt < 4; ++attempt) {
@@ -483,7 +494,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->partials, double, (int64_t)c->blocks_cap * PART_STRIDE);
     ALLOC(c->react, double, PD_MAX_WALLS * 3);
     ALLOC(c->disp, double, 1);
-    ALLOC(c->wall_pos, double, PD_MAX_WALLS * 3);
+    ALLOC(c->wall_pos, double, PD_MAX_WALLS * 6);  // wall points, then the wall impulses
     ALLOC(c->dscratch, double, 8192);
     ALLOC(c->counter, unsigned, 1);
     ALLOC(c->vmax_bits, unsigned, 1);
@@ -711,6 +722,12 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     ALLOC(c->snap_brk, uint32_t, c->nwords);
     ALLOC(c->stage_b, uint8_t, B + 16);
     CK(cudaMemsetAsync(c->brk, 0, sizeof(uint32_t) * c->nwords, c->st));
+    // mixed path: neighbour index with the broken flag in bit 31, one word per slot
+    release(c, c->colf);
+    if (c->opt.precision == PD_MIXED) {
+        ALLOC(c->colf, int32_t, B + 16);
+        sync_colf_flags(c->brk, c->col, B, c->colf, c->st);
+    }
     CK(cudaGetLastError());
     s = sync(c);
     if (s) return s;
@@ -750,6 +767,7 @@ pd_status pd_set_walls(pd_ctx *c, int nw, const pd_wall *w)
     }
     CK(cudaSetDevice(c->opt.device));
     CK(cudaMemcpyAsync(c->wall_pos, pos, sizeof(pos), cudaMemcpyHostToDevice, c->st));
+    CK(reset_impulse(c));
     pd_status s = sync(c);
     if (s) return s;
     c->walls = ws;
@@ -865,9 +883,10 @@ static pd_status snapshot(pd_ctx *c, bool restore)
         CK(cp(c->snap_acc, c->acc, nb));
     }
     CK(cp(c->snap_brk, c->brk, sizeof(uint32_t) * c->nwords));
-    CK(cp(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 3));
+    CK(cp(c->dscratch + 4096, c->wall_pos, sizeof(double) * PD_MAX_WALLS * 6));
     if (restore) {
         if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
+        if (c->colf) sync_colf_flags(c->brk, c->col, c->B, c->colf, c->st);
         CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
     }
     return PD_OK;
@@ -961,6 +980,7 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches,
             *ms_out = ms;
             *force_ms_out = fm;
             c->t += dt * (double)m;
+            c->impulse_span += dt * (double)m;
             return PD_OK;
         }
         c->cur = cur0;
@@ -1022,17 +1042,13 @@ pd_status pd_damage(pd_ctx *c, double *phi)
     return sync(c);
 }
 
-pd_status pd_bulk_stress(pd_ctx *c, const double *area, double sigma[6], double *wall_force)
+// Voigt stress (xx, yy, zz, yz, xz, xy) from wall forces R (nw*3) on areas:
+// the wall pushes on the aggregate with -R_l over A_l, whose outward normal is
+// m_l = -n_l; sigma e_k = -(R_l / A_l) sign(m_l . e_k) for the dominant axis k
+// of m_l, averaged over the walls of each axis, then symmetrised (Sec. 6.4).
+static pd_status stress_of(pd_ctx *c, const double *area, const double *R, double sigma[6])
 {
-    if (!c || !sigma) return PD_EINVAL;
     const int nw = c->walls.nw;
-    double R[PD_MAX_WALLS * 3] = {0};
-    if (nw) {
-        if (!area) return fail(c, PD_EINVAL, "area is required when walls are set");
-        CK(cudaMemcpyAsync(R, c->react, sizeof(double) * 3 * nw, cudaMemcpyDeviceToHost, c->st));
-        pd_status s = sync(c);
-        if (s) return s;
-    }
     double S[3][3] = {{0}}, cnt[3] = {0, 0, 0};
     for (int l = 0; l < nw; ++l) {
         if (!(area[l] > 0)) return fail(c, PD_EINVAL, "wall areas must be positive");
@@ -1052,8 +1068,49 @@ pd_status pd_bulk_stress(pd_ctx *c, const double *area, double sigma[6], double 
         for (int b2 = 0; b2 < 3; ++b2) T[a][b2] = 0.5 * (S[a][b2] + S[b2][a]);
     sigma[0] = T[0][0]; sigma[1] = T[1][1]; sigma[2] = T[2][2];
     sigma[3] = T[1][2]; sigma[4] = T[0][2]; sigma[5] = T[0][1];
+    return PD_OK;
+}
+
+pd_status pd_bulk_stress(pd_ctx *c, const double *area, double sigma[6], double *wall_force)
+{
+    if (!c || !sigma) return PD_EINVAL;
+    const int nw = c->walls.nw;
+    double R[PD_MAX_WALLS * 3] = {0};
+    if (nw) {
+        if (!area) return fail(c, PD_EINVAL, "area is required when walls are set");
+        CK(cudaMemcpyAsync(R, c->react, sizeof(double) * 3 * nw, cudaMemcpyDeviceToHost, c->st));
+        pd_status s = sync(c);
+        if (s) return s;
+    }
+    pd_status s = stress_of(c, area, R, sigma);
+    if (s) return s;
     if (wall_force)
         for (int q = 0; q < 3 * nw; ++q) wall_force[q] = R[q];
+    return PD_OK;
+}
+
+pd_status pd_bulk_stress_mean(pd_ctx *c, const double *area, double sigma[6], double *wall_force, double *span)
+{
+    if (!c || !sigma) return PD_EINVAL;
+    const int nw = c->walls.nw;
+    double J[PD_MAX_WALLS * 3] = {0}, R[PD_MAX_WALLS * 3] = {0};
+    if (nw && !area) return fail(c, PD_EINVAL, "area is required when walls are set");
+    const double T = c->impulse_span;
+    CK(cudaSetDevice(c->opt.device));
+    if (nw) {
+        CK(cudaMemcpyAsync(J, c->wall_pos + PD_MAX_WALLS * 3, sizeof(double) * 3 * nw, cudaMemcpyDeviceToHost,
+                           c->st));
+        CK(reset_impulse(c));
+        pd_status s = sync(c);
+        if (s) return s;
+    }
+    c->impulse_span = 0;
+    for (int q = 0; q < 3 * nw; ++q) R[q] = T > 0 ? J[q] / T : 0.0;
+    pd_status s = stress_of(c, area, R, sigma);
+    if (s) return s;
+    if (wall_force)
+        for (int q = 0; q < 3 * nw; ++q) wall_force[q] = R[q];
+    if (span) *span = T;
     return PD_OK;
 }
 
@@ -1210,11 +1267,13 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
             CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
             bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
             if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
+            if (c->colf) sync_colf_flags(c->brk, c->col, c->B, c->colf, c->st);
         }
     }
     if (t) c->t = *t;
     c->latched = 0;
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
+    CK(reset_impulse(c));
     pd_status s = sync(c);
     if (s) return s;
     if (c->bonds_ready) return eval_forces(c);

@@ -427,6 +427,14 @@ __global__ void k_sync_lcol_flags(const uint32_t *__restrict__ brk, int64_t B, u
         lcol[k] = (uint16_t)((lcol[k] & 0x7fffu) | (((brk[k >> 5] >> (k & 31)) & 1u) << 15));
 }
 
+// neighbour index with the slot's broken flag in bit 31
+__global__ void k_sync_colf_flags(const uint32_t *__restrict__ brk, const int32_t *__restrict__ col, int64_t B,
+                                  int32_t *colf)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < B; k += (int64_t)gridDim.x * blockDim.x)
+        colf[k] = (int32_t)((uint32_t)col[k] | (((brk[k >> 5] >> (k & 31)) & 1u) << 31));
+}
+
 // ---- state conversion -----------------------------------------------------------
 __global__ void k_to_caller(const dbl4 *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, double *out)
 {
@@ -673,4 +681,9 @@ void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B
 void sync_lcol_flags(const uint32_t *brk, int64_t B, uint16_t *lcol, cudaStream_t st)
 {
     k_sync_lcol_flags<<<grid_of(B), 256, 0, st>>>(brk, B, lcol);
+}
+
+void sync_colf_flags(const uint32_t *brk, const int32_t *col, int64_t B, int32_t *colf, cudaStream_t st)
+{
+    if (B > 0) k_sync_colf_flags<<<grid_of(B), 256, 0, st>>>(brk, col, B, colf);
 }

@@ -57,3 +57,4 @@ void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B
                  uint64_t *keys, uint64_t *keys_alt, int64_t *flag, int64_t *pos, int64_t *tmp, int32_t *ulist,
                  int64_t *tile_ptr, uint16_t *lcol, uint16_t *lrow, cudaStream_t st);
 void sync_lcol_flags(const uint32_t *brk, int64_t B, uint16_t *lcol, cudaStream_t st);
+void sync_colf_flags(const uint32_t *brk, const int32_t *col, int64_t B, int32_t *colf, cudaStream_t st);

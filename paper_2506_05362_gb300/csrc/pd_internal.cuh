@@ -77,6 +77,7 @@ struct StepParams {
     unsigned *vmax_bits;           // max |v|^2 of the step as FP32 bits (atomicMax)
     unsigned *err;
     double *react;                 // nw*3 final wall reactions
+    double *impulse;               // nw*3 sum over steps of dt * react (not in MODE_FORCES)
     double *disp;                  // accumulated displacement bound since last rebuild
     double skin;
     int *stale;                    // set when 2*disp >= skin
@@ -87,6 +88,7 @@ struct StepParams {
     const int64_t *tile_ptr;
     const int32_t *ulist;
     uint16_t *lcol;                // bit 15 = broken (kept in step with brk)
+    int32_t *colf;                 // mixed path: col with bit 31 = broken (kept in step with brk)
     const uint16_t *lrow;
 };
 

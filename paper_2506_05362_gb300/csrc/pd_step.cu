@@ -121,14 +121,51 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
     const bool brk = p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f);
     if (brk) {
         atomicOr(p.brk + (k >> 5), 1u << (k & 31));
-        // the tiled path also carries the flag in bit 15 of the 16-bit local index
+        // the tiled path also carries the flag in bit 15 of the 16-bit local index,
+        // the global mixed path in bit 31 of the index
         if (FLAG) atomicOr((unsigned int *)(p.lcol) + (k >> 1), 0x8000u << (16 * (int)(k & 1)));
+        if (p.colf) atomicOr((unsigned int *)p.colf + k, 0x80000000u);
     } else {
         const float g = p.cf * a0.w * s * ry;
         fbx = fmaf(g, yx, fbx);
         fby = fmaf(g, yy, fby);
         fbz = fmaf(g, yz, fbz);
     }
+}
+
+// One slot of the global mixed path.  raw = neighbour index with the broken flag
+// in bit 31.  The bond is evaluated whatever the flag and its force masked, so
+// that intact and broken slots take the same instruction stream; a bond that
+// breaks now flags its slot in both copies of the bond memory.
+__device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, int32_t raw, const float4 &o0,
+                                                   const float4 &o1, const float4 &o2, const float *ol,
+                                                   const float4 &a0, const float4 &a1, const float4 &a2, float &fbx,
+                                                   float &fby, float &fbz)
+{
+    float al[3];
+    xl_unpack(a1.w, a2.w, al);
+    const float xx = (a0.x - o0.x) + (al[0] - ol[0]);
+    const float xy = (a0.y - o0.y) + (al[1] - ol[1]);
+    const float xz = (a0.z - o0.z) + (al[2] - ol[2]);
+    const float ex = (a1.x - o1.x) + (a2.x - o2.x);
+    const float ey = (a1.y - o1.y) + (a2.y - o2.y);
+    const float ez = (a1.z - o1.z) + (a2.z - o2.z);
+    const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
+    const float L2 = fmaf(xx, xx, fmaf(xy, xy, xz * xz));
+    const float y2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz));
+    const float num = fmaf(ex, xx + yx, fmaf(ey, xy + yy, ez * (xz + yz)));
+    const float rL = rsqrtf(L2), ry = rsqrtf(y2);
+    const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
+    const bool intact = raw >= 0;
+    const bool brk = intact && (p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f));
+    if (brk) {
+        p.colf[k] = (int32_t)((uint32_t)raw | 0x80000000u);
+        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+    }
+    const float g = (intact && !brk) ? p.cf * a0.w * s * ry : 0.f;
+    fbx = fmaf(g, yx, fbx);
+    fby = fmaf(g, yy, fby);
+    fbz = fmaf(g, yz, fbz);
 }
 
 // u of node i in FP64: the double-float state of the mixed path, or the FP64 array
@@ -262,26 +299,25 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             xl_unpack(o1.w, o2.w, ol);
             const int i0 = (int)k0, i1 = (int)k1;
             for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
-                int kk[PD_INFLIGHT], jj[PD_INFLIGHT];
-                uint32_t ww[PD_INFLIGHT];
+                int32_t raw[PD_INFLIGHT];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
-                    kk[q] = k + q * G;
-                    const bool has = kk[q] < i1;
-                    ww[q] = has ? __ldg(p.brk + (kk[q] >> 5)) : 0xffffffffu;
-                    jj[q] = has ? __ldg(p.col + kk[q]) : jj[0];
+                    // a slot past the row end reuses the first slot's node, flagged
+                    const int kq = k + q * G;
+                    raw[q] = q == 0 ? __ldg(p.colf + kq)
+                                    : (kq < i1 ? __ldg(p.colf + kq) : (int32_t)((uint32_t)raw[0] | 0x80000000u));
                 }
                 float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
-                    a0[q] = __ldg(p.xh4 + jj[q]);
-                    a1[q] = __ldg(p.uh_in + jj[q]);
-                    a2[q] = __ldg(p.ul_in + jj[q]);
+                    const int j = raw[q] & 0x7fffffff;
+                    a0[q] = __ldg(p.xh4 + j);
+                    a1[q] = __ldg(p.uh_in + j);
+                    a2[q] = __ldg(p.ul_in + j);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)
-                    if (!((ww[q] >> (kk[q] & 31)) & 1u))
-                        bond_mixed(p, kk[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
+                    bond_mixed_flagged(p, k + q * G, raw[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
             }
         } else {
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
@@ -444,7 +480,10 @@ __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_rea
         for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(p.partials + (int64_t)b * PART_STRIDE + c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) p.react[c] = s;
+        if (lane == 0) {
+            p.react[c] = s;
+            if (p.mode != MODE_FORCES) p.impulse[c] = dadd(p.impulse[c], dmul(p.dt, s));
+        }
     }
     if (threadIdx.x == 0) {
         const double vm = (double)__uint_as_float(atomicExch(p.vmax_bits, 0u));  // max |v|^2, reset

@@ -85,6 +85,7 @@ def lib():
                 "pd_step": (i32, [P, f64, i64]),
                 "pd_damage": (i32, [P, P]),
                 "pd_bulk_stress": (i32, [P, P, P, P]),
+                "pd_bulk_stress_mean": (i32, [P, P, P, P, P]),
                 "pd_num_bonds": (i32, [P, P]),
                 "pd_bonds": (i32, [P, P, P]),
                 "pd_contacts": (i32, [P, P, P]),
@@ -230,6 +231,15 @@ def pd_bulk_stress(h, areas, nw):
     ar = None if areas is None else _f64(areas)
     _check(lib().pd_bulk_stress(h, _ptr(ar), _ptr(s), _ptr(wf)), h)
     return s, wf[:nw]
+
+
+def pd_bulk_stress_mean(h, areas, nw):
+    s = np.zeros(6)
+    wf = np.zeros((max(nw, 1), 3))
+    span = ctypes.c_double()
+    ar = None if areas is None else _f64(areas)
+    _check(lib().pd_bulk_stress_mean(h, _ptr(ar), _ptr(s), _ptr(wf), ctypes.byref(span)), h)
+    return s, wf[:nw], span.value
 
 
 def pd_num_bonds(h):
@@ -378,6 +388,10 @@ class Context:
 
     def bulk_stress(self, areas=None):
         return pd_bulk_stress(self.h, areas, self.nw)
+
+    def bulk_stress_mean(self, areas=None):
+        """(sigma, mean wall forces, span) over the steps since the last call; resets."""
+        return pd_bulk_stress_mean(self.h, areas, self.nw)
 
     def bonds(self):
         return pd_bonds(self.h, self.n)

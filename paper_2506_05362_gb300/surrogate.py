@@ -116,7 +116,8 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
         hi_t = np.array([pos[1, 0], pos[3, 1], pos[5, 2]])
         L = hi_t - lo_t
         areas = np.array([L[1] * L[2]] * 2 + [L[0] * L[2]] * 2 + [L[0] * L[1]] * 2)
-        sig, _ = ctx.bulk_stress(areas)
+        # stress of the wall forces averaged over the record interval
+        sig, _, _ = ctx.bulk_stress_mean(areas)
         strain[r, :3] = (L - L0) / L0
         stress[r] = sig
         phi = ctx.damage()

@@ -165,6 +165,15 @@ def test_sphere_trajectory_200_steps(pd, precision, tol, tiles):
     sig, wf = ctx.bulk_stress([sc.wall_area] * 2)
     assert rel_l2(wf, ref.react) <= max(tol, 1e-9)
     assert np.allclose(sig, ref.bulk_stress([sc.wall_area] * 2), rtol=max(tol, 1e-9))
+    # wall forces averaged over the 200 steps (impulse / time)
+    sig_m, wf_m, span = ctx.bulk_stress_mean([sc.wall_area] * 2)
+    osig_m, owf_m, ospan = ref.bulk_stress_mean([sc.wall_area] * 2)
+    assert span == pytest.approx(ospan, rel=1e-14)
+    assert np.abs(owf_m).max() > 0
+    assert rel_l2(wf_m, owf_m) <= max(tol, 1e-9)
+    assert np.allclose(sig_m, osig_m, rtol=max(tol, 1e-9))
+    # the call resets the accumulator
+    assert ctx.bulk_stress_mean([sc.wall_area] * 2)[2] == 0.0
     ctx.close()
 
 

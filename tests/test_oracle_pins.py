@@ -374,3 +374,35 @@ def test_bulk_stress_sign_convention():
     s = oracle.bulk_stress(normals, react, [2.0, 2.0])
     assert s[2] == pytest.approx(-2.5)
     assert np.all(s[[0, 1, 3, 4, 5]] == 0)
+
+
+def test_wall_impulse_balances_momentum():
+    """Newton's second law over a window of steps: bond and contact forces cancel
+    in sum_i V_i F_i, so the body's momentum changes only by the wall forces.
+    Velocity Verlet integrates them with the trapezoid rule, the accumulated
+    impulse J with the rectangle rule at the step ends; hence
+    rho sum_i V_i (v_N - v_0) = -(J + dt (R_0 - R_N) / 2), summed over walls."""
+    sc = S.sphere()
+    m = oracle.Model.from_scenario(sc)
+    dt = 0.8 * m.stable_dt()
+    m.init()
+    m.step(dt, 60)          # walls reach the sphere
+    m.bulk_stress_mean([1.0, 1.0])   # reset the accumulator
+    R0 = m.react.sum(0)
+    p0 = sc.material.rho * (m.v * sc.vol[:, None]).sum(0)
+    m.step(dt, 120)
+    RN = m.react.sum(0)
+    p1 = sc.material.rho * (m.v * sc.vol[:, None]).sum(0)
+    J = m.impulse.sum(0)
+    assert np.abs(m.impulse).max() > 0, "walls should touch the sphere"
+    lhs = p1 - p0
+    rhs = -(J + 0.5 * dt * (R0 - RN))
+    assert np.abs(lhs).max() > 0.1 * np.abs(J).max()   # the momentum really changed
+    assert np.abs(lhs - rhs).max() < 1e-9 * np.abs(m.impulse).sum()
+    J_walls = m.impulse.copy()
+    sig, mean, span = m.bulk_stress_mean([sc.wall_area] * 2)
+    assert span == pytest.approx(120 * dt, rel=1e-15)
+    assert np.allclose(mean, J_walls / span, rtol=1e-15, atol=0)
+    assert np.all(m.impulse == 0) and m.impulse_span == 0.0
+    # the mean stress is the stress of the mean wall forces
+    assert np.allclose(sig, oracle.bulk_stress(m.walls[:, 0:3], mean, [sc.wall_area] * 2), rtol=0, atol=0)
