@@ -51,6 +51,7 @@ struct pd_ctx {
     int64_t cand_cap = 0;
     uint32_t *gk = nullptr, *gk2 = nullptr, *gv = nullptr, *gv2 = nullptr, *gstart = nullptr, *gend = nullptr;
     uint64_t *gcell = nullptr;
+    float4 *gpf = nullptr;  // FP32 positions of the grid's nodes (distance prefilter)
     uint32_t nbuckets = 0;
     int64_t *tmp = nullptr;  // scan / radix scratch for n-sized problems
 
@@ -275,7 +276,7 @@ void enqueue_rebuild(pd_ctx *c, int in)
     for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];
     const double cut = c->mat.contact_radius + skin_of(c);
     grid_build(g, c->x4, u, c->n, cut * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
-               c->gend, c->gcell, c->tmp, c->st);
+               c->gend, c->gcell, c->tmp, c->gpf, c->st);
     cand_count(c->x4, u, c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_cnt, c->st);
     scan_exclusive_i64(c->cand_cnt, c->cand_ptr, c->n, c->tmp, c->st);
     cand_fill(c->x4, u, c->grain, c->rowptr, c->col, c->n, g, cut, c->cand_ptr, c->cand, c->cand_cap,
@@ -483,6 +484,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->gstart, uint32_t, nb);
     ALLOC(c->gend, uint32_t, nb);
     ALLOC(c->gcell, uint64_t, n);
+    ALLOC(c->gpf, float4, n);
     ALLOC(c->cand_ptr, int64_t, n + 1);
     ALLOC(c->cand_cnt, int64_t, n + 1);
     CK(cudaMemsetAsync(c->cand_ptr, 0, sizeof(int64_t) * (n + 1), c->st));
@@ -615,7 +617,7 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     GridView g;
     for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];
     grid_build(g, c->x4, nullptr, n, horizon * (1.0 + 1e-7), c->nbuckets, c->gk, c->gk2, c->gv, c->gv2, c->gstart,
-               c->gend, c->gcell, c->tmp, c->st);
+               c->gend, c->gcell, c->tmp, c->gpf, c->st);
     int64_t *cnt;
     ALLOC(cnt, int64_t, n + 1);
     ALLOC(c->rowptr, int64_t, n + 1);

@@ -79,7 +79,7 @@ __global__ void k_gather_nodes(const uint32_t *__restrict__ perm, int64_t n, con
 // ---- grid --------------------------------------------------------------------
 __global__ void k_cell_keys(const dbl4 *__restrict__ x4, const dbl4 *__restrict__ u4, int64_t n, double lx,
                             double ly, double lz, double cs, uint32_t mask, uint32_t *key, uint32_t *val,
-                            uint64_t *cell)
+                            uint64_t *cell, float4 *pf)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         dbl4 a = x4[i];
@@ -90,6 +90,8 @@ __global__ void k_cell_keys(const dbl4 *__restrict__ x4, const dbl4 *__restrict_
         }
         int cx = grid_coord(px, lx, cs), cy = grid_coord(py, ly, cs), cz = grid_coord(pz, lz, cs);
         cell[i] = grid_pack(cx, cy, cz);
+        const float fx = (float)dsub(px, lx), fy = (float)dsub(py, ly), fz = (float)dsub(pz, lz);
+        pf[i] = make_float4(fx, fy, fz, fmaxf(fabsf(fx), fmaxf(fabsf(fy), fabsf(fz))));
         key[i] = grid_hash(cx, cy, cz, mask);
         val[i] = (uint32_t)i;
     }
@@ -138,8 +140,10 @@ __global__ void k_bonds(const dbl4 *__restrict__ x4, const int32_t *__restrict__
                         const int32_t *__restrict__ perm, int64_t n, GridView g, double delta2, FilterSet f,
                         int64_t *cnt, const int64_t *__restrict__ off, uint64_t *keys, int sh)
 {
+    const float deltaf = (float)sqrt(delta2);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const dbl4 a = x4[i];
+        const float4 pi = g.pf[i];
         const int gi = grain[i];
         const int32_t ci = perm[i];
         const uint64_t pc = g.cell[i];
@@ -158,9 +162,17 @@ __global__ void k_bonds(const dbl4 *__restrict__ x4, const int32_t *__restrict__
                     for (uint32_t t = s; t < e; ++t) {
                         const int32_t j = (int32_t)g.node[t];
                         if (j == i || g.cell[j] != want || grain[j] != gi) continue;
+                        // FP32 decides pairs clearly inside or outside the horizon;
+                        // the exact FP64 predicate decides the band between
+                        const float4 pj = g.pf[j];
+                        const float d2f = pf_dist2(pi, pj), sl = pf_slack(deltaf, pi, pj);
+                        const float hi = deltaf + sl, lo = deltaf - sl;
+                        if (!(d2f < hi * hi)) continue;
                         const dbl4 bj = x4[j];
-                        const double r2 = sq3(dsub(bj.x, a.x), dsub(bj.y, a.y), dsub(bj.z, a.z));
-                        if (!(r2 < delta2)) continue;
+                        if (!(d2f < lo * lo)) {
+                            const double r2 = sq3(dsub(bj.x, a.x), dsub(bj.y, a.y), dsub(bj.z, a.z));
+                            if (!(r2 < delta2)) continue;
+                        }
                         if (f.nf) {
                             const double pa[3] = {a.x, a.y, a.z}, pb[3] = {bj.x, bj.y, bj.z};
                             const bool drop = (ci < perm[j]) ? filter_drops(pa, pb, f) : filter_drops(pb, pa, f);
@@ -204,9 +216,9 @@ __global__ void k_cand(const dbl4 *__restrict__ x4, const dbl4 *__restrict__ u4,
         if (off[n] > cap) atomicOr(err, (unsigned)PDE_CAPACITY);
     }
     if (FILL && off[n] > cap) return;
+    const float cutf = (float)sqrt(cut2);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const dbl4 a = x4[i], ua = u4[i];
-        const double px = dadd(a.x, ua.x), py = dadd(a.y, ua.y), pz = dadd(a.z, ua.z);
+        const float4 pi = g.pf[i];
         const int gi = grain[i];
         const uint64_t pc = g.cell[i];
         const int cx = (int)((pc >> 42) & 0x1fffff) - 1048576, cy = (int)((pc >> 21) & 0x1fffff) - 1048576,
@@ -224,10 +236,11 @@ __global__ void k_cand(const dbl4 *__restrict__ x4, const dbl4 *__restrict__ u4,
                     for (uint32_t t = s; t < e; ++t) {
                         const int32_t j = (int32_t)g.node[t];
                         if (j == i || g.cell[j] != want) continue;
-                        const dbl4 bj = x4[j], uj = u4[j];
-                        const double r2 = sq3(dsub(dadd(bj.x, uj.x), px), dsub(dadd(bj.y, uj.y), py),
-                                              dsub(dadd(bj.z, uj.z), pz));
-                        if (!(r2 < cut2)) continue;
+                        // a superset of the pairs closer than cut: the step kernel
+                        // applies the exact FP64 contact predicate
+                        const float4 pj = g.pf[j];
+                        const float lim = cutf + pf_slack(cutf, pi, pj);
+                        if (!(pf_dist2(pi, pj) < lim * lim)) continue;
                         if (FILL) {
                             int2 c;
                             c.x = j;
@@ -527,11 +540,12 @@ void gather_nodes(const uint32_t *order, int64_t n, const double *x, const doubl
 
 void grid_build(GridView &g, const dbl4 *x4, const dbl4 *u4, int64_t n, double cs, uint32_t nbuckets,
                 uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint32_t *start,
-                uint32_t *end, uint64_t *cell, int64_t *tmp, cudaStream_t st)
+                uint32_t *end, uint64_t *cell, int64_t *tmp, float4 *pf, cudaStream_t st)
 {
     g.cs = cs;
     g.mask = nbuckets - 1;
-    k_cell_keys<<<grid_of(n), 256, 0, st>>>(x4, u4, n, g.lo[0], g.lo[1], g.lo[2], cs, g.mask, keys, vals, cell);
+    k_cell_keys<<<grid_of(n), 256, 0, st>>>(x4, u4, n, g.lo[0], g.lo[1], g.lo[2], cs, g.mask, keys, vals, cell,
+                                            pf);
     int bits = 0;
     while ((1u << bits) < nbuckets) ++bits;
     uint32_t *k = keys, *ka = keys_alt, *v = vals, *va = vals_alt;
@@ -543,6 +557,7 @@ void grid_build(GridView &g, const dbl4 *x4, const dbl4 *u4, int64_t n, double c
     g.end = end;
     g.node = v;
     g.cell = cell;
+    g.pf = pf;
 }
 
 void bonds_count(const dbl4 *x4, const int32_t *grain, const int32_t *perm, int64_t n, const GridView &g,

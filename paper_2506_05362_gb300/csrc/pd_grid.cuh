@@ -18,7 +18,22 @@ struct GridView {
     const uint32_t *end;          // bucket -> one past last
     const uint32_t *node;         // sorted entries -> node index
     const uint64_t *cell;         // node -> packed cell coordinates
+    const float4 *pf;             // node -> FP32 (p - lo), .w = max |component| (prefilter)
 };
+
+// Conservative FP32 distance test.  pf = fl32(p - lo) carries an error of at
+// most 2^-24 |pf|_inf per component; a difference of two such points and its
+// squared norm in FP32 stay within r + 1.04e-7 (m_i + m_j) + 1.5e-7 r of the
+// exact distance r (m = max |component|).  The bound below is four times that.
+__device__ __forceinline__ float pf_slack(float cut, const float4 &a, const float4 &b)
+{
+    return cut * 1e-6f + 4e-7f * (a.w + b.w);
+}
+__device__ __forceinline__ float pf_dist2(const float4 &a, const float4 &b)
+{
+    const float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
 
 __device__ __forceinline__ int grid_coord(double p, double lo, double cs)
 {
@@ -42,4 +57,4 @@ __device__ __forceinline__ uint32_t grid_hash(int cx, int cy, int cz, uint32_t m
 // Build step kernels (pd_grid.cu).
 void grid_build(GridView &g, const dbl4 *x4, const dbl4 *u4, int64_t n, double cs, uint32_t nbuckets,
                 uint32_t *keys, uint32_t *keys_alt, uint32_t *vals, uint32_t *vals_alt, uint32_t *start,
-                uint32_t *end, uint64_t *cell, int64_t *tmp, cudaStream_t st);
+                uint32_t *end, uint64_t *cell, int64_t *tmp, float4 *pf, cudaStream_t st);

@@ -34,7 +34,7 @@ constexpr int STEP_THREADS = 256;
 // bonds each lane keeps in flight per loop iteration, and the minimum resident
 // blocks per SM the compiler must allow (register budget)
 #ifndef PD_INFLIGHT
-#define PD_INFLIGHT 2
+#define PD_INFLIGHT 3
 #endif
 #ifndef PD_MINB_GLOBAL
 #define PD_MINB_GLOBAL 4
