@@ -6,10 +6,11 @@ an MLP learns the bulk stress of small star-grain aggregates from their recent
 strain history and descriptors, from data that the peridynamic hot path itself
 generates, and is judged against a fresh full PD run.
 
-Data: an aggregate in a box of six rigid walls is strained at a constant rate
-along one of 8 loading paths (wall velocities per axis); every ``stride`` steps
-the macroscopic strain (from wall positions) and bulk stress (pd_bulk_stress)
-are recorded.  A sample is a window of 16 strain records (6 Voigt components,
+Data: an aggregate in a box of six rigid walls is compressed isotropically to a
+confining pressure, then strained at a constant rate along one of 8 loading paths
+(wall velocities per axis); every ``stride`` steps the macroscopic strain (from
+wall positions) and the bulk stress of the wall forces averaged over the interval
+(pd_bulk_stress_mean) are recorded.  A sample is a window of 16 strain records (6 Voigt components,
 the shear ones are zero for axis-aligned walls) plus 13 descriptors at the
 window end (109 inputs); the target is the stress (6) at the window end.
 Inputs and targets are standardised with the training set's statistics.
@@ -19,6 +20,7 @@ tensor-core kernels (pd_mlp_*); this module only arranges arrays.
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 import time
 from dataclasses import dataclass
@@ -52,9 +54,12 @@ class Run:
     strain: np.ndarray      # (T, 6)
     stress: np.ndarray      # (T, 6) Pa
     desc: np.ndarray        # (T, 13)
-    pd_seconds: float       # device+host time of the PD steps
+    pd_seconds: float       # device+host time of the PD steps (pre-compression included)
     steps: int
     nodes: int
+    precompress_steps: int = 0
+    p_confine: float = 0.0  # mean wall stress reached by the pre-compression, Pa
+    sf_confine: float = 0.0 # solid fraction at the end of the pre-compression
 
 
 def grain_shape_stats(x, grain, vol):
@@ -74,30 +79,70 @@ def grain_shape_stats(x, grain, vol):
     return np.array(req), np.array(sph), np.array(asp)
 
 
-def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.03,
-            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8) -> Run:
-    """One compression run of an aggregate along ``path`` at strain rate ``rate``
-    (1/s) up to ``strain_end`` on the dominant axis, recorded ``records`` times.
+def _box(pos):
+    """(lo, hi) corners of the six-wall box from the wall points (order -x, +x, -y, +y, -z, +z)."""
+    lo = np.array([pos[0, 0], pos[2, 1], pos[4, 2]])
+    hi = np.array([pos[1, 0], pos[3, 1], pos[5, 2]])
+    return lo, hi
+
+
+def _areas(L):
+    return np.array([L[1] * L[2]] * 2 + [L[0] * L[2]] * 2 + [L[0] * L[1]] * 2)
+
+
+def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.04,
+            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8,
+            p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 40000,
+            G0: float = None) -> Run:
+    """One RVE run: an aggregate in a box of six rigid walls is first compressed
+    isotropically at strain rate ``rate`` until the mean wall stress reaches the
+    confining pressure ``p_confine`` (a connected contact network; the solid
+    fraction is capped at ``sf_max``), then strained along ``path`` at ``rate`` up
+    to ``strain_end`` on the dominant axis, recorded ``records`` times.  Strain is
+    measured from the box at the end of the pre-compression; the recorded stress
+    is that of the wall forces averaged over each record interval.
+
     The step kernel's configuration is fixed (``lanes`` per node, no tiles) so
     that a run is reproducible: the autotuner's choice would change the order of
     the force sums, and a granular packing amplifies rounding differences."""
     from . import pd
     sc = S.aggregate(n_grains=n_grains, seed=seed, h=h, gap_cells=0.5)
+    if G0 is not None:  # fracture energy of the grains (glass: 135 J/m^2)
+        sc.material = dataclasses.replace(sc.material, G0=G0)
     mult = np.array(LOADING_PATHS[path])
     walls = S.walls_array(sc.walls)
-    lo = np.array([walls[0, 3], walls[2, 4], walls[4, 5]])
-    hi = np.array([walls[1, 3], walls[3, 4], walls[5, 5]])
+    lo, hi = _box(walls[:, 3:6])
     L0 = hi - lo
-    # wall order from the generator: -x, +x, -y, +y, -z, +z (normals into the box)
-    for k in range(3):
-        vk = 0.5 * mult[k] * rate * L0[k]
-        walls[2 * k, 6:9] = 0.0
-        walls[2 * k + 1, 6:9] = 0.0
-        walls[2 * k, 6 + k] = vk        # lower wall moves up
-        walls[2 * k + 1, 6 + k] = -vk   # upper wall moves down
+    walls[:, 6:9] = 0.0
+    for k in range(3):  # isotropic pre-compression: every wall moves inward
+        walls[2 * k, 6 + k] = 0.5 * rate * L0[k]
+        walls[2 * k + 1, 6 + k] = -0.5 * rate * L0[k]
     sc.walls = [S.Wall(tuple(w[0:3]), tuple(w[3:6]), tuple(w[6:9])) for w in walls]
     ctx = pd.Context.from_scenario(sc, device=device, stream=stream, lanes=lanes, tiles=-1)
     dt = 0.8 * ctx.stable_dt()
+    vol_sum = sc.vol.sum()
+    t0 = time.perf_counter()
+    chunk, pc_steps, p_mean, sf = 64, 0, 0.0, 0.0
+    while pc_steps < max_precompress:
+        ctx.step(dt, chunk)
+        pc_steps += chunk
+        lo, hi = _box(ctx.get_walls())
+        L = hi - lo
+        sig, _, _ = ctx.bulk_stress_mean(_areas(L))
+        p_mean = -float(np.mean(sig[:3]))
+        sf = vol_sum / np.prod(L)
+        if p_mean >= p_confine or sf >= sf_max:
+            break
+    # loading path from the compacted box
+    lo, hi = _box(ctx.get_walls())
+    Lp = hi - lo
+    walls[:, 3:6] = ctx.get_walls()
+    walls[:, 6:9] = 0.0
+    for k in range(3):
+        vk = 0.5 * mult[k] * rate * Lp[k]
+        walls[2 * k, 6 + k] = vk        # lower wall moves up
+        walls[2 * k + 1, 6 + k] = -vk   # upper wall moves down
+    ctx.set_walls(walls)
     t_end = strain_end / (rate * max(abs(mult).max(), 1e-9))
     steps_total = max(records, int(math.ceil(t_end / dt)))
     stride = max(1, steps_total // records)
@@ -106,29 +151,25 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
     strain = np.zeros((records, 6))
     stress = np.zeros((records, 6))
     desc = np.zeros((records, N_DESC))
-    vol_sum = sc.vol.sum()
-    B = max(ctx.B, 1)
-    t0 = time.perf_counter()
+    rp, _ = ctx.bonds()
+    nb0 = np.diff(rp).astype(np.float64)
+    B = max(float(nb0.sum()), 1.0)
     for r in range(records):
         ctx.step(dt, stride)
-        pos = ctx.get_walls()
-        lo_t = np.array([pos[0, 0], pos[2, 1], pos[4, 2]])
-        hi_t = np.array([pos[1, 0], pos[3, 1], pos[5, 2]])
+        lo_t, hi_t = _box(ctx.get_walls())
         L = hi_t - lo_t
-        areas = np.array([L[1] * L[2]] * 2 + [L[0] * L[2]] * 2 + [L[0] * L[1]] * 2)
-        # stress of the wall forces averaged over the record interval
-        sig, _, _ = ctx.bulk_stress_mean(areas)
-        strain[r, :3] = (L - L0) / L0
+        sig, _, _ = ctx.bulk_stress_mean(_areas(L))
+        strain[r, :3] = (L - Lp) / Lp
         stress[r] = sig
         phi = ctx.damage()
-        _, _, broken, _ = ctx.get_state()
         ncont = len(ctx.contacts())
         desc[r] = [vol_sum / np.prod(L), static[0], static[1], static[2], static[3], phi.mean(),
-                   broken.sum() / B, static[4], ncont / n_grains, static[5], static[6], L.max() / L.min(),
-                   rate * abs(mult).max()]
+                   float((phi * nb0).sum()) / B, static[4], ncont / n_grains, static[5], static[6],
+                   L.max() / L.min(), rate * abs(mult).max()]
     pd_seconds = time.perf_counter() - t0
     ctx.close()
-    return Run(path, n_grains, seed, strain, stress, desc, pd_seconds, stride * records, sc.n)
+    return Run(path, n_grains, seed, strain, stress, desc, pd_seconds, pc_steps + stride * records, sc.n,
+               pc_steps, p_mean, sf)
 
 
 def windows(run: Run):
