@@ -44,7 +44,8 @@ class Problem(ctypes.Structure):
                 ("c", ctypes.c_double), ("s0", ctypes.c_double), ("Kn", ctypes.c_double),
                 ("Rc", ctypes.c_double), ("rho", ctypes.c_double),
                 ("break_mode", ctypes.c_int), ("contact", ctypes.c_int), ("nw", ctypes.c_int),
-                ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3), ("frozen", ctypes.c_int)]
+                ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3), ("frozen", ctypes.c_int),
+                ("beta_d", ctypes.c_double)]
 
 
 def lib():
@@ -63,7 +64,7 @@ def lib():
             L.orc_bonds_cells.restype = i64
             L.orc_contact_pairs.argtypes = [P, P, P, i32, P]
             L.orc_contact_pairs.restype = i64
-            L.orc_forces.argtypes = [P, P, P, P, P, P]
+            L.orc_forces.argtypes = [P, P, P, P, P, P, P]
             L.orc_forces.restype = i32
             L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P, P]
             L.orc_step.restype = i32
@@ -141,6 +142,7 @@ class Model:
         self.P.rowptr, self.P.col = _p(self.rowptr), _p(self.col)
         self.P.c, self.P.s0, self.P.Kn, self.P.Rc, self.P.rho = self.c, self.s0, self.Kn, m.contact_radius, m.rho
         self.P.break_mode = m.break_mode
+        self.P.beta_d = getattr(m, "beta_d", 0.0)
         self.P.contact = 1 if contact else 0
         self.P.nw = self.walls.shape[0]
         self.P.walls = _p(self.walls)
@@ -178,7 +180,7 @@ class Model:
         """F at the current state, sets react; returns F.  Applies breaking unless
         frozen, which evaluates with the current bond memory unchanged."""
         self.P.frozen = 1 if frozen else 0
-        self.err |= lib().orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.wall_pos),
+        self.err |= lib().orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.wall_pos),
                                      _p(self.broken), _p(self.F), _p(self.react))
         self.P.frozen = 0
         return self.F

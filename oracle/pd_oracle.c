@@ -15,6 +15,7 @@
  *   Sec. 3.1.1, Table "peri-combined", bond memory gamma,
  *   Eq. (peri-damage)                                      -> breaking, damage
  *   Sec. 3.2, Eq. (repulsive-force)                        -> inter-grain contact
+ *   Sec. 3.3, Eq. (damping-force)                          -> normal contact damping
  *   Sec. 5 "Self-contact forces", Eq. (peri-damage-self)    -> same-grain contact
  *   Sec. 4.1 "Contact between peridynamic body and wall"    -> wall force
  *   Sec. 3.5 Eq. (motion), Sec. 5.2 velocity-Verlet        -> time integration
@@ -313,6 +314,7 @@ typedef struct {
     const double *walls;    /* nw*9: inward normal, point at t=0, velocity */
     double b[3];            /* body force density, N/m^3 */
     int frozen;             /* 1: evaluate with the given bond memory, no new breaking */
+    double beta_d;          /* normal damping coefficient (Sec. 3.3), N s / m^7; 0 = none */
 } orc_problem;
 
 /* slot of j in row i (binary search on the ascending row), or -1 */
@@ -401,6 +403,13 @@ int64_t orc_contact_pairs(const orc_problem *P, const double *u, const uint8_t *
  *    - same grain and |x_j - x_i| < R_c (a once-bonded pair):
  *        F_i += c min(0, (|d| - |xi|) / |xi|) e V_j
  *    Reading: |d| = 0 has no direction and contributes nothing.
+ *    Normal damping (Sec. 3.3, Eq. damping-force), when v is given and
+ *    beta_d != 0, on the same pairs: F_i += beta_d ((v_j - v_i) . e) e V_j.
+ *    Reading: the printed law -beta_d (v/|v| . e) e with v = v_j - v_i pushes
+ *    approaching points towards each other, while the text says the force acts
+ *    against e for them; and its unit-length v gives a force of magnitude
+ *    beta_d cos(angle) at any speed, while the text calls the law linear and a
+ *    viscoelastic spring.  The dissipative linear law is used.
  * 3. Walls (Sec. 4.1), for each wall l with inward unit normal n_l and current
  *    point w_l: d = (p_i - w_l) . n_l.  If d < R_c the ball of radius R_c
  *    around p_i overlaps the wall in a spherical cap of volume
@@ -411,13 +420,20 @@ int64_t orc_contact_pairs(const orc_problem *P, const double *u, const uint8_t *
  *    the cap and makes the force attractive near d = R_c; the printed
  *    centroid formula is only consistent with (2 R_c + d).  d <= -R_c (a node
  *    a whole radius behind the wall) is undefined and flagged ORC_ERR_WALL.
+ *    Damping at the wall (Sec. 4.1: e -> e_l, V_y -> |S|, p_y -> c_l, the cap
+ *    moving with the wall velocity v_w): F_i += beta_d ((v_w - v_i) . n_l) n_l |S|,
+ *    which the wall's reaction includes.
+ * v (nullable) is the velocity the damping sees; orc_step passes the half-step
+ * velocity v(t + dt/2) of velocity Verlet (the velocity at hand when F(t + dt)
+ * is evaluated).
  * With P->frozen set, step 1 keeps the given bond memory (Eq. peri-damage with
  * gamma prescribed) so that two evaluations can be compared on one bond set.
  * Returns error bits.  react (nw*3) receives the total force on each wall.
  */
-int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, uint8_t *broken,
+int orc_forces(const orc_problem *P, const double *u, const double *v, const double *wall_pos, uint8_t *broken,
                double *F, double *react)
 {
+    const int damp = v != NULL && P->beta_d != 0.0;
     int64_t n = P->n;
     int err = 0;
     double *p = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -474,6 +490,14 @@ int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, ui
                     mag = P->c * (sr < 0.0 ? sr : 0.0);
                 }
                 for (int a = 0; a < 3; ++a) F[3 * i + a] += mag * (d[a] / dn) * P->vol[j];
+                if (damp) {
+                    /* Eq. (damping-force), read as the linear dissipative law
+                     * beta_d ((v_j - v_i) . e) e with e = d / |d| */
+                    double e[3], w = 0.0;
+                    for (int a = 0; a < 3; ++a) e[a] = d[a] / dn;
+                    for (int a = 0; a < 3; ++a) w += (v[3 * j + a] - v[3 * i + a]) * e[a];
+                    for (int a = 0; a < 3; ++a) F[3 * i + a] += P->beta_d * w * e[a] * P->vol[j];
+                }
             }
         }
         orc_grid_free(&g);
@@ -493,6 +517,14 @@ int orc_forces(const orc_problem *P, const double *u, const double *wall_pos, ui
             double q = P->Rc * P->Rc - d * d;
             double zbar = (ORC_PI / 4.0) * q * q / Vcap;
             double mag = P->Kn * (P->Rc - zbar) * Vcap;
+            if (damp) {
+                /* the wall's points in the cap move with the wall: the pair law
+                 * with e = -n, V_y = |S_l| (Sec. 4.1); ((v_w - v_i) . e) e is the
+                 * same along n */
+                double w = 0.0;
+                for (int a = 0; a < 3; ++a) w += (P->walls[9 * l + 6 + a] - v[3 * i + a]) * nl[a];
+                mag += P->beta_d * w * Vcap;
+            }
             for (int a = 0; a < 3; ++a) {
                 F[3 * i + a] += mag * nl[a];
                 react[3 * l + a] -= mag * nl[a] * P->vol[i];
@@ -529,7 +561,8 @@ int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *b
         for (int l = 0; l < P->nw; ++l)
             for (int a = 0; a < 3; ++a)
                 wall_pos[3 * l + a] = wall_pos[3 * l + a] + dt * P->walls[9 * l + 6 + a];
-        err |= orc_forces(P, u, wall_pos, broken, F, react);
+        /* velocity-dependent forces see the half-step velocity v(t + dt/2) */
+        err |= orc_forces(P, u, v, wall_pos, broken, F, react);
         if (impulse)
             for (int l = 0; l < 3 * P->nw; ++l) impulse[l] += dt * react[l];
         for (int64_t i = 0; i < n; ++i)

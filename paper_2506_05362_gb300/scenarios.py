@@ -41,6 +41,7 @@ class Material:
     contact_factor: float = 5.0  # K_n = contact_factor * c / delta
     constants: int = 0      # 0 = self-consistent c, s0; 1 = paper's table values
     break_mode: int = 0     # 0 = tension s > s0; 1 = |s| > s0
+    beta_d: float = 0.0     # normal contact damping (Sec. 3.3), N s / m^7; 0 = none
 
 
 @dataclass

@@ -62,6 +62,16 @@ class Run:
     sf_confine: float = 0.0 # solid fraction at the end of the pre-compression
 
 
+def damping_coefficient(material, horizon: float, volume: float, zeta: float) -> float:
+    """beta_d (Sec. 3.3) giving a damping ratio ``zeta`` to two nodes of ``volume`` in
+    contact: their relative motion has stiffness K_n V^2 (K_n = f_c 18 K / (pi delta^5),
+    K = 2E/3), reduced mass rho V / 2 and damping beta_d V^2, so critical damping is
+    beta_d = sqrt(2 K_n rho / V)."""
+    K = 2.0 * material.E / 3.0
+    Kn = material.contact_factor * 18.0 * K / (math.pi * horizon ** 5)
+    return zeta * math.sqrt(2.0 * Kn * material.rho / volume)
+
+
 def grain_shape_stats(x, grain, vol):
     """Equivalent radius, sphericity proxy (r_eq / r_max) and aspect ratio
     (sqrt of the extreme covariance eigenvalues) of every grain."""

@@ -406,3 +406,93 @@ def test_wall_impulse_balances_momentum():
     assert np.all(m.impulse == 0) and m.impulse_span == 0.0
     # the mean stress is the stress of the mean wall forces
     assert np.allclose(sig, oracle.bulk_stress(m.walls[:, 0:3], mean, [sc.wall_area] * 2), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("zeta", [0.1, 0.3, 0.6])
+def test_damped_contact_restitution(zeta):
+    """Normal damping (Sec. 3.3) on two single-node grains meeting head-on: spring
+    K_n (R_c - |d|) V V plus dashpot beta_d (v_rel . e) V V is the damped linear
+    oscillator with damping ratio zeta = beta_d V^2 / (2 sqrt(k m_red)): contact
+    lasts pi / (omega_0 sqrt(1 - zeta^2)) and the rebound keeps the fraction
+    exp(-zeta pi / sqrt(1 - zeta^2)) of the approach speed."""
+    Rc, V, delta = 1e-4, 1e-12, 1e-3
+    K, c, s0, Kn = oracle.constants(72e9, 135, delta)
+    rho = 2440.0
+    k = Kn * V * V
+    mred = rho * V / 2
+    beta = zeta * 2 * math.sqrt(k * mred) / (V * V)
+    mat = S.Material(E=72e9, rho=rho, G0=135, contact_radius=Rc, beta_d=beta)
+    vel = 0.05
+    w0 = math.sqrt(k / mred)
+    td = math.pi / (w0 * math.sqrt(1 - zeta ** 2))
+    dt = td / 4000
+    x = np.array([[0.0, 0, 0], [Rc + 40 * dt * vel, 0, 0]])
+    m = model_for(x, mat, delta, grain=np.array([0, 1], np.int32), vol=np.full(2, V),
+                  v0=np.array([[vel, 0, 0], [-vel, 0, 0]]))
+    m.init()
+    inside, t_in, t_out, t = False, None, None, 0.0
+    for _ in range(40000):
+        m.step(dt)
+        t += dt
+        d = (x[1, 0] + m.u[1, 0]) - (x[0, 0] + m.u[0, 0])
+        if not inside and d < Rc:
+            inside, t_in = True, t
+        if inside and d >= Rc:
+            t_out = t
+            break
+    assert t_out is not None
+    assert t_out - t_in == pytest.approx(td, rel=2e-3)
+    e = math.exp(-zeta * math.pi / math.sqrt(1 - zeta ** 2))
+    assert -m.v[0, 0] / vel == pytest.approx(e, rel=3e-3)
+    assert m.v[0, 0] + m.v[1, 0] == pytest.approx(0.0, abs=1e-12)   # momentum
+
+
+def test_damping_forces_conserve_momentum_and_dissipate():
+    """Pair damping is antisymmetric (sum_i V_i F_i = 0) and never does positive
+    work on the relative motion: sum_i V_i F_d,i . v_i <= 0."""
+    h = 1e-4
+    a = lattice_block(5, 5, 4, h, jitter=0.05, seed=1)
+    b = lattice_block(5, 5, 4, h, jitter=0.05, seed=2) + np.array([0.2 * h, 0.3 * h, 3.55 * h])
+    x = np.concatenate([a, b])
+    grain = np.repeat(np.array([0, 1], np.int32), len(a))
+    vol = np.full(len(x), h ** 3)
+    mat = S.Material(E=72e9, rho=2440, G0=135, contact_radius=0.6 * h, beta_d=1e9)
+    m = model_for(x, mat, 3 * h, grain=grain, vol=vol)
+    rng = np.random.default_rng(9)
+    m.v = rng.normal(0, 1.0, (m.n, 3))
+    sc = S.Scenario(name="pair", x=x, vol=vol, grain=grain, v0=m.v, material=mat, horizon=3 * h, h=h)
+    F1 = m.forces(frozen=False).copy()
+    pairs = len(m.contact_pairs())
+    assert pairs > 0
+    m.P.beta_d = 0.0
+    F0 = m.forces(frozen=True).copy()
+    Fd = F1 - F0
+    assert np.abs(Fd).max() > 0
+    tot = (Fd * sc.vol[:, None]).sum(0)
+    assert np.abs(tot).max() < 1e-12 * np.abs(Fd * sc.vol[:, None]).sum()
+    assert (Fd * sc.vol[:, None] * m.v).sum() < 0
+
+
+def test_wall_damping_closed_form():
+    """Damping at a wall (Sec. 4.1 substitution): a node at distance d moving with
+    v feels beta_d ((v_w - v) . n) n |S| more than without damping, with the cap
+    volume |S| = (pi/3)(R_c - d)^2 (2 R_c + d)."""
+    Rc = 1e-4
+    x = np.array([[0.0, 0.0, 0.4 * Rc]])
+    vw = np.array([0.0, 0.0, 0.3])
+    walls = np.array([[0, 0, 1.0, 0, 0, 0, *vw]])
+    v = np.array([[0.2, -0.1, -1.5]])
+    d = 0.4 * Rc
+    S_cap = math.pi / 3 * (Rc - d) ** 2 * (2 * Rc + d)
+    mat = S.Material(E=72e9, rho=2440, G0=135, contact_radius=Rc)
+    m = model_for(x, mat, 3e-4, walls=walls, vol=np.full(1, 1e-12), v0=v)
+    F0 = m.forces().copy()
+    # a coefficient that makes damping a tenth of the repulsion here
+    beta = 0.1 * abs(F0[0, 2]) / (abs((vw - v[0])[2]) * S_cap)
+    m.P.beta_d = beta
+    F1 = m.forces().copy()
+    R1 = m.react.copy()
+    expect = beta * ((vw - v[0]) @ np.array([0, 0, 1.0])) * S_cap
+    assert expect > 0   # the wall pushes a node that approaches it
+    assert F1[0] - F0[0] == pytest.approx([0, 0, expect], rel=1e-12, abs=1e-12 * abs(expect))
+    assert R1[0] == pytest.approx(-F1[0] * 1e-12, rel=1e-12)
