@@ -61,7 +61,15 @@ enum { PD_MIXED = 0,  /* FP32 bond arithmetic; xi and eta from double-float pair
  * constants = 1: the paper's table row (c = 12E/(pi delta^4 (1-nu)),
  * s0 = sqrt(5 pi G0/(12 E delta))).  K_n = contact_factor * 18K/(pi delta^5)
  * (Sec. 3.2).  break_mode = 0 breaks a bond when s > s0 (definition of the bond
- * memory gamma); 1 when |s| > s0 (the sentence before the table). */
+ * memory gamma); 1 when |s| > s0 (the sentence before the table).
+ * beta_d: normal contact damping (Sec. 3.3, Eq. damping-force), N s/m^7, 0 =
+ * none.  Every contact pair adds beta_d ((v_j - v_i) . e) e V_j to the force
+ * density of i (e = unit vector from p_i to p_j), and every node within R_c of
+ * a wall adds beta_d ((v_wall - v_i) . n) n |S| (the wall substitution of
+ * Sec. 4.1, |S| the cap volume), which the wall reaction includes.  The
+ * velocity is the half-step velocity of velocity Verlet (pd_forces: the
+ * current velocity).  Reading: the printed law pushes approaching points
+ * together and normalises v; the dissipative linear law is used. */
 typedef struct {
     double E;               /* Young's modulus, Pa (> 0) */
     double rho;             /* density, kg/m^3 (> 0) */
@@ -70,6 +78,7 @@ typedef struct {
     double contact_factor;  /* f_c in K_n (>= 0; 0 disables contact stiffness) */
     int constants;          /* 0 or 1, see above */
     int break_mode;         /* 0 or 1, see above */
+    double beta_d;          /* normal contact damping coefficient (>= 0), see above */
 } pd_material;
 
 typedef struct {

@@ -49,6 +49,7 @@ struct pd_ctx {
     int64_t *cand_ptr = nullptr, *cand_cnt = nullptr;
     int2 *cand = nullptr;
     int64_t cand_cap = 0;
+    dbl4 *cand_fd = nullptr;  // pair damping force per candidate (float4 view on the mixed path)
     uint32_t *gk = nullptr, *gk2 = nullptr, *gv = nullptr, *gv2 = nullptr, *gstart = nullptr, *gend = nullptr;
     uint64_t *gcell = nullptr;
     float4 *gpf = nullptr;  // FP32 positions of the grid's nodes (distance prefilter)
@@ -231,6 +232,8 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.cf = (float)c->c;
     p.s0f = (float)c->s0;
     p.break_mode = c->mat.break_mode;
+    p.beta_d = c->mat.beta_d;
+    p.cand_fd = c->cand_fd;
     p.mode = mode;
     p.walls = c->walls;
     p.wall_pos = c->wall_pos;
@@ -290,6 +293,10 @@ pd_status grow_candidates(pd_ctx *c)
     int64_t cap = std::max<int64_t>(2 * c->cand_cap, need + need / 2 + 1024);
     release(c, c->cand);
     ALLOC(c->cand, int2, cap);
+    if (c->mat.beta_d > 0) {
+        release(c, c->cand_fd);
+        ALLOC(c->cand_fd, dbl4, cap);
+    }
     c->cand_cap = cap;
     clear_graphs(c);
     return PD_OK;
@@ -490,6 +497,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     CK(cudaMemsetAsync(c->cand_ptr, 0, sizeof(int64_t) * (n + 1), c->st));
     c->cand_cap = std::max<int64_t>(1024, 8 * n);
     ALLOC(c->cand, int2, c->cand_cap);
+    if (c->mat.beta_d > 0) ALLOC(c->cand_fd, dbl4, c->cand_cap);  // damping force per candidate
     // reductions
     c->blocks_cap = 0;
     for (int g : {4, 8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device, mixed, false, 0));
@@ -530,7 +538,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (n < 1 || n > 0x7fffffffLL || !x || !vol || !grain || !mat) return PD_EINVAL;
     if (!(mat->E > 0) || !(mat->rho > 0) || !(mat->G0 > 0) || !(mat->contact_radius > 0) ||
         !(mat->contact_factor >= 0) || (mat->constants != 0 && mat->constants != 1) ||
-        (mat->break_mode != 0 && mat->break_mode != 1))
+        (mat->break_mode != 0 && mat->break_mode != 1) || !(mat->beta_d >= 0) || !isfinite(mat->beta_d))
         return PD_EINVAL;
     pd_ctx *c = new pd_ctx();
     if (opt) c->opt = *opt; else pd_default_options(&c->opt);
@@ -838,7 +846,7 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
             cudaEventRecord(c->prof_ev[c->prof_used + 1], c->st);
             c->prof_used += 2;
         }
-        ++launches;
+        launches += (c->opt.contact && c->cand_fd) ? 2 : 1;  // the pair-damping kernel runs first
         if (!last) in ^= 1;
     }
     return launches;

@@ -63,8 +63,8 @@ __device__ __forceinline__ double group_sum(double v)
 
 // Wall cap force on a node at p (Sec. 4.1).  Returns error bits.
 __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, double py, double pz,
-                                               double vol, double &fx, double &fy, double &fz,
-                                               double *react)
+                                               double vol, double vx, double vy, double vz, double &fx,
+                                               double &fy, double &fz, double *react)
 {
     unsigned e = 0;
     for (int l = 0; l < p.walls.nw; ++l) {
@@ -78,6 +78,9 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
         double q = p.Rc * p.Rc - d * d;
         double zbar = (M_PI / 4.0) * q * q / vcap;
         double mag = p.Kn * (p.Rc - zbar) * vcap;
+        if (p.beta_d > 0.0)  // damping: the cap moves with the wall (Sec. 4.1 substitution)
+            mag += p.beta_d * (((p.walls.v[l][0] - vx) * nx + (p.walls.v[l][1] - vy) * ny) +
+                               (p.walls.v[l][2] - vz) * nz) * vcap;
         fx += mag * nx; fy += mag * ny; fz += mag * nz;
         react[3 * l + 0] -= mag * nx * vol;
         react[3 * l + 1] -= mag * ny * vol;
@@ -256,7 +259,8 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
                 const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
                              uz = df_to_double(df{uh.z, ul.z});
                 double fx = 0.0, fy = 0.0, fz = 0.0;
-                err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, fx, fy, fz, react);
+                err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, df_to_double(df{vh.x, vl.x}),
+                                  df_to_double(df{vh.y, vl.y}), df_to_double(df{vh.z, vl.z}), fx, fy, fz, react);
                 wx = (float)fx; wy = (float)fy; wz = (float)fz;
             }
         }
@@ -272,6 +276,105 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
     v2 += __shfl_xor_sync(0xffffffffu, v2, 2);
     vmax2 = fmaxf(vmax2, v2);
     return err;
+}
+
+// One contact candidate q of row i (Sec. 3.2, the self-contact law, and the
+// normal damping of Sec. 3.3): false when the pair does not touch or is still
+// bonded; otherwise (gx, gy, gz) = its force density on i.  The predicate is
+// evaluated in FP64 without FMA, so contact pair sets are exact.
+template <bool MIXED>
+__device__ __forceinline__ bool contact_term(const StepParams &p, int64_t q, const dbl4 &ox, double pix, double piy,
+                                             double piz, int gi, double R2, double &gx, double &gy, double &gz)
+{
+    const int2 cj = p.cand[q];
+    const int j = cj.x;
+    if (cj.y >= 0) {
+        const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
+        if (!((w >> (cj.y & 31)) & 1u)) return false;  // bond intact
+    }
+    const dbl4 xj = p.x4[j], uj = load_u_t<MIXED>(p, j);
+    const double dx = dadd(xj.x, uj.x) - pix;
+    const double dy = dadd(xj.y, uj.y) - piy;
+    const double dz = dadd(xj.z, uj.z) - piz;
+    const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+    if (!(d2 < R2)) return false;
+    const double dn = sqrt(d2);
+    if (dn == 0.0) return false;
+    double mag;
+    const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
+    const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
+    if (p.grain[j] != gi || L >= p.Rc) {
+        mag = -p.Kn * (p.Rc - dn);
+    } else {
+        const double sr = (dn - L) / L;
+        mag = p.c * (sr < 0.0 ? sr : 0.0);
+    }
+    const double gm = mag * xj.w / dn;
+    gx = gm * dx; gy = gm * dy; gz = gm * dz;
+    if (p.beta_d > 0.0) {  // damping of this pair, computed before the step by k_pair_damping
+        if (MIXED) {
+            const float4 f = ((const float4 *)p.cand_fd)[q];
+            gx += f.x; gy += f.y; gz += f.z;
+        } else {
+            const dbl4 f = ((const dbl4 *)p.cand_fd)[q];
+            gx += f.x; gy += f.y; gz += f.z;
+        }
+    }
+    return true;
+}
+
+// velocity of node i in FP64 (double-float pair on the mixed path)
+template <bool MIXED>
+__device__ __forceinline__ void load_v_t(const StepParams &p, int64_t i, double &vx, double &vy, double &vz)
+{
+    if (MIXED) {
+        const float4 h = p.vh[i], l = p.vl[i];
+        vx = df_to_double(df{h.x, l.x}); vy = df_to_double(df{h.y, l.y}); vz = df_to_double(df{h.z, l.z});
+    } else {
+        const dbl4 v = p.v[i];
+        vx = v.x; vy = v.y; vz = v.z;
+    }
+}
+
+// Normal damping of every contact candidate (Sec. 3.3), read as the dissipative
+// linear law beta_d ((v_j - v_i) . e) e V_j.  Runs before the step kernel, while
+// no kernel writes velocities, so that the step kernel (which updates v in
+// place) reads a consistent half-step velocity field; candidates that do not
+// touch get zero, and the step kernel adds the term only to pairs it accepts.
+template <bool MIXED>
+__global__ void k_pair_damping(const StepParams p)
+{
+    const double R2 = dmul(p.Rc, p.Rc);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c0 = p.cand_ptr[i], c1 = p.cand_ptr[i + 1];
+        if (c1 <= c0) continue;
+        const dbl4 ox = p.x4[i], ou = load_u_t<MIXED>(p, i);
+        const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
+        double vix, viy, viz;
+        load_v_t<MIXED>(p, i, vix, viy, viz);
+        for (int64_t q = c0; q < c1; ++q) {
+            const int j = p.cand[q].x;
+            const dbl4 xj = p.x4[j], uj = load_u_t<MIXED>(p, j);
+            const double dx = dadd(xj.x, uj.x) - pix;
+            const double dy = dadd(xj.y, uj.y) - piy;
+            const double dz = dadd(xj.z, uj.z) - piz;
+            const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+            double fx = 0.0, fy = 0.0, fz = 0.0;
+            if (d2 < R2 && d2 > 0.0) {
+                const double dn = sqrt(d2);
+                const double ex = dx / dn, ey = dy / dn, ez = dz / dn;
+                double vjx, vjy, vjz;
+                load_v_t<MIXED>(p, j, vjx, vjy, vjz);
+                const double w = (vjx - vix) * ex + (vjy - viy) * ey + (vjz - viz) * ez;
+                const double g = p.beta_d * w * xj.w;
+                fx = g * ex; fy = g * ey; fz = g * ez;
+            }
+            if (MIXED)
+                ((float4 *)p.cand_fd)[q] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
+            else
+                ((dbl4 *)p.cand_fd)[q] = dbl4{fx, fy, fz, 0.0};
+        }
+    }
 }
 
 // Tile staging of the mixed path: the records of the nodes a tile touches.
@@ -352,34 +455,12 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             const int gi = p.grain[row];
             const double R2 = dmul(p.Rc, p.Rc);
             for (int64_t q = c0 + gl; q < c1; q += G) {
-                const int2 cj = p.cand[q];
-                const int j = cj.x;
-                if (cj.y >= 0) {
-                    const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
-                    if (!((w >> (cj.y & 31)) & 1u)) continue;  // bond intact
-                }
-                const dbl4 xj = p.x4[j], uj = load_u(p, j);
-                const double dx = dadd(xj.x, uj.x) - pix;
-                const double dy = dadd(xj.y, uj.y) - piy;
-                const double dz = dadd(xj.z, uj.z) - piz;
-                const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-                if (!(d2 < R2)) continue;
-                const double dn = sqrt(d2);
-                if (dn == 0.0) continue;
-                double mag;
-                const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
-                const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
-                if (p.grain[j] != gi || L >= p.Rc) {
-                    mag = -p.Kn * (p.Rc - dn);
-                } else {
-                    const double sr = (dn - L) / L;
-                    mag = p.c * (sr < 0.0 ? sr : 0.0);
-                }
-                const double gm = mag * xj.w / dn;
+                double gx, gy, gz;
+                if (!contact_term<MIXED>(p, q, ox, pix, piy, piz, gi, R2, gx, gy, gz)) continue;
                 if (MIXED) {  // FP32 accumulators of the mixed path
-                    fbx += (float)(gm * dx); fby += (float)(gm * dy); fbz += (float)(gm * dz);
+                    fbx += (float)gx; fby += (float)gy; fbz += (float)gz;
                 } else {
-                    fdx += gm * dx; fdy += gm * dy; fdz += gm * dz;
+                    fdx += gx; fdy += gy; fdz += gz;
                 }
             }
         }
@@ -403,7 +484,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
         const double hdt = 0.5 * p.dt;
         double Fx = fdx, Fy = fdy, Fz = fdz;
         const dbl4 ox = p.x4[row], ou = p.u_in[row];
-        if (p.walls.nw) err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, Fx, Fy, Fz, react);
+        const dbl4 ov = p.v[row];
+        if (p.walls.nw)
+            err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, ov.x, ov.y, ov.z, Fx, Fy,
+                              Fz, react);
         if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
         dbl4 a;
         a.x = __ddiv_rn(dadd(Fx, p.b[0]), p.rho);
@@ -637,31 +721,9 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
                     const int gi = p.grain[row];
                     const double R2 = dmul(p.Rc, p.Rc);
                     for (int64_t q = c0 + gl; q < c1; q += G) {
-                        const int2 cj = p.cand[q];
-                        const int j = cj.x;
-                        if (cj.y >= 0) {
-                            const uint32_t w = *((volatile uint32_t *)(p.brk + (cj.y >> 5)));
-                            if (!((w >> (cj.y & 31)) & 1u)) continue;
-                        }
-                        const dbl4 xj = p.x4[j], uj = load_u_t<true>(p, j);
-                        const double dx = dadd(xj.x, uj.x) - pix;
-                        const double dy = dadd(xj.y, uj.y) - piy;
-                        const double dz = dadd(xj.z, uj.z) - piz;
-                        const double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-                        if (!(d2 < R2)) continue;
-                        const double dn = sqrt(d2);
-                        if (dn == 0.0) continue;
-                        double mag;
-                        const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
-                        const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
-                        if (p.grain[j] != gi || L >= p.Rc) {
-                            mag = -p.Kn * (p.Rc - dn);
-                        } else {
-                            const double sr = (dn - L) / L;
-                            mag = p.c * (sr < 0.0 ? sr : 0.0);
-                        }
-                        const double gm = mag * xj.w / dn;
-                        fbx += (float)(gm * dx); fby += (float)(gm * dy); fbz += (float)(gm * dz);
+                        double gx, gy, gz;
+                        if (!contact_term<true>(p, q, ox, pix, piy, piz, gi, R2, gx, gy, gz)) continue;
+                        fbx += (float)gx; fby += (float)gy; fbz += (float)gz;
                     }
                 }
             }
@@ -811,6 +873,13 @@ int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem)
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st)
 {
     const bool mixed = p.xh4 != nullptr;
+    if (p.beta_d > 0.0 && p.contact && p.cand_fd) {
+        const int db = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (p.n + 127) / 128));
+        if (mixed)
+            k_pair_damping<true><<<db, 128, 0, st>>>(p);
+        else
+            k_pair_damping<false><<<db, 128, 0, st>>>(p);
+    }
     switch (lanes) {
         case 4: launch_g<4>(p, blocks, st, mixed); break;
         case 8: launch_g<8>(p, blocks, st, mixed); break;

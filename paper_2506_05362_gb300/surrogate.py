@@ -103,12 +103,13 @@ def _areas(L):
 def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.04,
             records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8,
             p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 40000,
-            G0: float = None) -> Run:
+            G0: float = None, zeta: float = 0.0) -> Run:
     """One RVE run: an aggregate in a box of six rigid walls is first compressed
     isotropically at strain rate ``rate`` until the mean wall stress reaches the
     confining pressure ``p_confine`` (a connected contact network; the solid
     fraction is capped at ``sf_max``), then strained along ``path`` at ``rate`` up
-    to ``strain_end`` on the dominant axis, recorded ``records`` times.  Strain is
+    to ``strain_end`` on the dominant axis, recorded ``records`` times.  ``zeta`` > 0
+    turns on the normal contact damping at that fraction of critical.  Strain is
     measured from the box at the end of the pre-compression; the recorded stress
     is that of the wall forces averaged over each record interval.
 
@@ -119,6 +120,9 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
     sc = S.aggregate(n_grains=n_grains, seed=seed, h=h, gap_cells=0.5)
     if G0 is not None:  # fracture energy of the grains (glass: 135 J/m^2)
         sc.material = dataclasses.replace(sc.material, G0=G0)
+    if zeta > 0:  # normal contact damping (Sec. 3.3) at this ratio of critical for a node pair
+        sc.material = dataclasses.replace(sc.material, beta_d=damping_coefficient(sc.material, sc.horizon,
+                                                                                  float(sc.vol.mean()), zeta))
     mult = np.array(LOADING_PATHS[path])
     walls = S.walls_array(sc.walls)
     lo, hi = _box(walls[:, 3:6])

@@ -391,3 +391,82 @@ def test_error_paths(pd):
     ctx.set_walls(np.array([[0, 0, -1.0, 0, 0, top, 0, 0, 0.0]]))
     ctx.set_state(u=u0)
     ctx.step(dt, 2)
+
+
+# --------------------------------------------------------------------------- damping (Sec. 3.3)
+def damped_blocks(beta_zeta=0.4):
+    """Two jittered blocks of different grains pressed into each other, the lower
+    one resting in a wall's contact range, with random velocities."""
+    from paper_2506_05362_gb300 import surrogate as SG
+    h = 1e-4
+    rng = np.random.default_rng(3)
+    I, J, K = np.meshgrid(np.arange(6), np.arange(5), np.arange(4), indexing="ij")
+    lat = np.stack([I.ravel(), J.ravel(), K.ravel()], 1).astype(np.float64) * h
+    a = lat + rng.uniform(-0.05, 0.05, lat.shape) * h
+    b = lat + rng.uniform(-0.05, 0.05, lat.shape) * h + np.array([0.2 * h, 0.3 * h, 3.55 * h])
+    x = np.concatenate([a, b])
+    grain = np.repeat(np.array([0, 1], np.int32), len(a))
+    vol = np.full(len(x), h ** 3)
+    mat = S.Material(E=72e9, rho=2440, G0=135, contact_radius=0.6 * h)
+    mat.beta_d = SG.damping_coefficient(mat, 3 * h, h ** 3, beta_zeta)
+    zmin = x[:, 2].min()
+    walls = [S.Wall((0.0, 0.0, 1.0), (0.0, 0.0, zmin - 0.5 * mat.contact_radius), (0.0, 0.0, 0.3))]
+    v0 = rng.normal(0, 0.5, x.shape)
+    return S.Scenario(name="damped", x=x, vol=vol, grain=grain, v0=v0, material=mat, horizon=3 * h, h=h,
+                      walls=walls, wall_area=1e-6)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_FORCE_TOL), ("fp64", FP64_FORCE_TOL)])
+def test_damping_forces_same_state(pd, precision, tol):
+    """Pair and wall damping at one state (current velocities) against the oracle;
+    the damping term alone is checked too, so it cannot hide under the springs."""
+    sc = damped_blocks()
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=8)
+    ref = oracle.Model.from_scenario(sc)
+    F = ctx.forces()
+    ref.forces()
+    assert len(ref.contact_pairs()) > 0
+    assert rel_l2(F, ref.F) <= tol
+    sig, wf = ctx.bulk_stress([1e-6])
+    assert rel_l2(wf, ref.react) <= max(tol, 1e-9)
+    # damping alone: the same state without damping
+    sc0 = damped_blocks()
+    sc0.material.beta_d = 0.0
+    ctx0 = pd.Context.from_scenario(sc0, precision=precision, lanes=8)
+    ref.P.beta_d = 0.0
+    Fd_ref = ref.F.copy() - ref.forces(frozen=True).copy()
+    Fd = F - ctx0.forces()
+    assert np.abs(Fd_ref).max() > 1e-3 * np.abs(ref.F).max()
+    assert rel_l2(Fd, Fd_ref) <= (1e-4 if precision == "mixed" else 1e-9)
+    ctx.close(); ctx0.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-9)])
+def test_damped_collision_trajectory(pd, precision, tol):
+    """Two grains colliding with pair damping (zeta = 0.3) and a damped wall: the
+    trajectory follows the oracle, and the collision dissipates energy."""
+    from paper_2506_05362_gb300 import surrogate as SG
+    sc = S.aggregate(n_grains=2, h=0.5e-3 / 4, gap_cells=0.5, seed=4)
+    c = sc.x[sc.grain == 0].mean(0) - sc.x[sc.grain == 1].mean(0)
+    c /= np.linalg.norm(c)
+    sc.v0 = np.where((sc.grain == 0)[:, None], -5.0 * c, 5.0 * c)
+    sc.walls = []
+    sc.material.beta_d = SG.damping_coefficient(sc.material, sc.horizon, sc.h ** 3, 0.3)
+    ctx = pd.Context.from_scenario(sc, precision=precision)
+    ref = oracle.Model.from_scenario(sc)
+    dt = 0.5 * ref.stable_dt()
+    ref.init()
+    ke0 = 0.5 * sc.material.rho * (sc.vol[:, None] * ref.v ** 2).sum()
+    touched, total = 0, 0
+    while total < 20000 and touched < 60:
+        ref.step(dt, 10)
+        ctx.step(dt, 10)
+        total += 10
+        if touched or len(ref.contact_pairs()) > 0:
+            touched += 10
+    assert touched > 0, "grains never met"
+    u, v, broken, _ = ctx.get_state()
+    assert rel_l2(u, ref.u) < tol
+    assert rel_l2(v, ref.v) < 10 * tol
+    ke1 = 0.5 * sc.material.rho * (sc.vol[:, None] * ref.v ** 2).sum()
+    assert ke1 < ke0
