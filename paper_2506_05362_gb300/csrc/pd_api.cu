@@ -34,9 +34,11 @@ struct pd_ctx {
 
     int32_t *perm = nullptr, *inv = nullptr, *grain = nullptr;
     dbl4 *x4 = nullptr, *u[2] = {nullptr, nullptr}, *v = nullptr, *acc = nullptr, *F = nullptr;
-    float4 *xh4 = nullptr, *xl4 = nullptr, *uh[2] = {nullptr, nullptr}, *ul[2] = {nullptr, nullptr};
+    float4 *xh4 = nullptr, *xl4 = nullptr;
+    float4 *rec[2] = {nullptr, nullptr};                 // mixed path: REC float4 per node, current / next
+    float4 *uh[2] = {nullptr, nullptr}, *ul[2] = {nullptr, nullptr};  // views rec + 1, rec + 2 (stride REC)
     float4 *vh = nullptr, *vl = nullptr, *af = nullptr;  // mixed path: v pairs, a
-    float4 *snap_vh = nullptr, *snap_vl = nullptr, *snap_af = nullptr, *snap_uh = nullptr, *snap_ul = nullptr;
+    float4 *snap_vh = nullptr, *snap_vl = nullptr, *snap_af = nullptr, *snap_rec = nullptr;
     bool own_stream = false;
     int cur = 0;
 
@@ -194,7 +196,7 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.col = c->col;
     p.brk = c->brk;
     p.colf = c->colf;
-    p.xh4 = mixed ? c->xh4 : nullptr;
+    p.xh4 = mixed ? c->rec[in] : nullptr;
     p.xl4 = mixed ? c->xl4 : nullptr;
     p.uh_in = mixed ? c->uh[in] : nullptr;
     p.ul_in = mixed ? c->ul[in] : nullptr;
@@ -265,7 +267,7 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
 const dbl4 *upos(pd_ctx *c, int in)
 {
     if (c->opt.precision == PD_MIXED) {
-        materialize_df(c->uh[in], c->ul[in], c->n, c->u[0], c->st);
+        materialize_df(c->uh[in], c->ul[in], REC, c->n, c->u[0], c->st);
         return c->u[0];
     }
     return c->u[in];
@@ -450,14 +452,14 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
         ALLOC(c->xh4, float4, n);
         ALLOC(c->xl4, float4, n);
         for (int q = 0; q < 2; ++q) {
-            ALLOC(c->uh[q], float4, n);
-            ALLOC(c->ul[q], float4, n);
+            ALLOC(c->rec[q], float4, (int64_t)REC * n);
+            c->uh[q] = c->rec[q] + 1;
+            c->ul[q] = c->rec[q] + 2;
         }
         ALLOC(c->vh, float4, n);
         ALLOC(c->vl, float4, n);
         ALLOC(c->af, float4, n);
-        ALLOC(c->snap_uh, float4, n);
-        ALLOC(c->snap_ul, float4, n);
+        ALLOC(c->snap_rec, float4, (int64_t)REC * n);
         ALLOC(c->snap_vh, float4, n);
         ALLOC(c->snap_vl, float4, n);
         ALLOC(c->snap_af, float4, n);
@@ -468,16 +470,16 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     CK(cudaGetLastError());
     for (int q = 0; q < 2; ++q) {
         CK(cudaMemsetAsync(c->u[q], 0, sizeof(dbl4) * n, c->st));
-        if (mixed) {
-            CK(cudaMemsetAsync(c->uh[q], 0, sizeof(float4) * n, c->st));
-            CK(cudaMemsetAsync(c->ul[q], 0, sizeof(float4) * n, c->st));
-        }
+        if (mixed) CK(cudaMemsetAsync(c->rec[q], 0, sizeof(float4) * REC * n, c->st));
     }
     CK(cudaMemsetAsync(c->acc, 0, sizeof(dbl4) * n, c->st));
     CK(cudaMemsetAsync(c->F, 0, sizeof(dbl4) * n, c->st));
     if (mixed) {
-        split_df(c->v, nullptr, n, c->vh, c->vl, c->st);
-        for (int q = 0; q < 2; ++q) split_df(c->u[q], c->xl4, n, c->uh[q], c->ul[q], c->st);
+        split_df(c->v, nullptr, n, c->vh, c->vl, 1, c->st);
+        for (int q = 0; q < 2; ++q) {
+            fill_record_x(c->xh4, n, c->rec[q], c->st);  // x slots are static
+            split_df(c->u[q], c->xl4, n, c->uh[q], c->ul[q], REC, c->st);
+        }
         CK(cudaMemsetAsync(c->af, 0, sizeof(float4) * n, c->st));
     }
     // grid and contact buffers
@@ -882,8 +884,7 @@ static pd_status snapshot(pd_ctx *c, bool restore)
         return cudaMemcpyAsync(restore ? (void *)src : dst, restore ? dst : src, bytes, cudaMemcpyDeviceToDevice, c->st);
     };
     if (mixed) {
-        CK(cp(c->snap_uh, c->uh[c->cur], nf));
-        CK(cp(c->snap_ul, c->ul[c->cur], nf));
+        CK(cp(c->snap_rec, c->rec[c->cur], (size_t)REC * nf));
         CK(cp(c->snap_vh, c->vh, nf));
         CK(cp(c->snap_vl, c->vl, nf));
         CK(cp(c->snap_af, c->af, nf));
@@ -907,7 +908,7 @@ static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
     if (!c->opt.contact) { *k = 1 << 30; return PD_OK; }
     if (c->opt.contact_every > 0) { *k = c->opt.contact_every; return PD_OK; }
     int nb = vmax_blocks(c->n);
-    if (c->opt.precision == PD_MIXED) materialize_df(c->vh, c->vl, c->n, c->v, c->st);
+    if (c->opt.precision == PD_MIXED) materialize_df(c->vh, c->vl, 1, c->n, c->v, c->st);
     vmax(c->v, c->n, c->dscratch, c->st);
     std::vector<double> h(nb);
     CK(cudaMemcpyAsync(h.data(), c->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
@@ -1229,7 +1230,7 @@ pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double 
     }
     if (v) {
         if (u) { pd_status s = sync(c); if (s) return s; }
-        if (mixed) materialize_df(c->vh, c->vl, c->n, c->v, c->st);
+        if (mixed) materialize_df(c->vh, c->vl, 1, c->n, c->v, c->st);
         to_caller(c->v, c->perm, c->n, c->stage, c->st);
         CK(cudaMemcpyAsync(v, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
     }
@@ -1255,7 +1256,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
         CK(cudaMemcpyAsync(c->stage, u, nb, cudaMemcpyHostToDevice, c->st));
         if (c->opt.precision == PD_MIXED) {
             from_caller(c->stage, c->perm, c->n, c->u[0], c->st);
-            split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], c->st);
+            split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], REC, c->st);
         } else {
             from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
         }
@@ -1267,7 +1268,7 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
             if (!isfinite(v[q])) return fail(c, PD_EINVAL, "v contains a non-finite value");
         CK(cudaMemcpyAsync(c->stage, v, nb, cudaMemcpyHostToDevice, c->st));
         from_caller(c->stage, c->perm, c->n, c->v, c->st);
-        if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, c->st);
+        if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
         pd_status s = sync(c);
         if (s) return s;
     }

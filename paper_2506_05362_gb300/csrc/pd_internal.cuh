@@ -38,16 +38,22 @@ struct WallSet {
 };
 
 // Everything the force/update kernels need, passed by value.
+constexpr int REC = 3;  // float4 per mixed-path node record
+
 struct StepParams {
     int64_t n;
     const int64_t *rowptr;
     const int32_t *col;
     uint32_t *brk;                 // broken bit per directed slot
     // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
-    const float4 *xh4;             // (x_hi, V), x relative to the bounding-box centre
-    const float4 *xl4;             // (x_lo, 0)
-    const float4 *uh_in, *ul_in;   // (u_hi, packed x_lo.xy), (u_lo, packed x_lo.z); current buffer
-    float4 *uh_out, *ul_out;       // u, next buffer
+    // mixed-path node records, REC float4 per node, interleaved so that one
+    // neighbour gather is one 48-byte record: [REC*i] = (x_hi, V) with x relative
+    // to the bounding-box centre (static), [REC*i+1] = (u_hi, packed x_lo.xy),
+    // [REC*i+2] = (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
+    const float4 *xh4;             // record base of the current buffer (index REC*i)
+    const float4 *xl4;             // (x_lo, 0), dense
+    const float4 *uh_in, *ul_in;   // = xh4 + 1, xh4 + 2 (index REC*i)
+    float4 *uh_out, *ul_out;       // next buffer's u slots (index REC*i)
     float4 *vh, *vl;               // v (in place)
     float4 *af;                    // a = (F + b)/rho, stored for the next drift
     float dt_hi, dt_lo, hdt_hi, hdt_lo, inv_rho_f, bf[3], Rc_f;
@@ -116,8 +122,10 @@ void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
 void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float state <-> FP64 (mixed path)
-void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st);
-void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
+// double-float pair arrays with an element stride (1 for dense, REC for records)
+void materialize_df(const float4 *hi, const float4 *lo, int stride, int64_t n, dbl4 *out, cudaStream_t st);
+void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, int stride, cudaStream_t st);
+void fill_record_x(const float4 *xh4, int64_t n, float4 *rec, cudaStream_t st);
 int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem);
 size_t tiled_smem(int tile_cap, int tile_rows, int slot_cap);
 

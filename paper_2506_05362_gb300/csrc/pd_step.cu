@@ -177,7 +177,7 @@ __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
 {
     dbl4 r;
     if (MIXED) {
-        const float4 h = p.uh_in[i], l = p.ul_in[i];
+        const float4 h = p.uh_in[REC * i], l = p.ul_in[REC * i];
         r.x = df_to_double(df{h.x, l.x});
         r.y = df_to_double(df{h.y, l.y});
         r.z = df_to_double(df{h.z, l.z});
@@ -212,11 +212,11 @@ __device__ __forceinline__ unsigned epilogue_component(const StepParams &p, int6
         const float uhc = c == 0 ? uh.x : (c == 1 ? uh.y : uh.z);
         const float ulc = c == 0 ? ul.x : (c == 1 ? ul.y : ul.z);
         const df u = df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v));
-        ((float *)(p.uh_out + row))[c] = u.hi;
-        ((float *)(p.ul_out + row))[c] = u.lo;
+        ((float *)(p.uh_out + REC * row))[c] = u.hi;
+        ((float *)(p.ul_out + REC * row))[c] = u.lo;
         if (c == 0) {  // packed x_lo travels with the record
-            ((float *)(p.uh_out + row))[3] = uh.w;
-            ((float *)(p.ul_out + row))[3] = ul.w;
+            ((float *)(p.uh_out + REC * row))[3] = uh.w;
+            ((float *)(p.ul_out + REC * row))[3] = ul.w;
         }
         vc2 = v.hi * v.hi;
         if (!isfinite(v.hi) || !isfinite(u.hi)) err |= PDE_NONFINITE;
@@ -397,7 +397,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
     if (active) {
         const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
         if (MIXED) {
-            const float4 o0 = __ldg(p.xh4 + row), o1 = __ldg(p.uh_in + row), o2 = __ldg(p.ul_in + row);
+            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row), o2 = __ldg(p.ul_in + REC * row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
             const int i0 = (int)k0, i1 = (int)k1;
@@ -414,9 +414,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
                     const int j = raw[q] & 0x7fffffff;
-                    a0[q] = __ldg(p.xh4 + j);
-                    a1[q] = __ldg(p.uh_in + j);
-                    a2[q] = __ldg(p.ul_in + j);
+                    const float4 *rj = p.xh4 + REC * j;  // one 48-byte record
+                    a0[q] = __ldg(rj);
+                    a1[q] = __ldg(rj + 1);
+                    a2[q] = __ldg(rj + 2);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)
@@ -475,7 +476,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
     if (MIXED) {
         float4 oxh = make_float4(0.f, 0.f, 0.f, 0.f), ouh = oxh, oul = oxh, ovh = oxh, ovl = oxh;
         if (active && gl < 3) {
-            oxh = __ldg(p.xh4 + row); ouh = __ldg(p.uh_in + row); oul = __ldg(p.ul_in + row);
+            oxh = __ldg(p.xh4 + REC * row); ouh = __ldg(p.uh_in + REC * row); oul = __ldg(p.ul_in + REC * row);
             ovh = p.vh[row]; ovl = p.vl[row];
         }
         err |= epilogue_lanes<G>(p, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
@@ -671,9 +672,9 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             }
             for (int q = threadIdx.x; q < len; q += STEP_THREADS) {
                 const int j = __ldg(p.ulist + base + q);
-                r0s[q] = __ldg(p.xh4 + j);
-                r1s[q] = __ldg(p.uh_in + j);
-                r2s[q] = __ldg(p.ul_in + j);
+                r0s[q] = __ldg(p.xh4 + REC * j);
+                r1s[q] = __ldg(p.uh_in + REC * j);
+                r2s[q] = __ldg(p.ul_in + REC * j);
             }
         }
         __syncthreads();
@@ -747,7 +748,7 @@ __global__ void k_drift(const StepParams p)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (MIXED) {
-            const float4 a = p.af[i], vh = p.vh[i], vl = p.vl[i], uh = p.uh_in[i], ul = p.ul_in[i];
+            const float4 a = p.af[i], vh = p.vh[i], vl = p.vl[i], uh = p.uh_in[REC * i], ul = p.ul_in[REC * i];
             const df h{p.hdt_hi, p.hdt_lo}, dt{p.dt_hi, p.dt_lo};
             const df vx = df_add(df{vh.x, vl.x}, df_mul_f(h, a.x));
             const df vy = df_add(df{vh.y, vl.y}, df_mul_f(h, a.y));
@@ -757,8 +758,8 @@ __global__ void k_drift(const StepParams p)
             const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
             p.vh[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
             p.vl[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
-            p.uh_out[i] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
-            p.ul_out[i] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
+            p.uh_out[REC * i] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
+            p.ul_out[REC * i] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
         } else {
             dbl4 v = p.v[i];
             const dbl4 a = p.acc[i], u = p.u_in[i];
@@ -782,10 +783,11 @@ __global__ void k_drift(const StepParams p)
 }
 
 // u (FP64) from the double-float state, for the rebuild kernels and queries
-__global__ void k_materialize(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int64_t n, dbl4 *out)
+__global__ void k_materialize(const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride, int64_t n,
+                              dbl4 *out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 h = hi[i], l = lo[i];
+        const float4 h = hi[stride * i], l = lo[stride * i];
         dbl4 r;
         r.x = df_to_double(df{h.x, l.x});
         r.y = df_to_double(df{h.y, l.y});
@@ -798,7 +800,7 @@ __global__ void k_materialize(const float4 *__restrict__ hi, const float4 *__res
 // double -> double-float; with xl (the static x_lo) the spare lanes get the packed
 // x_lo of the u records
 __global__ void k_split_df(const dbl4 *__restrict__ in, const float4 *__restrict__ xl, int64_t n, float4 *hi,
-                           float4 *lo)
+                           float4 *lo, int stride)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const dbl4 a = in[i];
@@ -812,9 +814,15 @@ __global__ void k_split_df(const dbl4 *__restrict__ in, const float4 *__restrict
             w1 = __uint_as_float(bx | (by << 16));
             w2 = __uint_as_float(bz);
         }
-        hi[i] = make_float4(x.hi, y.hi, z.hi, w1);
-        lo[i] = make_float4(x.lo, y.lo, z.lo, w2);
+        hi[stride * i] = make_float4(x.hi, y.hi, z.hi, w1);
+        lo[stride * i] = make_float4(x.lo, y.lo, z.lo, w2);
     }
+}
+
+__global__ void k_fill_record_x(const float4 *__restrict__ xh4, int64_t n, float4 *rec)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        rec[REC * i] = xh4[i];
 }
 
 template <int G>
@@ -894,14 +902,19 @@ static int small_grid(int64_t n)
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
 }
 
-void materialize_df(const float4 *hi, const float4 *lo, int64_t n, dbl4 *out, cudaStream_t st)
+void materialize_df(const float4 *hi, const float4 *lo, int stride, int64_t n, dbl4 *out, cudaStream_t st)
 {
-    k_materialize<<<small_grid(n), 256, 0, st>>>(hi, lo, n, out);
+    k_materialize<<<small_grid(n), 256, 0, st>>>(hi, lo, stride, n, out);
 }
 
-void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, cudaStream_t st)
+void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, int stride, cudaStream_t st)
 {
-    k_split_df<<<small_grid(n), 256, 0, st>>>(in, xl, n, hi, lo);
+    k_split_df<<<small_grid(n), 256, 0, st>>>(in, xl, n, hi, lo, stride);
+}
+
+void fill_record_x(const float4 *xh4, int64_t n, float4 *rec, cudaStream_t st)
+{
+    k_fill_record_x<<<small_grid(n), 256, 0, st>>>(xh4, n, rec);
 }
 
 void launch_drift(const StepParams &p, cudaStream_t st)
