@@ -477,7 +477,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     if (mixed) {
         split_df(c->v, nullptr, n, c->vh, c->vl, 1, c->st);
         for (int q = 0; q < 2; ++q) {
-            fill_record_x(c->xh4, n, c->rec[q], c->st);  // x slots are static
+            fill_record_x(c->xh4, n, 1.0f, c->rec[q], c->st);  // x slots are static (c V once bonds exist)
             split_df(c->u[q], c->xl4, n, c->uh[q], c->ul[q], REC, c->st);
         }
         CK(cudaMemsetAsync(c->af, 0, sizeof(float4) * n, c->st));
@@ -623,6 +623,8 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     c->delta = horizon;
     constants(c);
     const int64_t n = c->n;
+    if (c->opt.precision == PD_MIXED)  // the records carry c V for the bond force
+        for (int q = 0; q < 2; ++q) fill_record_x(c->xh4, n, (float)c->c, c->rec[q], c->st);
     // grid over the reference positions, cell = horizon
     GridView g;
     for (int a = 0; a < 3; ++a) g.lo[a] = c->lo[a];

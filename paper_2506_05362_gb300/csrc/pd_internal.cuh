@@ -47,8 +47,8 @@ struct StepParams {
     uint32_t *brk;                 // broken bit per directed slot
     // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
     // mixed-path node records, REC float4 per node, interleaved so that one
-    // neighbour gather is one 48-byte record: [REC*i] = (x_hi, V) with x relative
-    // to the bounding-box centre (static), [REC*i+1] = (u_hi, packed x_lo.xy),
+    // neighbour gather is one 48-byte record: [REC*i] = (x_hi, c V) with x
+    // relative to the bounding-box centre (static; c V set at bond build), [REC*i+1] = (u_hi, packed x_lo.xy),
     // [REC*i+2] = (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
     const float4 *xh4;             // record base of the current buffer (index REC*i)
     const float4 *xl4;             // (x_lo, 0), dense
@@ -125,7 +125,7 @@ void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float pair arrays with an element stride (1 for dense, REC for records)
 void materialize_df(const float4 *hi, const float4 *lo, int stride, int64_t n, dbl4 *out, cudaStream_t st);
 void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *lo, int stride, cudaStream_t st);
-void fill_record_x(const float4 *xh4, int64_t n, float4 *rec, cudaStream_t st);
+void fill_record_x(const float4 *xh4, int64_t n, float cf, float4 *rec, cudaStream_t st);
 int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem);
 size_t tiled_smem(int tile_cap, int tile_rows, int slot_cap);
 

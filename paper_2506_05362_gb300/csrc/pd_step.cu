@@ -129,7 +129,7 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
         if (FLAG) atomicOr((unsigned int *)(p.lcol) + (k >> 1), 0x8000u << (16 * (int)(k & 1)));
         if (p.colf) atomicOr((unsigned int *)p.colf + k, 0x80000000u);
     } else {
-        const float g = p.cf * a0.w * s * ry;
+        const float g = a0.w * s * ry;  // a0.w holds c V_j
         fbx = fmaf(g, yx, fbx);
         fby = fmaf(g, yy, fby);
         fbz = fmaf(g, yz, fbz);
@@ -145,18 +145,24 @@ __device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, i
                                                    const float4 &a0, const float4 &a1, const float4 &a2, float &fbx,
                                                    float &fby, float &fbz)
 {
+    // The x and y components go through packed FP32x2 instructions (Blackwell):
+    // a 16-byte load leaves them in a register pair, and each lane of a packed
+    // add/mul/fma rounds exactly like the scalar instruction, so this is the same
+    // arithmetic, operation for operation, as the scalar form of bond_mixed.
     float al[3];
     xl_unpack(a1.w, a2.w, al);
-    const float xx = (a0.x - o0.x) + (al[0] - ol[0]);
-    const float xy = (a0.y - o0.y) + (al[1] - ol[1]);
+    const float2 xxy = __fadd2_rn(__fadd2_rn(make_float2(a0.x, a0.y), make_float2(-o0.x, -o0.y)),
+                                  __fadd2_rn(make_float2(al[0], al[1]), make_float2(-ol[0], -ol[1])));
     const float xz = (a0.z - o0.z) + (al[2] - ol[2]);
-    const float ex = (a1.x - o1.x) + (a2.x - o2.x);
-    const float ey = (a1.y - o1.y) + (a2.y - o2.y);
+    const float2 exy = __fadd2_rn(__fadd2_rn(make_float2(a1.x, a1.y), make_float2(-o1.x, -o1.y)),
+                                  __fadd2_rn(make_float2(a2.x, a2.y), make_float2(-o2.x, -o2.y)));
     const float ez = (a1.z - o1.z) + (a2.z - o2.z);
-    const float yx = xx + ex, yy = xy + ey, yz = xz + ez;
-    const float L2 = fmaf(xx, xx, fmaf(xy, xy, xz * xz));
-    const float y2 = fmaf(yx, yx, fmaf(yy, yy, yz * yz));
-    const float num = fmaf(ex, xx + yx, fmaf(ey, xy + yy, ez * (xz + yz)));
+    const float2 yxy = __fadd2_rn(xxy, exy);
+    const float yz = xz + ez;
+    const float L2 = fmaf(xxy.x, xxy.x, fmaf(xxy.y, xxy.y, xz * xz));
+    const float y2 = fmaf(yxy.x, yxy.x, fmaf(yxy.y, yxy.y, yz * yz));
+    const float2 txy = __fadd2_rn(xxy, yxy);
+    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * (xz + yz)));
     const float rL = rsqrtf(L2), ry = rsqrtf(y2);
     const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
     const bool intact = raw >= 0;
@@ -165,9 +171,11 @@ __device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, i
         p.colf[k] = (int32_t)((uint32_t)raw | 0x80000000u);
         atomicOr(p.brk + (k >> 5), 1u << (k & 31));
     }
-    const float g = (intact && !brk) ? p.cf * a0.w * s * ry : 0.f;
-    fbx = fmaf(g, yx, fbx);
-    fby = fmaf(g, yy, fby);
+    // a0.w holds c V_j (the record's volume slot is scaled at bond build)
+    const float g = (intact && !brk) ? a0.w * s * ry : 0.f;
+    const float2 f = __ffma2_rn(make_float2(g, g), yxy, make_float2(fbx, fby));
+    fbx = f.x;
+    fby = f.y;
     fbz = fmaf(g, yz, fbz);
 }
 
@@ -819,10 +827,15 @@ __global__ void k_split_df(const dbl4 *__restrict__ in, const float4 *__restrict
     }
 }
 
-__global__ void k_fill_record_x(const float4 *__restrict__ xh4, int64_t n, float4 *rec)
+// x slot of the records: (x_hi, c V) with c the micromodulus as FP32 (the bond
+// force uses V only as c V)
+__global__ void k_fill_record_x(const float4 *__restrict__ xh4, int64_t n, float cf, float4 *rec)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        rec[REC * i] = xh4[i];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 r = xh4[i];
+        r.w = cf * r.w;
+        rec[REC * i] = r;
+    }
 }
 
 template <int G>
@@ -912,9 +925,9 @@ void split_df(const dbl4 *in, const float4 *xl, int64_t n, float4 *hi, float4 *l
     k_split_df<<<small_grid(n), 256, 0, st>>>(in, xl, n, hi, lo, stride);
 }
 
-void fill_record_x(const float4 *xh4, int64_t n, float4 *rec, cudaStream_t st)
+void fill_record_x(const float4 *xh4, int64_t n, float cf, float4 *rec, cudaStream_t st)
 {
-    k_fill_record_x<<<small_grid(n), 256, 0, st>>>(xh4, n, rec);
+    k_fill_record_x<<<small_grid(n), 256, 0, st>>>(xh4, n, cf, rec);
 }
 
 void launch_drift(const StepParams &p, cudaStream_t st)
