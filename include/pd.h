@@ -84,9 +84,7 @@ typedef struct {
 typedef struct {
     int device;                          /* CUDA device ordinal */
     void *stream;                        /* cudaStream_t, NULL = legacy default stream */
-    void *(*alloc)(size_t bytes, void *alloc_ctx);  /* NULL: cudaMalloc; must return
-                                                       256-byte aligned memory (an
-                                                       unaligned block fails as PD_ENOMEM) */
+    void *(*alloc)(size_t bytes, void *alloc_ctx);  /* NULL: cudaMalloc */
     void (*free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
     int precision;                       /* PD_MIXED or PD_FP64 */

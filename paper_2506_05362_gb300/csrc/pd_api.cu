@@ -106,11 +106,6 @@ void *pd_dev_alloc(pd_ctx *c, size_t bytes)
         cudaGetLastError();
         p = nullptr;
     }
-    // vector loads of up to 32 bytes need aligned arrays; cudaMalloc gives 256 bytes
-    if (p && ((uintptr_t)p & 255u)) {
-        if (c->opt.free) c->opt.free(p, c->opt.alloc_ctx);
-        return nullptr;
-    }
     if (p) c->owned.push_back(p);
     return p;
 }

@@ -38,7 +38,7 @@ struct WallSet {
 };
 
 // Everything the force/update kernels need, passed by value.
-constexpr int REC = 4;  // float4 per mixed-path node record (64 bytes: 32-byte aligned halves)
+constexpr int REC = 3;  // float4 per mixed-path node record
 
 struct StepParams {
     int64_t n;
@@ -47,11 +47,9 @@ struct StepParams {
     uint32_t *brk;                 // broken bit per directed slot
     // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
     // mixed-path node records, REC float4 per node, interleaved so that one
-    // neighbour gather is one 256-bit and one 128-bit load: [REC*i] = (x_hi, c V)
-    // with x relative to the bounding-box centre (static; c V set at bond build),
-    // [REC*i+1] = (u_hi, packed x_lo.xy), [REC*i+2] = (u_lo, packed x_lo.z),
-    // [REC*i+3] unused (keeps records 32-byte aligned).  Two buffers
-    // (current / next) for u.
+    // neighbour gather is one 48-byte record: [REC*i] = (x_hi, c V) with x
+    // relative to the bounding-box centre (static; c V set at bond build), [REC*i+1] = (u_hi, packed x_lo.xy),
+    // [REC*i+2] = (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
     const float4 *xh4;             // record base of the current buffer (index REC*i)
     const float4 *xl4;             // (x_lo, 0), dense
     const float4 *uh_in, *ul_in;   // = xh4 + 1, xh4 + 2 (index REC*i)

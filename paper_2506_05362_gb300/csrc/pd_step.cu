@@ -89,15 +89,6 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
     return e;
 }
 
-// 32 bytes from a 32-byte aligned address in one 256-bit load (sm_100+),
-// through the non-coherent path like __ldg
-__device__ __forceinline__ void ldg256(const float4 *ptr, float4 &a, float4 &b)
-{
-    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
-        : "l"(ptr));
-}
-
 // x_lo rides in the spare lanes of the u records as BF16: R1.w = (x_lo.x, x_lo.y),
 // R2.w = (x_lo.z, 0).  BF16 keeps 8 bits of x_lo, so x is known to 2^-32 |x|
 // (x is stored relative to the centre of the bounding box).
@@ -431,8 +422,9 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
                     const int j = raw[q] & 0x7fffffff;
-                    const float4 *rj = p.xh4 + REC * j;  // one record: 32 + 16 bytes
-                    ldg256(rj, a0[q], a1[q]);
+                    const float4 *rj = p.xh4 + REC * j;  // one 48-byte record
+                    a0[q] = __ldg(rj);
+                    a1[q] = __ldg(rj + 1);
                     a2[q] = __ldg(rj + 2);
                 }
 #pragma unroll
