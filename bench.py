@@ -334,7 +334,7 @@ def bench_surrogate(local, stream, reps=20):
     return {"dims": list(dims), "batch": B, "forward_ms": fwd_ms, "forward_samples_per_s": B / (fwd_ms * 1e-3),
             "train_step_ms": train_ms,
             "roofline": {"bound": "tensor", "achieved": fwd_tf, "peak": peak, "unit": "TFLOP/s",
-                         "frac": fwd_tf / peak, "peak_kind": kind, "kernel": "k_gemm (forward, all layers)"},
+                         "frac": fwd_tf / peak, "peak_kind": kind, "kernel": "k_mlp_fwd_tc (fused tcgen05 forward, all layers)"},
             "train_tflops": train_tf}
 
 

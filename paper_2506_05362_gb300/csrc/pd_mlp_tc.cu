@@ -9,10 +9,11 @@
 //               N = layer width, K = 16 per instruction) from the activation
 //               tile A and the weight stage into a TMEM accumulator, and
 //               tcgen05.commit's to release stages and to signal the epilogue;
-//   warps 2-5   epilogue: tcgen05.ld the accumulator (one TMEM lane quarter per
-//               warp = 32 rows), add the bias, exact-erf GELU, round to BF16 and
-//               write the next layer's A tile in the swizzled layout; the last
-//               layer writes FP32 outputs.  They also stage the input tile.
+//   warps 2-9   epilogue: tcgen05.ld the accumulator (two warps per TMEM lane
+//               quarter = 32 rows, each taking half of the columns), add the
+//               bias, exact-erf GELU, round to BF16 and write the next layer's A
+//               tile in the swizzled layout; the last layer writes FP32 outputs.
+//               They also stage the input tile with coalesced reads.
 // Every mbarrier wait is bounded; on timeout the kernel records an error word,
 // stops issuing, frees its TMEM and returns.
 #include <cuda.h>
@@ -32,7 +33,8 @@ constexpr int MAX_N = 256;
 constexpr int MAX_K = 256;
 constexpr int A_BYTES = TILE_M * MAX_K * 2;   // 64 KiB: 4 atoms of 128 rows x 128 B
 constexpr int W_STAGE_BYTES = MAX_N * KCHUNK * 2;  // 32 KiB
-constexpr int THREADS = 192;
+constexpr int EPI_THREADS = 256;              // 8 epilogue warps
+constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int MAX_LAYERS = 8;
 constexpr unsigned long long WAIT_NS = 1000000000ull;  // a wait gives up after 1 s
 
@@ -159,6 +161,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// two floats rounded to BF16 (nearest-even), packed low = a, high = b, in registers
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    __nv_bfloat162 t = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&t);
+}
+
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 
 // byte offset of element (m, k) of a 128-row K-major BF16 tile in the 128-byte
@@ -203,7 +212,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
             mbar_init(empty + s, 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(a_ready, 128);
+        mbar_init(a_ready, EPI_THREADS);
         mbar_init(done, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -269,25 +278,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
             if (!mbar_wait(done, 0)) atomicOr(P.err, 1u);
         }
     } else {
-        // ---------------- epilogue warps 2..5: TMEM lane quarter = warp % 4
+        // ---------------- epilogue warps 2..9: a warp may only read the TMEM lane
+        // quarter warp % 4, so two warps share each quarter (32 rows) and split the
+        // layer's columns between them
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int m = q * 32 + lane;  // row of the tile owned by this thread
+        const int et = threadIdx.x - 64;
         uint32_t accph = 0;
         bool stopped = false;
         for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const int64_t row = t * TILE_M + m;
-            // stage the input tile: BF16, zero beyond the input width and the batch
+            // stage the input tile (BF16, zero beyond the input width and the batch):
+            // consecutive threads take consecutive 8-column chunks of a row, so the
+            // FP32 reads are coalesced
             {
-                const int K0 = P.layer[0].K;
-                for (int k0 = 0; k0 < P.layer[0].kchunks * KCHUNK; k0 += 8) {
-                    __align__(16) __nv_bfloat16 h[8];
+                const int cpr = P.layer[0].kchunks * KCHUNK / 8;
+                for (int ci = et; ci < TILE_M * cpr; ci += EPI_THREADS) {
+                    const int mm = ci / cpr, k0 = (ci - mm * cpr) * 8;
+                    const int64_t rr = t * TILE_M + mm;
+                    float xv[8];
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         const int k = k0 + e;
-                        const float xv = (row < P.rows && k < P.in_cols && k < K0) ? P.X[row * P.in_cols + k] : 0.f;
-                        h[e] = __float2bfloat16_rn(xv);
+                        xv[e] = (rr < P.rows && k < P.in_cols) ? P.X[rr * P.in_cols + k] : 0.f;
                     }
-                    *(uint4 *)(sA + sw128_offset(m, k0)) = *(const uint4 *)h;
+                    *(uint4 *)(sA + sw128_offset(mm, k0)) =
+                        make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
+                                   pack_bf16x2(xv[6], xv[7]));
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -304,21 +322,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                 if (__any_sync(0xffffffffu, !ok || s_abort)) { stopped = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const bool last = (l == P.L - 1);
-                for (int c0 = 0; c0 < Ly.N; c0 += 32) {
+                const int hw = ((Ly.N / 2 + 31) / 32) * 32;  // columns per half, whole 32-column loads
+                const int cend = min(Ly.N, (half + 1) * hw);
+                for (int c0 = half * hw; c0 < cend; c0 += 32) {
                     float v[32];
                     __syncwarp();  // tcgen05.ld is warp-collective
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
                     if (!last) {
 #pragma unroll
                         for (int c8 = 0; c8 < 32; c8 += 8) {
-                            __align__(16) __nv_bfloat16 h[8];
+                            float g[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn(gelu(v[c8 + e] + __ldg(Ly.bias + c0 + c8 + e)));
-                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = *(const uint4 *)h;
+                            for (int e = 0; e < 8; ++e) {
+                                const int c = c0 + c8 + e;  // columns past N feed zero weights: keep them finite
+                                g[e] = c < Ly.N ? gelu(v[c8 + e] + __ldg(Ly.bias + c)) : 0.f;
+                            }
+                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) =
+                                make_uint4(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]), pack_bf16x2(g[4], g[5]),
+                                           pack_bf16x2(g[6], g[7]));
                         }
                     } else if (row < P.rows) {
-                        for (int e = 0; e < 32 && c0 + e < P.out_cols; ++e)
-                            P.Y[row * P.out_cols + c0 + e] = v[e] + __ldg(Ly.bias + c0 + e);
+#pragma unroll
+                        for (int e = 0; e < 32; ++e)  // static indices keep v in registers
+                            if (c0 + e < P.out_cols) P.Y[row * P.out_cols + c0 + e] = v[e] + __ldg(Ly.bias + c0 + e);
                     }
                 }
                 if (!last) {
