@@ -163,10 +163,18 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-network leg")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per node (0 = autotune)")
     ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--surrogate-only", action="store_true",
+                    help="time only the surrogate network (forward and training step) and print its figures")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate_only:
+        import torch
+        _, _, local = dist_env()
+        torch.cuda.set_device(local)
+        print(json.dumps(bench_surrogate(local, torch.cuda.Stream(local))))
+        return 0
 
     import torch
     ws, rank, local = dist_env()
