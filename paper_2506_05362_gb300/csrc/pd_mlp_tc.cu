@@ -9,8 +9,8 @@
 //               N = layer width, K = 16 per instruction) from the activation
 //               tile A and the weight stage into a TMEM accumulator, and
 //               tcgen05.commit's to release stages and to signal the epilogue;
-//   warps 2-9   epilogue: tcgen05.ld the accumulator (two warps per TMEM lane
-//               quarter = 32 rows, each taking half of the columns), add the
+//   warps 2-17  epilogue: tcgen05.ld the accumulator (four warps per TMEM lane
+//               quarter = 32 rows, each taking a quarter of the columns), add the
 //               bias, exact-erf GELU, round to BF16 and write the next layer's A
 //               tile in the swizzled layout; the last layer writes FP32 outputs.
 //               They also stage the input tile with coalesced reads.
@@ -33,7 +33,7 @@ constexpr int MAX_N = 256;
 constexpr int MAX_K = 256;
 constexpr int A_BYTES = TILE_M * MAX_K * 2;   // 64 KiB: 4 atoms of 128 rows x 128 B
 constexpr int W_STAGE_BYTES = MAX_N * KCHUNK * 2;  // 32 KiB
-constexpr int EPI_THREADS = 256;              // 8 epilogue warps
+constexpr int EPI_THREADS = 512;              // 16 epilogue warps, 4 per TMEM lane quarter
 constexpr int THREADS = 64 + EPI_THREADS;
 constexpr int MAX_LAYERS = 8;
 constexpr unsigned long long WAIT_NS = 1000000000ull;  // a wait gives up after 1 s
@@ -168,7 +168,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<uint32_t *>(&t);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 with erf from the rational
+// approximation of Abramowitz & Stegun, Handbook of Mathematical Functions,
+// eq. 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+// t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7; odd extension to x < 0.  The
+// error is far below the BF16 rounding of the activations (2^-9 relative).
+__device__ __forceinline__ float gelu(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = 1.0f - poly * __expf(-x * x);
+    return 0.5f * z * (1.0f + copysignf(e, z));
+}
 
 // byte offset of element (m, k) of a 128-row K-major BF16 tile in the 128-byte
 // swizzled layout: atoms of 64 columns (16 KiB), 8-row groups of 1024 bytes,
@@ -278,11 +291,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
             if (!mbar_wait(done, 0)) atomicOr(P.err, 1u);
         }
     } else {
-        // ---------------- epilogue warps 2..9: a warp may only read the TMEM lane
-        // quarter warp % 4, so two warps share each quarter (32 rows) and split the
-        // layer's columns between them
+        // ---------------- epilogue warps 2..17: a warp may only read the TMEM lane
+        // quarter warp % 4, so four warps share each quarter (32 rows) and split
+        // the layer's columns between them
         const int q = warp & 3;
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;  // 0..3
         const int m = q * 32 + lane;  // row of the tile owned by this thread
         const int et = threadIdx.x - 64;
         uint32_t accph = 0;
@@ -322,13 +335,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                 if (__any_sync(0xffffffffu, !ok || s_abort)) { stopped = true; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const bool last = (l == P.L - 1);
-                const int hw = ((Ly.N / 2 + 31) / 32) * 32;  // columns per half, whole 32-column loads
-                const int cend = min(Ly.N, (half + 1) * hw);
-                for (int c0 = half * hw; c0 < cend; c0 += 32) {
+                const int hw = ((Ly.N / 4 + 31) / 32) * 32;  // columns per part, whole 32-column loads
+                const int cend = min(Ly.N, (part + 1) * hw);
+                for (int c0 = part * hw; c0 < cend; c0 += 32) {
                     float v[32];
                     __syncwarp();  // tcgen05.ld is warp-collective
                     tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (!last) {
+                    if (!last && c0 + 32 <= Ly.N) {
+                        // a whole chunk: its 32 biases in 8 vector loads (the bias
+                        // array is 128-byte aligned at every 32-column boundary)
+                        float b[32];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const float4 t4 = __ldg((const float4 *)(Ly.bias + c0) + i);
+                            b[4 * i] = t4.x; b[4 * i + 1] = t4.y; b[4 * i + 2] = t4.z; b[4 * i + 3] = t4.w;
+                        }
+#pragma unroll
+                        for (int c8 = 0; c8 < 32; c8 += 8) {
+                            float g[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) g[e] = gelu(v[c8 + e] + b[c8 + e]);
+                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) =
+                                make_uint4(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]), pack_bf16x2(g[4], g[5]),
+                                           pack_bf16x2(g[6], g[7]));
+                        }
+                    } else if (!last) {
 #pragma unroll
                         for (int c8 = 0; c8 < 32; c8 += 8) {
                             float g[8];
