@@ -161,6 +161,47 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// GELU of two values at once on packed FP32x2 instructions, same method as
+// gelu() below (Abramowitz & Stegun eq. 7.1.26 for erf, odd extension):
+//   x = |z|/sqrt2, t = 1/(1 + p x), e = erf(x) = 1 - t P(t) exp(-x^2),
+//   GELU = z/2 (1 + sign(z) e); the Horner coefficients carry the minus sign so
+//   that e is one fused multiply-add, and sign(z) e is e with z's sign bit
+//   (e >= 0).  exp(-x^2) = 2^(-x^2 log2 e) on the hardware ex2.
+__device__ __forceinline__ float2 gelu2(float2 z)
+{
+    const float2 c = make_float2(0.70710678118654752f, 0.70710678118654752f);
+    float2 x = __fmul2_rn(z, c);
+    x.x = fabsf(x.x);
+    x.y = fabsf(x.y);
+    const float2 d = __ffma2_rn(make_float2(0.3275911f, 0.3275911f), x, make_float2(1.0f, 1.0f));
+    const float2 t = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+    float2 q = __ffma2_rn(t, make_float2(-1.061405429f, -1.061405429f), make_float2(1.453152027f, 1.453152027f));
+    q = __ffma2_rn(t, q, make_float2(-1.421413741f, -1.421413741f));
+    q = __ffma2_rn(t, q, make_float2(0.284496736f, 0.284496736f));
+    q = __ffma2_rn(t, q, make_float2(-0.254829592f, -0.254829592f));
+    q = __fmul2_rn(t, q);  // -t P(t)
+    const float2 w = __fmul2_rn(x, __fmul2_rn(x, make_float2(-1.4426950408889634f, -1.4426950408889634f)));
+    const float2 ex = make_float2(ex2_approx(w.x), ex2_approx(w.y));
+    const float2 e = __ffma2_rn(q, ex, make_float2(1.0f, 1.0f));
+    const float2 es = make_float2(__uint_as_float(__float_as_uint(e.x) | (__float_as_uint(z.x) & 0x80000000u)),
+                                  __uint_as_float(__float_as_uint(e.y) | (__float_as_uint(z.y) & 0x80000000u)));
+    const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+    return __ffma2_rn(hz, es, hz);
+}
+
 // two floats rounded to BF16 (nearest-even), packed low = a, high = b, in registers
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
 {
@@ -352,12 +393,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                         }
 #pragma unroll
                         for (int c8 = 0; c8 < 32; c8 += 8) {
-                            float g[8];
+                            uint32_t pk[4];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) g[e] = gelu(v[c8 + e] + b[c8 + e]);
-                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) =
-                                make_uint4(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]), pack_bf16x2(g[4], g[5]),
-                                           pack_bf16x2(g[6], g[7]));
+                            for (int e = 0; e < 8; e += 2) {
+                                const float2 zz = __fadd2_rn(make_float2(v[c8 + e], v[c8 + e + 1]),
+                                                             make_float2(b[c8 + e], b[c8 + e + 1]));
+                                const float2 g2 = gelu2(zz);
+                                pk[e / 2] = pack_bf16x2(g2.x, g2.y);
+                            }
+                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                         }
                     } else if (!last) {
 #pragma unroll
