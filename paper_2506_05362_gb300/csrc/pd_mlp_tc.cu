@@ -1,7 +1,9 @@
 // Fused MLP forward on the 5th-generation tensor cores (tcgen05, sm_100+).
 //
-// One persistent CTA works on 128-row tiles of the batch and keeps the tile's
-// activations in shared memory through every layer:
+// One persistent CTA per SM works on 128-row tiles of the batch, two at a time
+// (slots 0 and 1, each with its activation tile in shared memory and its own
+// 256-column TMEM accumulator), so that the tensor cores compute one slot's
+// layer while the epilogue warps finish the other's:
 //   warp 0      TMA producer: streams each layer's weights W_l [N x K] (BF16,
 //               K-major) in 64-column chunks into a 3-stage ring, 128-byte
 //               swizzle, completion counted on mbarriers;
@@ -243,37 +245,64 @@ struct Maps {
     CUtensorMap m[MAX_LAYERS];
 };
 
+// The CTA's tiles are blockIdx.x + k * gridDim.x, k = 0, 1, ...; they go in
+// pairs (slot 0 = even k, slot 1 = odd k), each slot with its own activation
+// tile in shared memory and its own TMEM accumulator.  All three roles walk the
+// same item sequence: for each pair, for each layer, slot 0 then slot 1 (an odd
+// last tile has slot-0 items only).  The MMAs of one slot's item run while the
+// epilogue warps finish the other slot's previous item.
+__device__ __forceinline__ int64_t pair_tile(int64_t r, int b) { return blockIdx.x + (2 * r + b) * (int64_t)gridDim.x; }
+
+// input tile -> BF16 swizzled A tile (zero beyond the input width and the batch);
+// consecutive threads take consecutive 8-column chunks of a row (coalesced reads)
+__device__ __forceinline__ void stage_input(const Params &P, int64_t t, unsigned char *sA, int et)
+{
+    const int cpr = P.layer[0].kchunks * KCHUNK / 8;
+    for (int ci = et; ci < TILE_M * cpr; ci += EPI_THREADS) {
+        const int mm = ci / cpr, k0 = (ci - mm * cpr) * 8;
+        const int64_t rr = t * TILE_M + mm;
+        float xv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int k = k0 + e;
+            xv[e] = (rr < P.rows && k < P.in_cols) ? P.X[rr * P.in_cols + k] : 0.f;
+        }
+        *(uint4 *)(sA + sw128_offset(mm, k0)) = make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]),
+                                                           pack_bf16x2(xv[4], xv[5]), pack_bf16x2(xv[6], xv[7]));
+    }
+}
+
 __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant__ Maps maps, const Params P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte alignment for the swizzle atoms
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *sA = base;                                 // activations (A operand)
-    unsigned char *sW = base + A_BYTES;                       // weight stages
-    float *sBias = (float *)(sW + STAGES * W_STAGE_BYTES);    // MAX_N floats
-    uint64_t *full = (uint64_t *)(sBias + MAX_N);
+    unsigned char *sW = base + 2 * A_BYTES;                   // weight stages
+    uint64_t *full = (uint64_t *)(sW + STAGES * W_STAGE_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *acc_full = empty + STAGES;
-    uint64_t *a_ready = acc_full + 1;
-    uint64_t *done = a_ready + 1;
+    uint64_t *acc_full = empty + STAGES;  // [2], per slot
+    uint64_t *a_ready = acc_full + 2;     // [2], per slot
+    uint64_t *done = a_ready + 2;
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full + s, 1);
-            mbar_init(empty + s, 1);
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(full + q, 1);
+            mbar_init(empty + q, 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(a_ready, EPI_THREADS);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(acc_full + q, 1);
+            mbar_init(a_ready + q, EPI_THREADS);
+        }
         mbar_init(done, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {  // TMEM: 256 columns x 128 lanes of FP32 accumulator
+    if (warp == 1) {  // TMEM: two accumulators of 256 columns x 128 lanes (FP32)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(MAX_N));
+                     "r"(2 * MAX_N));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -281,23 +310,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int64_t ntiles = (P.rows + TILE_M - 1) / TILE_M;
+    const int64_t my = ntiles > (int64_t)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t rounds = (my + 1) / 2;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: each item streams its layer's weights
         if (lane == 0) {
             int s = 0;
             uint32_t ph = 0;
             int last_ph[STAGES];
             for (int q = 0; q < STAGES; ++q) last_ph[q] = -1;
-            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x)
+            for (int64_t r = 0; r < rounds && !s_abort; ++r)
                 for (int l = 0; l < P.L && !s_abort; ++l)
-                    for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
-                        if (!mbar_wait(empty + s, ph ^ 1)) { atomicOr(P.err, 1u); s_abort = 1; break; }
-                        mbar_expect_tx(full + s, (uint32_t)(P.layer[l].N * KCHUNK * 2));
-                        tma_load_2d(sW + s * W_STAGE_BYTES, &maps.m[l], full + s, kc * KCHUNK, 0);
-                        last_ph[s] = (int)ph;
-                        if (++s == STAGES) { s = 0; ph ^= 1; }
-                    }
+                    for (int b = 0; b < 2 && 2 * r + b < my && !s_abort; ++b)
+                        for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
+                            if (!mbar_wait(empty + s, ph ^ 1)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                            mbar_expect_tx(full + s, (uint32_t)(P.layer[l].N * KCHUNK * 2));
+                            tma_load_2d(sW + s * W_STAGE_BYTES, &maps.m[l], full + s, kc * KCHUNK, 0);
+                            last_ph[s] = (int)ph;
+                            if (++s == STAGES) { s = 0; ph ^= 1; }
+                        }
             // no copy may still be landing in shared memory when the CTA exits
             for (int q = 0; q < STAGES; ++q)
                 if (last_ph[q] >= 0 && !mbar_wait(full + q, (uint32_t)last_ph[q])) atomicOr(P.err, 1u);
@@ -306,27 +338,30 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
         // ---------------- MMA issuer
         if (lane == 0) {
             int s = 0;
-            uint32_t ph = 0, aph = 0;
-            for (int64_t t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x)
-                for (int l = 0; l < P.L && !s_abort; ++l) {
-                    if (!mbar_wait(a_ready, aph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
-                    aph ^= 1;
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t idesc = idesc_bf16(TILE_M, P.layer[l].N);
-                    for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
-                        if (!mbar_wait(full + s, ph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+            uint32_t ph = 0, aph[2] = {0u, 0u};
+            for (int64_t r = 0; r < rounds && !s_abort; ++r)
+                for (int l = 0; l < P.L && !s_abort; ++l)
+                    for (int b = 0; b < 2 && 2 * r + b < my && !s_abort; ++b) {
+                        if (!mbar_wait(a_ready + b, aph[b])) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                        aph[b] ^= 1;
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t a0 = smem_u32(sA + kc * (TILE_M * 128));
-                        const uint32_t b0 = smem_u32(sW + s * W_STAGE_BYTES);
+                        const uint32_t idesc = idesc_bf16(TILE_M, P.layer[l].N);
+                        const uint32_t d = tmem + (uint32_t)(b * MAX_N);
+                        const unsigned char *sA = base + b * A_BYTES;
+                        for (int kc = 0; kc < P.layer[l].kchunks; ++kc) {
+                            if (!mbar_wait(full + s, ph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                            const uint32_t a0 = smem_u32(sA + kc * (TILE_M * 128));
+                            const uint32_t b0 = smem_u32(sW + s * W_STAGE_BYTES);
 #pragma unroll
-                        for (int kk = 0; kk < KCHUNK / 16; ++kk)
-                            mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
-                                     (kc | kk) != 0);
-                        mma_commit(empty + s);  // stage free once these MMAs completed
-                        if (++s == STAGES) { s = 0; ph ^= 1; }
+                            for (int kk = 0; kk < KCHUNK / 16; ++kk)
+                                mma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc,
+                                         (kc | kk) != 0);
+                            mma_commit(empty + s);  // stage free once these MMAs completed
+                            if (++s == STAGES) { s = 0; ph ^= 1; }
+                        }
+                        mma_commit(acc_full + b);  // this slot's accumulator complete
                     }
-                    mma_commit(acc_full);  // accumulator complete
-                }
             // every MMA issued by this thread has completed before TMEM is freed
             mma_commit(done);
             if (!mbar_wait(done, 0)) atomicOr(P.err, 1u);
@@ -337,104 +372,94 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
         // the layer's columns between them
         const int q = warp & 3;
         const int part = (warp - 2) >> 2;  // 0..3
-        const int m = q * 32 + lane;  // row of the tile owned by this thread
+        const int m = q * 32 + lane;       // row of the tile owned by this thread
         const int et = threadIdx.x - 64;
-        uint32_t accph = 0;
+        uint32_t accph[2] = {0u, 0u};
         bool stopped = false;
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int64_t row = t * TILE_M + m;
-            // stage the input tile (BF16, zero beyond the input width and the batch):
-            // consecutive threads take consecutive 8-column chunks of a row, so the
-            // FP32 reads are coalesced
-            {
-                const int cpr = P.layer[0].kchunks * KCHUNK / 8;
-                for (int ci = et; ci < TILE_M * cpr; ci += EPI_THREADS) {
-                    const int mm = ci / cpr, k0 = (ci - mm * cpr) * 8;
-                    const int64_t rr = t * TILE_M + mm;
-                    float xv[8];
+        for (int b = 0; b < 2 && b < my; ++b) stage_input(P, pair_tile(0, b), base + b * A_BYTES, et);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        for (int b = 0; b < 2 && b < my; ++b) mbar_arrive(a_ready + b);
+        for (int64_t r = 0; r < rounds && !stopped; ++r)
+            for (int l = 0; l < P.L && !stopped; ++l)
+                for (int b = 0; b < 2 && 2 * r + b < my; ++b) {
+                    const Layer &Ly = P.layer[l];
+                    unsigned char *sA = base + b * A_BYTES;
+                    const int64_t row = pair_tile(r, b) * TILE_M + m;
+                    // the decision to stop is warp-uniform, so that no lane is left
+                    // waiting in a warp-collective instruction
+                    __syncwarp();
+                    const bool ok = mbar_wait(acc_full + b, accph[b]);
+                    if (!ok) { atomicOr(P.err, 1u); s_abort = 1; }
+                    accph[b] ^= 1;
+                    if (__any_sync(0xffffffffu, !ok || s_abort)) { stopped = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const bool last = (l == P.L - 1);
+                    const int hw = ((Ly.N / 4 + 31) / 32) * 32;  // columns per part, whole 32-column loads
+                    const int cend = min(Ly.N, (part + 1) * hw);
+                    const uint32_t tacc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * MAX_N);
+                    for (int c0 = part * hw; c0 < cend; c0 += 32) {
+                        float v[32];
+                        __syncwarp();  // tcgen05.ld is warp-collective
+                        tmem_ld32(tacc + (uint32_t)c0, v);
+                        if (!last && c0 + 32 <= Ly.N) {
+                            // a whole chunk: its 32 biases in 8 vector loads (the bias
+                            // array is 128-byte aligned at every 32-column boundary)
+                            float bb[32];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int k = k0 + e;
-                        xv[e] = (rr < P.rows && k < P.in_cols) ? P.X[rr * P.in_cols + k] : 0.f;
+                            for (int i = 0; i < 8; ++i) {
+                                const float4 t4 = __ldg((const float4 *)(Ly.bias + c0) + i);
+                                bb[4 * i] = t4.x; bb[4 * i + 1] = t4.y; bb[4 * i + 2] = t4.z; bb[4 * i + 3] = t4.w;
+                            }
+#pragma unroll
+                            for (int c8 = 0; c8 < 32; c8 += 8) {
+                                uint32_t pk[4];
+#pragma unroll
+                                for (int e = 0; e < 8; e += 2) {
+                                    const float2 zz = __fadd2_rn(make_float2(v[c8 + e], v[c8 + e + 1]),
+                                                                 make_float2(bb[c8 + e], bb[c8 + e + 1]));
+                                    const float2 g2 = gelu2(zz);
+                                    pk[e / 2] = pack_bf16x2(g2.x, g2.y);
+                                }
+                                *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                            }
+                        } else if (!last) {
+#pragma unroll
+                            for (int c8 = 0; c8 < 32; c8 += 8) {
+                                float g[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) {
+                                    const int c = c0 + c8 + e;  // columns past N feed zero weights: keep them finite
+                                    g[e] = c < Ly.N ? gelu(v[c8 + e] + __ldg(Ly.bias + c)) : 0.f;
+                                }
+                                *(uint4 *)(sA + sw128_offset(m, c0 + c8)) =
+                                    make_uint4(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]),
+                                               pack_bf16x2(g[4], g[5]), pack_bf16x2(g[6], g[7]));
+                            }
+                        } else if (row < P.rows) {
+#pragma unroll
+                            for (int e = 0; e < 32; ++e)  // static indices keep v in registers
+                                if (c0 + e < P.out_cols) P.Y[row * P.out_cols + c0 + e] = v[e] + __ldg(Ly.bias + c0 + e);
+                        }
                     }
-                    *(uint4 *)(sA + sw128_offset(mm, k0)) =
-                        make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
-                                   pack_bf16x2(xv[6], xv[7]));
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(a_ready);
-            for (int l = 0; l < P.L; ++l) {
-                const Layer &Ly = P.layer[l];
-                // the decision to stop is warp-uniform, so that no lane is left
-                // waiting in a warp-collective instruction
-                __syncwarp();
-                const bool ok = mbar_wait(acc_full, accph);
-                if (!ok) { atomicOr(P.err, 1u); s_abort = 1; }
-                accph ^= 1;
-                if (__any_sync(0xffffffffu, !ok || s_abort)) { stopped = true; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const bool last = (l == P.L - 1);
-                const int hw = ((Ly.N / 4 + 31) / 32) * 32;  // columns per part, whole 32-column loads
-                const int cend = min(Ly.N, (part + 1) * hw);
-                for (int c0 = part * hw; c0 < cend; c0 += 32) {
-                    float v[32];
-                    __syncwarp();  // tcgen05.ld is warp-collective
-                    tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                    if (!last && c0 + 32 <= Ly.N) {
-                        // a whole chunk: its 32 biases in 8 vector loads (the bias
-                        // array is 128-byte aligned at every 32-column boundary)
-                        float b[32];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i) {
-                            const float4 t4 = __ldg((const float4 *)(Ly.bias + c0) + i);
-                            b[4 * i] = t4.x; b[4 * i + 1] = t4.y; b[4 * i + 2] = t4.z; b[4 * i + 3] = t4.w;
-                        }
-#pragma unroll
-                        for (int c8 = 0; c8 < 32; c8 += 8) {
-                            uint32_t pk[4];
-#pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                const float2 zz = __fadd2_rn(make_float2(v[c8 + e], v[c8 + e + 1]),
-                                                             make_float2(b[c8 + e], b[c8 + e + 1]));
-                                const float2 g2 = gelu2(zz);
-                                pk[e / 2] = pack_bf16x2(g2.x, g2.y);
-                            }
-                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                        }
-                    } else if (!last) {
-#pragma unroll
-                        for (int c8 = 0; c8 < 32; c8 += 8) {
-                            float g[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int c = c0 + c8 + e;  // columns past N feed zero weights: keep them finite
-                                g[e] = c < Ly.N ? gelu(v[c8 + e] + __ldg(Ly.bias + c)) : 0.f;
-                            }
-                            *(uint4 *)(sA + sw128_offset(m, c0 + c8)) =
-                                make_uint4(pack_bf16x2(g[0], g[1]), pack_bf16x2(g[2], g[3]), pack_bf16x2(g[4], g[5]),
-                                           pack_bf16x2(g[6], g[7]));
-                        }
-                    } else if (row < P.rows) {
-#pragma unroll
-                        for (int e = 0; e < 32; ++e)  // static indices keep v in registers
-                            if (c0 + e < P.out_cols) P.Y[row * P.out_cols + c0 + e] = v[e] + __ldg(Ly.bias + c0 + e);
+                    if (!last) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(a_ready + b);
+                    } else if (2 * (r + 1) + b < my) {
+                        // this slot's next tile; the accumulator has been read, and
+                        // its last MMAs (which read sA) have completed
+                        stage_input(P, pair_tile(r + 1, b), sA, et);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        mbar_arrive(a_ready + b);
                     }
                 }
-                if (!last) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    mbar_arrive(a_ready);
-                }
-            }
-            if (stopped) break;
-        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     __syncwarp();
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MAX_N));
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * MAX_N));
 }
 
 typedef CUresult (*encode_fn_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -459,7 +484,7 @@ encode_fn_t encoder()
 
 }  // namespace
 
-size_t mlp_tc_smem() { return 1024 + A_BYTES + STAGES * W_STAGE_BYTES + MAX_N * 4 + 256; }
+size_t mlp_tc_smem() { return 1024 + 2 * A_BYTES + STAGES * W_STAGE_BYTES + 256; }
 
 // Forward of an MLP whose layers all fit the fused kernel (K, N <= 256).
 // W[l]: padded BF16 weights [pad_out x pad_in] row-major; bias[l]: pad_out
