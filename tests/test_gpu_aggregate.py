@@ -1,0 +1,97 @@
+"""The 1000-grain aggregate at full size (star-shaped glass grains, h = R/12,
+~7.6 M nodes, ~0.8 G directed bonds) in one batched launch, in the launch
+configuration of the autotuner: sampled rows against the oracle computed one by
+one (brute-force bond rows over all nodes, forces on a sub-problem made of the
+sampled rows and their oracle neighbours)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_05362_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def agg():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2506_05362_gb300 import pd
+    sc = S.aggregate(n_grains=1000, seed=0)
+    ctx = pd.Context.from_scenario(sc)
+    yield sc, ctx
+    ctx.close()
+
+
+def sample_rows(sc, k, seed):
+    rng = np.random.default_rng(seed)
+    return np.sort(rng.choice(sc.n, k, replace=False))
+
+
+def test_aggregate_bond_rows_sampled(agg):
+    sc, ctx = agg
+    assert sc.n > 5_000_000
+    rp, col = ctx.bonds()
+    assert rp[-1] > 500_000_000
+    for i in sample_rows(sc, 40, 1):
+        ref = oracle.bond_row(sc.x, sc.grain, sc.horizon, int(i))
+        assert np.array_equal(col[rp[i]:rp[i + 1]], ref), f"row {i}"
+
+
+def test_aggregate_forces_sampled(agg):
+    """Forces at a perturbed state (an affine stretch of ~0.7 s0 plus noise) on
+    sampled rows; broken sets agree outside the tolerance band."""
+    sc, ctx = agg
+    rows = sample_rows(sc, 60, 2)
+    K, c, s0, Kn = oracle.constants(sc.material.E, sc.material.G0, sc.horizon, sc.material.contact_factor)
+    rng = np.random.default_rng(3)
+    A = np.diag([0.7 * s0, -0.2 * s0, 0.4 * s0]) + rng.normal(0, 0.1 * s0, (3, 3))
+    u = (sc.x - sc.x.mean(0)) @ A.T + rng.normal(0, 0.3 * s0 * sc.h, sc.x.shape)
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    rp, col = ctx.bonds()
+    _, _, broken, _ = ctx.get_state()
+    # oracle sub-problem: the sampled rows with their own (oracle) bond rows, and
+    # their neighbours as bond-less nodes carrying position and volume
+    orows = [oracle.bond_row(sc.x, sc.grain, sc.horizon, int(i)) for i in rows]
+    nodes = np.unique(np.concatenate([rows] + orows))
+    local = {int(g): k for k, g in enumerate(nodes)}
+    rptr = np.zeros(len(nodes) + 1, np.int64)
+    cols = []
+    for i, r in zip(rows, orows):
+        rptr[local[int(i)] + 1] = len(r)
+        cols.append(np.array([local[int(j)] for j in r], np.int32))
+    rptr = np.cumsum(rptr)
+    sub = oracle.Model(sc.x[nodes], sc.vol[nodes], sc.grain[nodes], rptr, np.concatenate(cols), sc.material,
+                       sc.horizon, contact=False)
+    sub.u = u[nodes].copy()
+    sub.forces()
+    band = 1e-6
+    for i, r in zip(rows, orows):
+        k = local[int(i)]
+        gb = broken[rp[i]:rp[i + 1]].astype(bool)
+        ob = sub.broken[rptr[k]:rptr[k + 1]].astype(bool)
+        xi = sc.x[r] - sc.x[i]
+        y = xi + (u[r] - u[i])
+        s = (np.linalg.norm(y, axis=1) - np.linalg.norm(xi, axis=1)) / np.linalg.norm(xi, axis=1)
+        assert np.all(np.abs(s[gb != ob] - s0) < band * s0)
+    assert sub.broken.sum() > 0, "the state should break some bonds"
+    # oracle forces with the GPU's decisions on band bonds
+    for i, r in zip(rows, orows):
+        k = local[int(i)]
+        sub.broken[rptr[k]:rptr[k + 1]] = broken[rp[i]:rp[i + 1]]
+    Fo = sub.forces(frozen=True)[[local[int(i)] for i in rows]]
+    Fg = F[rows]
+    assert np.linalg.norm(Fg - Fo) / np.linalg.norm(Fo) <= 1e-5
+
+
+def test_aggregate_steps_finite_and_tuned(agg):
+    sc, ctx = agg
+    lanes, tiled, ms = ctx.tuning()
+    assert lanes in (4, 8, 16, 32)
+    ctx.set_state(u=np.zeros_like(sc.x), v=sc.v0)
+    dt = 0.8 * ctx.stable_dt()
+    ctx.step(dt, 50)
+    u, v, broken, t = ctx.get_state()
+    assert np.all(np.isfinite(u)) and np.all(np.isfinite(v))
+    assert t == pytest.approx(50 * dt, rel=1e-12)
