@@ -30,6 +30,18 @@ sys.path.insert(0, ROOT)
 METRIC = "node-steps/s & bond-updates/s vs FP64 GPU path; HBM roofline %; RVE surrogate err"
 WORKLOAD = ("kalthoff notched steel plate 200x100x9 mm, h=1 mm, 178,200 nodes, delta=4h, "
             "E=190 GPa, G0=2.2e4 J/m^2, edge segment at 32 m/s, dt=0.8 dt_crit")
+WORKLOADS = {
+    "plate": WORKLOAD,
+    "sphere": "glass sphere radius 1 mm, h=0.1 mm, 4,139 nodes, delta=3h, plates at 1 m/s, dt=0.8 dt_crit",
+    "hollow": "glass hollow sphere R=1 mm, r=0.7 mm, h=0.02 mm, 343,846 nodes, delta=3h, plates at 5 m/s",
+    "aggregate": "1000 star-shaped glass grains, h=R/12, ~7.6 M nodes, delta=3h, six walls, top wall at 10 m/s",
+}
+
+
+def make_workload(name):
+    from paper_2506_05362_gb300 import scenarios as S
+    return {"plate": S.kalthoff, "sphere": S.sphere, "hollow": S.hollow,
+            "aggregate": lambda: S.aggregate(n_grains=1000, seed=0)}[name]()
 BYTES_PER_NODE = 170.0      # x, V, u (r/w), v (r/w), F, row pointers per node and step
 BYTES_PER_BOND = 4.0 + 1.0 / 8.0  # neighbour index + broken bit per directed bond
 
@@ -157,8 +169,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(sc, steps=8):
+def cpu_baseline(sc, name="plate"):
+    """The single-threaded oracle on a bounded sample: 8 steps (fewer above ~1 M nodes)."""
     import oracle
+    steps = 8 if sc.n < 1_000_000 else 1
     m = oracle.Model.from_scenario(sc)
     dt = 0.8 * m.stable_dt()
     m.init()
@@ -166,7 +180,7 @@ def cpu_baseline(sc, steps=8):
     m.step(dt, steps)
     el = time.perf_counter() - t0
     return {"value": sc.n * steps / el, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the full plate (single-threaded FP64 C oracle)",
+            "sample": f"{steps} steps of the full {name} workload (single-threaded FP64 C oracle)",
             "bond_updates_per_s": len(m.col) * steps / el}
 
 
@@ -183,6 +197,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-network leg")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per node (0 = autotune)")
     ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--workload", default="plate", choices=sorted(WORKLOADS),
+                    help="workload of the timed steps (the headline figure is the plate)")
     ap.add_argument("--no-aggregate", action="store_true",
                     help="skip the 1000-grain aggregate leg (7.6 M nodes, one batched launch)")
     ap.add_argument("--surrogate-only", action="store_true",
@@ -206,7 +222,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2506_05362_gb300 import pd, scenarios as S
 
-    sc = S.kalthoff()
+    sc = make_workload(args.workload)
     stream = torch.cuda.Stream(local)
     ctx = pd.Context.from_scenario(sc, precision=args.precision, device=local, stream=stream,
                                    lanes=args.lanes, tiles={"auto": 0, "on": 1, "off": -1}[args.tiles])
@@ -256,7 +272,7 @@ def main():
     if os.path.exists(traffic_file):
         try:
             tr = json.load(open(traffic_file))
-            if tr.get("kernel_source_hash") == kernel_hash():
+            if tr.get("kernel_source_hash") == kernel_hash() and args.workload == "plate":
                 roof["traffic"] = tr["bytes_per_launch"]
         except Exception:
             pass
@@ -303,12 +319,12 @@ def main():
     aggregate = None if args.no_aggregate else bench_aggregate(local, stream)
     if rank != 0:
         return
-    cpu = None if args.no_cpu_baseline else cpu_baseline(sc)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(sc, args.workload)
     line = {"metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": n, "directed_bonds": B, "precision": args.precision,
+            "config": {"workload": WORKLOADS[args.workload], "nodes": n, "directed_bonds": B, "precision": args.precision,
                        "l2": "inputs larger than L2: ~0.18 GB streamed from HBM per step (129 MB L2)",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "bond_updates_per_s": ws * B * args.steps / (ms * 1e-3),
