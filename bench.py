@@ -250,6 +250,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     _, _, launches = ctx.last_step_stats()
+    steps_done, rebuilds, rollbacks = ctx.step_counters()
     ms = reduce_max(ms, ws, device=f"cuda:{local}")
     ms_step = ms / args.steps
     value = ws * n * args.steps / (ms * 1e-3)
@@ -330,7 +331,7 @@ def main():
             "bond_updates_per_s": ws * B * args.steps / (ms * 1e-3),
             "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "fp64_gpu_path": fp64, "surrogate": surrogate, "aggregate": aggregate,
-            "tuning": tuning}
+            "tuning": tuning, "contact_rebuilds": rebuilds, "rollbacks": rollbacks, "steps_run": steps_done}
     print(json.dumps(line), flush=True)
     ctx.close()
 

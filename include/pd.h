@@ -240,6 +240,11 @@ pd_status pd_set_profiling(pd_ctx *ctx, int on);
  * launched by those segments. */
 pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, int64_t *launches);
 
+/* Counters since pd_create (each pointer nullable): steps taken, contact-list
+ * rebuilds of those steps, and segments rolled back and rerun because the list
+ * went stale or overflowed (see pd_step). */
+pd_status pd_step_counters(pd_ctx *ctx, int64_t *steps, int64_t *rebuilds, int64_t *rollbacks);
+
 const char *pd_last_error(const pd_ctx *ctx);
 void pd_destroy(pd_ctx *ctx);
 

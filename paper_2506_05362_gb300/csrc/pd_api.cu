@@ -89,6 +89,7 @@ struct pd_ctx {
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double impulse_span = 0;       // time covered by the wall impulses since their reset
+    int64_t n_rollbacks = 0, n_rebuilds = 0, n_steps = 0;  // since creation (successful segments' rebuilds)
     double last_ms = 0, last_force_ms = 0;
     int64_t last_launches = 0;
     bool profiling = false;
@@ -992,11 +993,18 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches,
             }
             *ms_out = ms;
             *force_ms_out = fm;
+            c->n_steps += m;
+            if (c->opt.contact)  // each chunk rebuilds at its steps 0, k, 2k, ...
+                for (int64_t left = m; left > 0; left -= c->opt.graph_chunk) {
+                    const int64_t len = std::min<int64_t>(left, c->opt.graph_chunk), kk = std::min<int64_t>(k, len);
+                    c->n_rebuilds += (len + kk - 1) / kk;
+                }
             c->t += dt * (double)m;
             c->impulse_span += dt * (double)m;
             return PD_OK;
         }
         c->cur = cur0;
+        ++c->n_rollbacks;
         s = snapshot(c, true);
         if (s) return s;
         if (e & (PDE_NONFINITE | PDE_WALL)) {
@@ -1307,6 +1315,15 @@ pd_status pd_set_profiling(pd_ctx *c, int on)
 {
     if (!c) return PD_EINVAL;
     c->profiling = on != 0;
+    return PD_OK;
+}
+
+pd_status pd_step_counters(pd_ctx *c, int64_t *steps, int64_t *rebuilds, int64_t *rollbacks)
+{
+    if (!c) return PD_EINVAL;
+    if (steps) *steps = c->n_steps;
+    if (rebuilds) *rebuilds = c->n_rebuilds;
+    if (rollbacks) *rollbacks = c->n_rollbacks;
     return PD_OK;
 }
 

@@ -94,6 +94,7 @@ def lib():
                 "pd_set_state": (i32, [P, P, P, P, P]),
                 "pd_tuning": (i32, [P, P, P, P]),
                 "pd_last_step_stats": (i32, [P, P, P, P]),
+                "pd_step_counters": (i32, [P, P, P, P]),
                 "pd_set_profiling": (i32, [P, i32]),
                 "pd_stable_dt_noalloc": (i32, [i64, P, P, P, P, f64, f64, P, P]),
                 "pd_last_error": (ctypes.c_char_p, [P]),
@@ -296,6 +297,12 @@ def pd_tuning(h):
     return lanes.value, bool(tiled.value), ms
 
 
+def pd_step_counters(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pd_step_counters(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
+    return a.value, b.value, c.value
+
+
 def pd_last_step_stats(h):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(lib().pd_last_step_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
@@ -417,6 +424,10 @@ class Context:
 
     def last_step_stats(self):
         return pd_last_step_stats(self.h)
+
+    def step_counters(self):
+        """(steps, contact-list rebuilds, rolled-back segments) since creation."""
+        return pd_step_counters(self.h)
 
     def close(self):
         if self.h:
