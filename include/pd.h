@@ -162,9 +162,10 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
  *   v += dt/2 a; u += dt v; walls move; a = (F(u) + b)/rho; v += dt/2 a,
  * where F is the bond force with breaking (Eq. peri-damage), contact and wall
  * force.  Captured and replayed as CUDA graphs.  Blocks until done.  The
- * steps run in segments of 8 graph chunks (512 steps by default); a segment
+ * steps run in segments of 2 graph chunks (128 steps by default); a segment
  * whose contact list went stale or overflowed is rolled back to its own start
- * and rerun with a shorter rebuild period or larger lists.
+ * and rerun with a shorter rebuild period or larger lists.  The contact list is
+ * rebuilt often enough for the fastest node (or wall) to double its speed.
  * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL
  * (dt <= 0, nsteps < 0), PD_ENONFINITE / PD_EWALL (state restored to the start
  * of the segment in which it happened, so t tells how far the call got, and

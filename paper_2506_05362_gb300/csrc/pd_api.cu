@@ -90,6 +90,7 @@ struct pd_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double impulse_span = 0;       // time covered by the wall impulses since their reset
     int64_t n_rollbacks = 0, n_rebuilds = 0, n_steps = 0;  // since creation (successful segments' rebuilds)
+    int k_cap = 1 << 30;  // rebuild period a stale list forced down; relaxed by 2x per clean segment
     double last_ms = 0, last_force_ms = 0;
     int64_t last_launches = 0;
     bool profiling = false;
@@ -877,7 +878,7 @@ static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, G
     return PD_OK;
 }
 
-#define PD_SEGMENT_CHUNKS 8  // graph chunks per rollback segment of pd_step
+#define PD_SEGMENT_CHUNKS 2  // graph chunks per rollback segment of pd_step
 
 static pd_status snapshot(pd_ctx *c, bool restore)
 {
@@ -922,8 +923,10 @@ static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
     for (int l = 0; l < c->walls.nw; ++l)
         vm = std::max(vm, sqrt(c->walls.v[l][0] * c->walls.v[l][0] + c->walls.v[l][1] * c->walls.v[l][1] +
                                c->walls.v[l][2] * c->walls.v[l][2]));
-    double steps = skin_of(c) / (2.0 * 1.5 * dt * std::max(vm, 1e-30));
-    *k = (int)std::max(1.0, std::min(steps, (double)c->opt.graph_chunk));
+    // a node struck by a moving wall can leave at twice the wall speed: allow the
+    // fastest speed now to double before the list must be rebuilt
+    double steps = skin_of(c) / (2.0 * 2.0 * dt * std::max(vm, 1e-30));
+    *k = (int)std::max(1.0, std::min({steps, (double)c->opt.graph_chunk, (double)c->k_cap}));
     return PD_OK;
 }
 
@@ -993,6 +996,7 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches,
             }
             *ms_out = ms;
             *force_ms_out = fm;
+            if (attempt == 0 && c->k_cap < (1 << 29)) c->k_cap *= 2;  // a clean segment relaxes the cap
             c->n_steps += m;
             if (c->opt.contact)  // each chunk rebuilds at its steps 0, k, 2k, ...
                 for (int64_t left = m; left > 0; left -= c->opt.graph_chunk) {
@@ -1019,6 +1023,7 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches,
         if (e & PDE_SKIN) {
             if (k == 1) return fail(c, PD_ETIMEOUT, "contact list stale even when rebuilt every step");
             k = std::max(1, k / 2);
+            c->k_cap = k;  // later segments start from the period that is being tried now
         }
     }
     return fail(c, PD_ECAPACITY, "pd_step retried too often");
