@@ -162,7 +162,8 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
  *   v += dt/2 a; u += dt v; walls move; a = (F(u) + b)/rho; v += dt/2 a,
  * where F is the bond force with breaking (Eq. peri-damage), contact and wall
  * force.  Captured and replayed as CUDA graphs.  Blocks until done.  The
- * steps run in segments of 2 graph chunks (128 steps by default); a segment
+ * steps run in segments of 2 graph chunks (up to 128 steps; a chunk is the
+ * largest multiple of the rebuild period within graph_chunk); a segment
  * whose contact list went stale or overflowed is rolled back to its own start
  * and rerun with a shorter rebuild period or larger lists.  The contact list is
  * rebuilt often enough for the fastest node (or wall) to double its speed.

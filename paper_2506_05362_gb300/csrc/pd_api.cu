@@ -930,12 +930,21 @@ static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
     return PD_OK;
 }
 
+// graph chunk length for rebuild period k: the largest multiple of k that fits
+// the chunk size, so that rebuilds fall exactly every k steps across chunks
+static int chunk_for(const pd_ctx *c, int k)
+{
+    const int gc = c->opt.graph_chunk;
+    return k < gc ? (gc / k) * k : gc;
+}
+
 static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t *launches)
 {
     int64_t left = nsteps;
     *launches = 0;
+    const int chunk = chunk_for(c, k);
     while (left > 0) {
-        int steps = (int)std::min<int64_t>(left, c->opt.graph_chunk);
+        int steps = (int)std::min<int64_t>(left, chunk);
         if (c->profiling) {
             int kk = std::min(k, steps);
             if ((int)c->prof_ev.size() < c->prof_used + 2 * steps) {
@@ -967,12 +976,15 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
 // snapshot, the graph chunks, one error check.  A segment whose contact list
 // went stale or outgrew its capacity is rolled back to its own start and run
 // again (shorter rebuild period, larger lists).
-static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches, double *ms_out,
+static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out, int64_t *launches, double *ms_out,
                              double *force_ms_out)
 {
     int k;
     pd_status s = rebuild_period(c, dt, &k);
     if (s) return s;
+    // a rollback costs at most one segment of work
+    int64_t m = std::min<int64_t>(left, (int64_t)PD_SEGMENT_CHUNKS * chunk_for(c, k));
+    *m_out = m;
     const int cur0 = c->cur;
     s = snapshot(c, false);
     if (s) return s;
@@ -999,8 +1011,8 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t m, int64_t *launches,
             if (attempt == 0 && c->k_cap < (1 << 29)) c->k_cap *= 2;  // a clean segment relaxes the cap
             c->n_steps += m;
             if (c->opt.contact)  // each chunk rebuilds at its steps 0, k, 2k, ...
-                for (int64_t left = m; left > 0; left -= c->opt.graph_chunk) {
-                    const int64_t len = std::min<int64_t>(left, c->opt.graph_chunk), kk = std::min<int64_t>(k, len);
+                for (int64_t rest = m; rest > 0; rest -= chunk_for(c, k)) {
+                    const int64_t len = std::min<int64_t>(rest, chunk_for(c, k)), kk = std::min<int64_t>(k, len);
                     c->n_rebuilds += (len + kk - 1) / kk;
                 }
             c->t += dt * (double)m;
@@ -1037,16 +1049,13 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
     if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return fail(c, PD_EINVAL, "dt must be > 0 and nsteps >= 0");
     if (nsteps == 0) return PD_OK;
     CK(cudaSetDevice(c->opt.device));
-    // a rollback costs at most one segment of work
-    const int64_t seg = (int64_t)PD_SEGMENT_CHUNKS * c->opt.graph_chunk;
     c->last_ms = 0;
     c->last_force_ms = 0;
     c->last_launches = 0;
     for (int64_t done = 0; done < nsteps;) {
-        const int64_t m = std::min(seg, nsteps - done);
-        int64_t launches = 0;
+        int64_t m = 0, launches = 0;
         double ms = 0, fm = 0;
-        pd_status s = run_segment(c, dt, m, &launches, &ms, &fm);
+        pd_status s = run_segment(c, dt, nsteps - done, &m, &launches, &ms, &fm);
         if (s) return s;
         c->last_ms += ms;
         c->last_force_ms += fm;
