@@ -166,7 +166,8 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
  * largest multiple of the rebuild period within graph_chunk); a segment
  * whose contact list went stale or overflowed is rolled back to its own start
  * and rerun with a shorter rebuild period or larger lists.  The contact list is
- * rebuilt often enough for the fastest node (or wall) to double its speed.
+ * rebuilt often enough for the fastest node (or wall) to gain 50% in speed
+ * (150% while speeds are growing).
  * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL
  * (dt <= 0, nsteps < 0), PD_ENONFINITE / PD_EWALL (state restored to the start
  * of the segment in which it happened, so t tells how far the call got, and

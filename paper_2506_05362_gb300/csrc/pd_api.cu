@@ -91,6 +91,7 @@ struct pd_ctx {
     double impulse_span = 0;       // time covered by the wall impulses since their reset
     int64_t n_rollbacks = 0, n_rebuilds = 0, n_steps = 0;  // since creation (successful segments' rebuilds)
     int k_cap = 1 << 30;  // rebuild period a stale list forced down; relaxed by 2x per clean segment
+    double last_vm = 0;   // fastest speed at the previous segment's start
     double last_ms = 0, last_force_ms = 0;
     int64_t last_launches = 0;
     bool profiling = false;
@@ -923,9 +924,11 @@ static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
     for (int l = 0; l < c->walls.nw; ++l)
         vm = std::max(vm, sqrt(c->walls.v[l][0] * c->walls.v[l][0] + c->walls.v[l][1] * c->walls.v[l][1] +
                                c->walls.v[l][2] * c->walls.v[l][2]));
-    // a node struck by a moving wall can leave at twice the wall speed: allow the
-    // fastest speed now to double before the list must be rebuilt
-    double steps = skin_of(c) / (2.0 * 2.0 * dt * std::max(vm, 1e-30));
+    // margin on the fastest speed: 1.5x while it is not growing; 2.5x while it
+    // grows (a node struck by a moving wall can leave at twice the wall speed)
+    const double margin = (c->last_vm > 0 && vm <= 1.05 * c->last_vm) ? 1.5 : 2.5;
+    c->last_vm = vm;
+    double steps = skin_of(c) / (2.0 * margin * dt * std::max(vm, 1e-30));
     *k = (int)std::max(1.0, std::min({steps, (double)c->opt.graph_chunk, (double)c->k_cap}));
     return PD_OK;
 }
