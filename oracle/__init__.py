@@ -71,6 +71,9 @@ def lib():
             L.orc_stable_dt.argtypes = [P]
             L.orc_stable_dt.restype = f64
             L.orc_damage.argtypes = [i64, P, P, P]
+            L.orc_fragments.argtypes = [i64, P, P, P, P]
+            L.orc_fragments.restype = i64
+            L.orc_fragment_stats.argtypes = [i64, P, P, P, P, i64, P, P, P]
             L.orc_energy.argtypes = [P, P, P, P]
             L.orc_energy.restype = f64
             _lib = L
@@ -92,6 +95,30 @@ def _filters(kinds, params):
     kinds = np.ascontiguousarray(kinds, np.int32)
     params = np.ascontiguousarray(params, np.float64).reshape(-1, 12)
     return len(kinds), kinds, params
+
+
+def fragments(rowptr, col, broken):
+    """Connected components over intact bonds (caller order CSR, broken per slot)."""
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    broken = np.ascontiguousarray(broken, np.uint8)
+    n = len(rowptr) - 1
+    label = np.zeros(max(n, 1), np.int32)
+    nf = lib().orc_fragments(n, _p(rowptr), _p(col), _p(broken), _p(label))
+    return label[:n], int(nf)
+
+
+def fragment_stats(rowptr, broken, vol, label, nfrag):
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    broken = np.ascontiguousarray(broken, np.uint8)
+    vol = np.ascontiguousarray(vol, np.float64)
+    label = np.ascontiguousarray(label, np.int32)
+    n = len(rowptr) - 1
+    size = np.zeros(max(nfrag, 1), np.int64)
+    volume = np.zeros(max(nfrag, 1))
+    damage = np.zeros(max(nfrag, 1))
+    lib().orc_fragment_stats(n, _p(rowptr), _p(broken), _p(vol), _p(label), nfrag, _p(size), _p(volume), _p(damage))
+    return size[:nfrag], volume[:nfrag], damage[:nfrag]
 
 
 def bond_row(x, grain, delta, i, kinds=(), params=()):
@@ -206,6 +233,15 @@ class Model:
         phi = np.zeros(self.n)
         lib().orc_damage(self.n, _p(self.rowptr), _p(self.broken), _p(phi))
         return phi
+
+    def fragments(self):
+        """(label (n,) int32: smallest node index of the node's fragment, count)."""
+        return fragments(self.rowptr, self.col, self.broken)
+
+    def fragment_stats(self):
+        """(size, volume, damage) per fragment in increasing label order."""
+        label, nf = self.fragments()
+        return fragment_stats(self.rowptr, self.broken, self.vol, label, nf)
 
     def energy(self):
         return float(lib().orc_energy(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.broken)))

@@ -20,6 +20,7 @@
  *   Sec. 4.1 "Contact between peridynamic body and wall"    -> wall force
  *   Sec. 3.5 Eq. (motion), Sec. 5.2 velocity-Verlet        -> time integration
  *   Sec. 5.3.1 / 5.3.2                                     -> bond removal filters
+ *   Sec. 1 (split-off particles), no algorithm given        -> fragments
  * Readings of gaps and errata are stated at each function.
  *
  * Parity status: every function below is pinned by tests under tests/
@@ -612,6 +613,67 @@ void orc_damage(int64_t n, const int64_t *rowptr, const uint8_t *broken, double 
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) intact += broken[k] ? 0 : 1;
         phi[i] = nb0 ? 1.0 - (double)intact / (double)nb0 : 0.0;
     }
+}
+
+/*
+ * Fragments (split-off pieces; the paper identifies them but gives no
+ * algorithm).  Reading: the connected components of the graph whose vertices
+ * are the nodes and whose edges are the intact bonds; a fragment is labelled by
+ * the smallest node index it contains.  Plain union-find: every intact slot
+ * (i, j) joins the sets of i and j (the set's representative is always its
+ * smallest member).  label (n) receives each node's fragment label; returns the
+ * number of fragments.
+ */
+static int64_t orc_find(int64_t *parent, int64_t x)
+{
+    while (parent[x] != x) x = parent[x];
+    return x;
+}
+
+int64_t orc_fragments(int64_t n, const int64_t *rowptr, const int32_t *col, const uint8_t *broken, int32_t *label)
+{
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) parent[i] = i;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (broken[k]) continue;
+            int64_t a = orc_find(parent, i), b = orc_find(parent, col[k]);
+            if (a == b) continue;
+            if (a < b) parent[b] = a; else parent[a] = b;
+        }
+    int64_t count = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t r = orc_find(parent, i);
+        label[i] = (int32_t)r;
+        if (r == i) ++count;
+    }
+    free(parent);
+    return count;
+}
+
+/*
+ * Per-fragment statistics, fragments in increasing label order: node count,
+ * volume, and damage read as the broken fraction of the fragment's initial bond
+ * slots, 1 - sum intact / sum initial (0 for a fragment without bonds).
+ */
+void orc_fragment_stats(int64_t n, const int64_t *rowptr, const uint8_t *broken, const double *vol,
+                        const int32_t *label, int64_t nfrag, int64_t *size, double *volume, double *damage)
+{
+    int64_t *index = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *intact = (int64_t *)calloc((size_t)(nfrag > 0 ? nfrag : 1), sizeof(int64_t));
+    int64_t *slots = (int64_t *)calloc((size_t)(nfrag > 0 ? nfrag : 1), sizeof(int64_t));
+    int64_t f = 0;
+    for (int64_t i = 0; i < n; ++i) index[i] = (label[i] == i) ? f++ : -1;
+    for (int64_t q = 0; q < nfrag; ++q) { size[q] = 0; volume[q] = 0.0; }
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t q = index[label[i]];
+        size[q] += 1;
+        volume[q] += vol[i];
+        slots[q] += rowptr[i + 1] - rowptr[i];
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) intact[q] += broken[k] ? 0 : 1;
+    }
+    for (int64_t q = 0; q < nfrag; ++q) damage[q] = slots[q] ? 1.0 - (double)intact[q] / (double)slots[q] : 0.0;
+    free(index); free(intact); free(slots);
 }
 
 /*

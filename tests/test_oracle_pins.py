@@ -496,3 +496,70 @@ def test_wall_damping_closed_form():
     assert expect > 0   # the wall pushes a node that approaches it
     assert F1[0] - F0[0] == pytest.approx([0, 0, expect], rel=1e-12, abs=1e-12 * abs(expect))
     assert R1[0] == pytest.approx(-F1[0] * 1e-12, rel=1e-12)
+
+
+# --------------------------------------------------------------------------- fragments
+def random_bond_graph(n, deg, frac_broken, seed):
+    """Symmetric random graph as a caller-order CSR with ascending rows and a
+    symmetric broken pattern."""
+    rng = np.random.default_rng(seed)
+    pairs = set()
+    for i in range(n):
+        for j in rng.choice(n, deg, replace=False):
+            if j != i:
+                pairs.add((min(i, j), max(i, j)))
+    pairs = sorted(pairs)
+    brk_pair = {p: rng.random() < frac_broken for p in pairs}
+    rows = [[] for _ in range(n)]
+    for (a, b) in pairs:
+        rows[a].append(b)
+        rows[b].append(a)
+    rowptr = np.zeros(n + 1, np.int64)
+    col, broken = [], []
+    for i in range(n):
+        r = sorted(rows[i])
+        rowptr[i + 1] = rowptr[i] + len(r)
+        col += r
+        broken += [brk_pair[(min(i, j), max(i, j))] for j in r]
+    return rowptr, np.array(col, np.int32), np.array(broken, np.uint8)
+
+
+@pytest.mark.parametrize("n,deg,frac,seed", [(1, 0, 0.0, 0), (60, 2, 0.5, 1), (500, 3, 0.6, 2), (2000, 4, 0.45, 3)])
+def test_fragments_match_connected_components(n, deg, frac, seed):
+    """Fragments are the connected components of the intact-bond graph: the same
+    partition as scipy's connected_components, labelled by the smallest member."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import connected_components
+    rowptr, col, broken = random_bond_graph(n, deg, frac, seed)
+    label, nf = oracle.fragments(rowptr, col, broken)
+    data = (broken == 0).astype(np.int8)
+    G = csr_matrix((data, col.copy(), rowptr.copy()), shape=(n, n))  # eliminate_zeros works in place
+    G.eliminate_zeros()
+    ncc, cc = connected_components(G, directed=False)
+    assert nf == ncc
+    # same partition: the map component -> label is one-to-one
+    assert len(set(zip(cc.tolist(), label.tolist()))) == ncc
+    # labels are the smallest member of each component
+    for c in range(ncc):
+        members = np.flatnonzero(cc == c)
+        assert np.all(label[members] == members.min())
+    # no intact bond crosses two fragments
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    intact = broken == 0
+    assert np.all(label[rows[intact]] == label[col[intact]])
+
+
+def test_fragment_stats_by_hand():
+    """Two blocks bonded inside, one bond between them broken: two fragments with
+    the right sizes, volumes and broken fractions (counted by hand)."""
+    # path 0-1-2 | 3-4 ; bonds (0,1),(1,2),(2,3) broken,(3,4) broken
+    rowptr = np.array([0, 1, 3, 5, 7, 8], np.int64)
+    col = np.array([1, 0, 2, 1, 3, 2, 4, 3], np.int32)
+    broken = np.array([0, 0, 0, 0, 1, 1, 1, 1], np.uint8)
+    label, nf = oracle.fragments(rowptr, col, broken)
+    assert nf == 3 and label.tolist() == [0, 0, 0, 3, 4]
+    size, vol, dmg = oracle.fragment_stats(rowptr, broken, np.array([1.0, 2, 3, 4, 5]), label, nf)
+    assert size.tolist() == [3, 1, 1]
+    assert vol.tolist() == [6.0, 4.0, 5.0]
+    # fragment {0,1,2}: slots 1+2+2 = 5, intact 4 -> 1/5 broken; {3}: 2 slots, none intact; {4}: 1 slot
+    assert dmg == pytest.approx([0.2, 1.0, 1.0])
