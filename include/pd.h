@@ -198,6 +198,21 @@ pd_status pd_bulk_stress(pd_ctx *ctx, const double *area, double sigma[6], doubl
 pd_status pd_bulk_stress_mean(pd_ctx *ctx, const double *area, double sigma[6], double *wall_force,
                               double *span);
 
+/* Fragments (particles that split off; the paper identifies them, Sec. 1, but
+ * gives no algorithm): the connected components of the graph of nodes and
+ * intact bonds at the current state.  label (n, nullable, caller order): the
+ * smallest caller index in the node's fragment; *nfrag: number of fragments.
+ * Errors: PD_ESTATE before pd_build_bonds, PD_ENOMEM, PD_ECUDA. */
+pd_status pd_fragments(pd_ctx *ctx, int32_t *label, int64_t *nfrag);
+
+/* Per-fragment statistics at the current state, fragments in increasing label
+ * order: node count (size), summed nodal volume, and damage read as the broken
+ * fraction of the fragment's initial bond slots (1 - intact / initial, 0 without
+ * bonds).  nfrag must equal pd_fragments' count for this state (PD_EINVAL
+ * otherwise); each output (nfrag entries) is nullable.  Volumes are summed with
+ * atomics, so their last bits may vary between calls. */
+pd_status pd_fragment_stats(pd_ctx *ctx, int64_t nfrag, int64_t *size, double *volume, double *damage);
+
 /* Number of directed bonds B (each undirected bond counted twice). */
 pd_status pd_num_bonds(pd_ctx *ctx, int64_t *B);
 

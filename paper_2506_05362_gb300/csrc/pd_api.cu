@@ -1152,6 +1152,85 @@ pd_status pd_bulk_stress_mean(pd_ctx *c, const double *area, double sigma[6], do
     return PD_OK;
 }
 
+// ---- fragments ------------------------------------------------------------------
+// Components of the current state into device scratch (freed by the caller):
+// caller-order labels and the fragment index of every label (exclusive scan).
+struct FragScratch {
+    int32_t *parent = nullptr, *minc = nullptr, *label = nullptr;
+    int64_t *is_label = nullptr, *fidx = nullptr;
+};
+
+static void frag_release(pd_ctx *c, FragScratch &f)
+{
+    release(c, f.parent); release(c, f.minc); release(c, f.label); release(c, f.is_label); release(c, f.fidx);
+}
+
+static pd_status frag_run(pd_ctx *c, FragScratch &f, int64_t *nfrag)
+{
+    const int64_t n = c->n;
+    ALLOC(f.parent, int32_t, n);
+    ALLOC(f.minc, int32_t, n);
+    ALLOC(f.label, int32_t, n);
+    ALLOC(f.is_label, int64_t, n + 1);
+    ALLOC(f.fidx, int64_t, n + 1);
+    fragments_device(c->rowptr, c->col, c->brk, c->perm, n, f.parent, f.minc, f.label, f.is_label, c->st);
+    scan_exclusive_i64(f.is_label, f.fidx, n, c->tmp, c->st);
+    CK(cudaMemcpyAsync(nfrag, f.fidx + n, sizeof(int64_t), cudaMemcpyDeviceToHost, c->st));
+    return sync(c);
+}
+
+pd_status pd_fragments(pd_ctx *c, int32_t *label, int64_t *nfrag)
+{
+    if (!c || !nfrag) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_fragments before pd_build_bonds");
+    CK(cudaSetDevice(c->opt.device));
+    FragScratch f;
+    pd_status s = frag_run(c, f, nfrag);
+    if (!s && label) {
+        if (cudaMemcpyAsync(label, f.label, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost, c->st) != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(c, PD_ECUDA, "fragment label copy failed");
+        }
+        if (!s) s = sync(c);
+    }
+    frag_release(c, f);
+    return s;
+}
+
+pd_status pd_fragment_stats(pd_ctx *c, int64_t nfrag, int64_t *size, double *volume, double *damage)
+{
+    if (!c || nfrag < 0) return PD_EINVAL;
+    if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_fragment_stats before pd_build_bonds");
+    CK(cudaSetDevice(c->opt.device));
+    FragScratch f;
+    int64_t have = 0;
+    pd_status s = frag_run(c, f, &have);
+    if (!s && have != nfrag) s = fail(c, PD_EINVAL, "nfrag does not match the current number of fragments");
+    unsigned long long *dsize = nullptr, *dslots = nullptr, *dintact = nullptr;
+    double *dvol = nullptr, *ddmg = nullptr;
+    if (!s && nfrag > 0) {
+        const int64_t m = nfrag;
+        if (!(dsize = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
+            !(dslots = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
+            !(dintact = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
+            !(dvol = (double *)pd_dev_alloc(c, sizeof(double) * m)) || !(ddmg = (double *)pd_dev_alloc(c, sizeof(double) * m))) {
+            s = fail(c, PD_ENOMEM, "device allocation failed: fragment statistics");
+        } else {
+            fragment_stats_device(c->rowptr, c->brk, c->perm, c->x4, f.label, f.fidx, c->n, m, dsize, dvol, dslots,
+                                  dintact, ddmg, c->st);
+            bool ok = true;
+            if (size) ok &= cudaMemcpyAsync(size, dsize, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
+            if (volume) ok &= cudaMemcpyAsync(volume, dvol, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
+            if (damage) ok &= cudaMemcpyAsync(damage, ddmg, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
+            if (!ok) { cudaGetLastError(); s = fail(c, PD_ECUDA, "fragment statistics copy failed"); }
+            if (!s) s = sync(c);
+        }
+    }
+    release(c, dsize); release(c, dslots); release(c, dintact); release(c, dvol); release(c, ddmg);
+    frag_release(c, f);
+    return s;
+}
+
 pd_status pd_num_bonds(pd_ctx *c, int64_t *B)
 {
     if (!c || !B) return PD_EINVAL;

@@ -86,6 +86,8 @@ def lib():
                 "pd_damage": (i32, [P, P]),
                 "pd_bulk_stress": (i32, [P, P, P, P]),
                 "pd_bulk_stress_mean": (i32, [P, P, P, P, P]),
+                "pd_fragments": (i32, [P, P, P]),
+                "pd_fragment_stats": (i32, [P, i64, P, P, P]),
                 "pd_num_bonds": (i32, [P, P]),
                 "pd_bonds": (i32, [P, P, P]),
                 "pd_contacts": (i32, [P, P, P]),
@@ -241,6 +243,21 @@ def pd_bulk_stress_mean(h, areas, nw):
     ar = None if areas is None else _f64(areas)
     _check(lib().pd_bulk_stress_mean(h, _ptr(ar), _ptr(s), _ptr(wf), ctypes.byref(span)), h)
     return s, wf[:nw], span.value
+
+
+def pd_fragments(h, n):
+    label = np.zeros(n, np.int32)
+    nf = ctypes.c_int64()
+    _check(lib().pd_fragments(h, _ptr(label), ctypes.byref(nf)), h)
+    return label, nf.value
+
+
+def pd_fragment_stats(h, nfrag):
+    size = np.zeros(max(nfrag, 1), np.int64)
+    vol = np.zeros(max(nfrag, 1))
+    dmg = np.zeros(max(nfrag, 1))
+    _check(lib().pd_fragment_stats(h, nfrag, _ptr(size), _ptr(vol), _ptr(dmg)), h)
+    return size[:nfrag], vol[:nfrag], dmg[:nfrag]
 
 
 def pd_num_bonds(h):
@@ -402,6 +419,15 @@ class Context:
 
     def bonds(self):
         return pd_bonds(self.h, self.n)
+
+    def fragments(self):
+        """(label (n,) int32, caller order: smallest caller index of the node's fragment, count)."""
+        return pd_fragments(self.h, self.n)
+
+    def fragment_stats(self):
+        """(size, volume, damage) per fragment in increasing label order."""
+        _, nf = pd_fragments(self.h, self.n)
+        return pd_fragment_stats(self.h, nf)
 
     def contacts(self):
         return pd_contacts(self.h)

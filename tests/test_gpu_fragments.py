@@ -1,0 +1,80 @@
+"""Fragments on the GPU (connected components over intact bonds, lock-free
+union-find) against the oracle's union-find, on broken patterns the test
+prescribes (the same input to both sides)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_05362_gb300 import scenarios as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pd():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2506_05362_gb300 import pd as _pd
+    return _pd
+
+
+def pattern(x, rp, col, frac, seed, cut_axis=None):
+    """Symmetric broken flags in canonical slot order: a random fraction of the
+    undirected bonds, plus (optionally) every bond crossing the mid-plane of an
+    axis, which splits the body in two."""
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    lo, hi = np.minimum(rows, col), np.maximum(rows, col)
+    key = lo.astype(np.int64) * (len(rp) + 1) + hi
+    rng = np.random.default_rng(seed)
+    uniq, inv = np.unique(key, return_inverse=True)
+    brk = (rng.random(len(uniq)) < frac)[inv]
+    if cut_axis is not None:
+        mid = x[:, cut_axis].mean()
+        brk |= (x[rows, cut_axis] < mid) != (x[col, cut_axis] < mid)
+    return brk.astype(np.uint8)
+
+
+@pytest.mark.parametrize("name,frac,cut", [("block", 0.0, 0), ("block", 0.6, None), ("sphere", 0.5, 2),
+                                           ("aggregate", 0.0, None), ("kalthoff", 0.75, 1)])
+def test_fragments_match_oracle(pd, name, frac, cut):
+    sc = {"block": lambda: S.small_block(nx=12, ny=7, nz=5, jitter=0.1), "sphere": S.sphere,
+          "aggregate": lambda: S.aggregate(n_grains=6, h=0.5e-3 / 5, gap_cells=0.5, seed=3),
+          "kalthoff": S.kalthoff}[name]()
+    ctx = pd.Context.from_scenario(sc, lanes=8, contact=False)
+    rp, col = ctx.bonds()
+    orp, ocol = oracle.bonds(sc.x, sc.grain, sc.horizon, *S.filters_array(sc.filters))
+    assert np.array_equal(rp, orp) and np.array_equal(col, ocol)
+    brk = pattern(sc.x, orp, ocol, frac, seed=7, cut_axis=cut)
+    ctx.set_state(broken=brk)
+    label, nf = ctx.fragments()
+    olabel, onf = oracle.fragments(orp, ocol, brk)
+    assert nf == onf
+    assert np.array_equal(label, olabel)
+    if name == "aggregate":
+        assert nf >= 6  # no bond crosses grains
+    if cut is not None and frac == 0.0:
+        assert nf == 2
+    size, vol, dmg = ctx.fragment_stats()
+    osize, ovol, odmg = oracle.fragment_stats(orp, brk, sc.vol, olabel, onf)
+    assert np.array_equal(size, osize)
+    assert np.array_equal(dmg, odmg)
+    assert np.allclose(vol, ovol, rtol=1e-12, atol=0)
+    ctx.close()
+
+
+def test_fragments_after_tearing(pd):
+    """A block torn apart by opposing velocities: the GPU's fragments of its own
+    state equal the components of its own broken set (a consistency check), and
+    the tear made at least two pieces."""
+    sc = S.small_block(nx=14, ny=6, nz=5, jitter=0.05)
+    sc.v0 = np.zeros_like(sc.x)
+    sc.v0[:, 0] = np.where(sc.x[:, 0] > sc.x[:, 0].mean(), 60.0, -60.0)
+    ctx = pd.Context.from_scenario(sc, lanes=8)
+    dt = 0.5 * ctx.stable_dt()
+    ctx.step(dt, 150)
+    rp, col = ctx.bonds()
+    _, _, broken, _ = ctx.get_state()
+    label, nf = ctx.fragments()
+    olabel, onf = oracle.fragments(rp, col, broken)
+    assert nf >= 2 and nf == onf and np.array_equal(label, olabel)
+    ctx.close()
