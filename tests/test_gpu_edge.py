@@ -38,8 +38,10 @@ def test_single_node_free_fall(pd, precision):
     ctx.step(dt, 100)
     u, v, broken, t = ctx.get_state()
     T = 100 * dt
-    # the mixed path carries u, v as double-float pairs: ~48 bits
-    rel = 1e-12 if precision == "fp64" else 1e-11
+    # the mixed path holds u, v in double-float pairs but forms the acceleration
+    # (F + b) / rho in FP32 (force arithmetic in FP32): 2^-24 relative per step,
+    # the same sign every step here
+    rel = 1e-12 if precision == "fp64" else 1e-6
     assert u[0, 2] == pytest.approx(0.5 * g * T * T, rel=rel)
     assert v[0, 2] == pytest.approx(g * T, rel=rel)
     assert np.all(u[0, :2] == 0) and np.all(v[0, :2] == 0)
