@@ -45,7 +45,7 @@ class Problem(ctypes.Structure):
                 ("Rc", ctypes.c_double), ("rho", ctypes.c_double),
                 ("break_mode", ctypes.c_int), ("contact", ctypes.c_int), ("nw", ctypes.c_int),
                 ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3), ("frozen", ctypes.c_int),
-                ("beta_d", ctypes.c_double)]
+                ("beta_d", ctypes.c_double), ("conic", ctypes.c_int), ("delta", ctypes.c_double)]
 
 
 def lib():
@@ -55,7 +55,7 @@ def lib():
             L = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
-            L.orc_constants.argtypes = [f64, f64, f64, f64, i32, P]
+            L.orc_constants.argtypes = [f64, f64, f64, f64, i32, i32, P]
             L.orc_bond_row.argtypes = [i64, P, P, f64, i32, P, P, i64, P]
             L.orc_bond_row.restype = i64
             L.orc_bonds_brute.argtypes = [i64, P, P, f64, i32, P, P, P, P]
@@ -84,10 +84,10 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
 
 
-def constants(E, G0, delta, contact_factor=5.0, mode=0):
+def constants(E, G0, delta, contact_factor=5.0, mode=0, micromodulus=0):
     """(K, c, s0, Kn) of the material (see orc_constants)."""
     out = np.zeros(4)
-    lib().orc_constants(E, G0, delta, contact_factor, mode, _p(out))
+    lib().orc_constants(E, G0, delta, contact_factor, mode, micromodulus, _p(out))
     return tuple(float(v) for v in out)
 
 
@@ -160,7 +160,8 @@ class Model:
         self.col = np.ascontiguousarray(col, np.int32)
         n = self.x.shape[0]
         m = material
-        self.K, self.c, self.s0, self.Kn = constants(m.E, m.G0, horizon, m.contact_factor, m.constants)
+        self.K, self.c, self.s0, self.Kn = constants(m.E, m.G0, horizon, m.contact_factor, m.constants,
+                                                     getattr(m, "micromodulus", 0))
         self.walls = np.ascontiguousarray(walls if walls is not None else np.zeros((0, 9)), np.float64).reshape(-1, 9)
         self.wall_pos = self.walls[:, 3:6].copy()
         self.P = Problem()
@@ -170,6 +171,8 @@ class Model:
         self.P.c, self.P.s0, self.P.Kn, self.P.Rc, self.P.rho = self.c, self.s0, self.Kn, m.contact_radius, m.rho
         self.P.break_mode = m.break_mode
         self.P.beta_d = getattr(m, "beta_d", 0.0)
+        self.P.conic = getattr(m, "micromodulus", 0)
+        self.P.delta = horizon
         self.P.contact = 1 if contact else 0
         self.P.nw = self.walls.shape[0]
         self.P.walls = _p(self.walls)

@@ -59,14 +59,24 @@
  * pair; it is kept only behind the switch.
  * Contact stiffness (Sec. 3.2): K_n = 18 K / (pi delta^5) times a factor f_c,
  * i.e. K_n = f_c c / delta with the default c.
+ * micromodulus == 1: the conic micromodulus of the table, c(|xi|) = c (delta - |xi|);
+ * c is then the coefficient.  Self-consistent values (same two energy matches):
+ *   c  = 90 K / (pi delta^5),  s0 = sqrt(2 G0 / (3 K delta));
+ * printed (constants == 1): c = 60 E / (pi delta^5 (1 - nu)), s0 = sqrt(7 pi G0 / (12 E delta)).
  */
-void orc_constants(double E, double G0, double delta, double contact_factor, int constants,
+void orc_constants(double E, double G0, double delta, double contact_factor, int constants, int micromodulus,
                    double out[4] /* K, c, s0, Kn */)
 {
     const double nu = 0.25;
     double K = E / (3.0 * (1.0 - 2.0 * nu));
     double c, s0;
-    if (constants == 1) {
+    if (micromodulus == 1 && constants == 1) {
+        c = 60.0 * E / (ORC_PI * pow(delta, 5) * (1.0 - nu));
+        s0 = sqrt(7.0 * ORC_PI * G0 / (12.0 * E * delta));
+    } else if (micromodulus == 1) {
+        c = 90.0 * K / (ORC_PI * pow(delta, 5));
+        s0 = sqrt(2.0 * G0 / (3.0 * K * delta));
+    } else if (constants == 1) {
         c = 12.0 * E / (ORC_PI * pow(delta, 4) * (1.0 - nu));
         s0 = sqrt(5.0 * ORC_PI * G0 / (12.0 * E * delta));
     } else {
@@ -316,7 +326,12 @@ typedef struct {
     double b[3];            /* body force density, N/m^3 */
     int frozen;             /* 1: evaluate with the given bond memory, no new breaking */
     double beta_d;          /* normal damping coefficient (Sec. 3.3), N s / m^7; 0 = none */
+    int conic;              /* 1: conic micromodulus c (delta - |xi|) */
+    double delta;           /* horizon (used by the conic micromodulus) */
 } orc_problem;
+
+/* micromodulus of a bond of reference length L: c, or c (delta - L) when conic */
+static double orc_cw(const orc_problem *P, double L) { return P->conic ? P->c * (P->delta - L) : P->c; }
 
 /* slot of j in row i (binary search on the ascending row), or -1 */
 static int64_t orc_slot(const orc_problem *P, int64_t i, int64_t j)
@@ -461,7 +476,7 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
             double s = (l - L) / L;
             int brk = P->break_mode ? (fabs(s) > P->s0) : (s > P->s0);
             if (brk && !P->frozen) { broken[k] = 1; continue; }
-            double g = P->c * s * P->vol[j] / l;
+            double g = orc_cw(P, L) * s * P->vol[j] / l;
             for (int a = 0; a < 3; ++a) f[a] += g * y[a];
         }
         for (int a = 0; a < 3; ++a) F[3 * i + a] = f[a];
@@ -488,7 +503,7 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
                     mag = -P->Kn * (P->Rc - dn);
                 } else {
                     double sr = (dn - L) / L;
-                    mag = P->c * (sr < 0.0 ? sr : 0.0);
+                    mag = orc_cw(P, L) * (sr < 0.0 ? sr : 0.0);
                 }
                 for (int a = 0; a < 3; ++a) F[3 * i + a] += mag * (d[a] / dn) * P->vol[j];
                 if (damp) {
@@ -591,7 +606,7 @@ double orc_stable_dt(const orc_problem *P)
             int64_t j = P->col[k];
             double L = sqrt(sq3(P->x[3 * j] - P->x[3 * i], P->x[3 * j + 1] - P->x[3 * i + 1],
                                 P->x[3 * j + 2] - P->x[3 * i + 2]));
-            sum += P->vol[j] * P->c / L;
+            sum += P->vol[j] * orc_cw(P, L) / L;
         }
         double dt = sqrt(2.0 * P->rho / sum);
         if (dt < best) best = dt;
@@ -700,7 +715,7 @@ double orc_energy(const orc_problem *P, const double *u, const double *v, const 
             }
             double L = sqrt(sq3(xi[0], xi[1], xi[2]));
             double s = (sqrt(sq3(y[0], y[1], y[2])) - L) / L;
-            pe += 0.25 * P->c * s * s * L * P->vol[i] * P->vol[j];
+            pe += 0.25 * orc_cw(P, L) * s * s * L * P->vol[i] * P->vol[j];
         }
     }
     if (P->contact) {

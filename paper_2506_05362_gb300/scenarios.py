@@ -42,6 +42,7 @@ class Material:
     constants: int = 0      # 0 = self-consistent c, s0; 1 = paper's table values
     break_mode: int = 0     # 0 = tension s > s0; 1 = |s| > s0
     beta_d: float = 0.0     # normal contact damping (Sec. 3.3), N s / m^7; 0 = none
+    micromodulus: int = 0   # 0 = constant, 1 = conic c (delta - |xi|) (table of Sec. 3.1.1)
 
 
 @dataclass

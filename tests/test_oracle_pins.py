@@ -563,3 +563,41 @@ def test_fragment_stats_by_hand():
     assert vol.tolist() == [6.0, 4.0, 5.0]
     # fragment {0,1,2}: slots 1+2+2 = 5, intact 4 -> 1/5 broken; {3}: 2 slots, none intact; {4}: 1 slot
     assert dmg == pytest.approx([0.2, 1.0, 1.0])
+
+
+# --------------------------------------------------------------------------- conic micromodulus
+def test_conic_micromodulus_energy_and_fracture():
+    """Conic micromodulus c (delta - |xi|) (table of Sec. 3.1.1): the coefficient
+    matches the bulk strain energy and s0 the crack energy, by the same
+    quadratures as the constant case; the printed row sits behind constants=1."""
+    E, G0, delta = 72e9, 135.0, 3e-4
+    K, c, s0, Kn = oracle.constants(E, G0, delta, micromodulus=1)
+    cw = lambda r: c * (delta - r)
+    s = 1e-3
+    radial, _ = integrate.quad(lambda r: 0.5 * cw(r) * s * s * r * 4 * math.pi * r * r, 0, delta)
+    assert 0.5 * radial == pytest.approx(4.5 * K * s * s, rel=1e-12)
+    w = lambda r: 0.5 * cw(r) * s0 * s0 * r
+
+    def inner(z):
+        return integrate.quad(lambda r: w(r) * 2 * math.pi * r * r * (1 - z / r), z, delta)[0]
+
+    G, _ = integrate.quad(inner, 0, delta)
+    assert G == pytest.approx(G0, rel=1e-10)
+    _, c1, s01, Kn1 = oracle.constants(E, G0, delta, mode=1, micromodulus=1)
+    assert c1 / c == pytest.approx(4.0 / 3.0, rel=1e-14)
+    assert s01 / s0 == pytest.approx(math.sqrt(7 * math.pi / 12), rel=1e-14)
+    assert Kn1 == Kn  # contact stiffness is defined from K, not from c
+
+
+def test_conic_bond_force_by_hand():
+    """Two nodes, one bond of length L stretched by s: the force density on node
+    0 is c (delta - L) s V_1 along the bond."""
+    mat = S.Material(E=72e9, rho=2440, G0=1e12, contact_radius=1e-5, micromodulus=1)
+    L, delta, V = 1e-4, 3e-4, 1e-12
+    m = model_for(np.array([[0.0, 0, 0], [L, 0, 0]]), mat, delta, vol=np.full(2, V), contact=False)
+    s = 2e-4
+    m.u = np.array([[0.0, 0, 0], [s * L, 0, 0]])
+    F = m.forces()
+    K, c, s0, _ = oracle.constants(mat.E, mat.G0, delta, micromodulus=1)
+    assert F[0, 0] == pytest.approx(c * (delta - L) * s * V, rel=1e-12)
+    assert F[1, 0] == pytest.approx(-F[0, 0], rel=1e-15)
