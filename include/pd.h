@@ -79,6 +79,12 @@ typedef struct {
     int constants;          /* 0 or 1, see above */
     int break_mode;         /* 0 or 1, see above */
     double beta_d;          /* normal contact damping coefficient (>= 0), see above */
+    int micromodulus;       /* 0 = constant (default); 1 = conic c (delta - |xi|) (table of
+                               Sec. 3.1.1): c = 90 K / (pi delta^5), s0 = sqrt(2 G0 / (3 K delta));
+                               with constants = 1 the printed row, c = 60 E / (pi delta^5 (1 - nu)),
+                               s0 = sqrt(7 pi G0 / (12 E delta)).  The bond force, the self-contact
+                               law and pd_stable_dt use c(|xi|); pd_stable_dt_noalloc takes a
+                               constant micromodulus only. */
 } pd_material;
 
 typedef struct {

@@ -177,7 +177,13 @@ void constants(pd_ctx *c)
 {
     const double nu = 0.25, E = c->mat.E, G0 = c->mat.G0, d = c->delta;
     c->K = E / (3.0 * (1.0 - 2.0 * nu));
-    if (c->mat.constants == 1) {
+    if (c->mat.micromodulus == 1 && c->mat.constants == 1) {  // conic, printed row
+        c->c = 60.0 * E / (M_PI * pow(d, 5) * (1.0 - nu));
+        c->s0 = sqrt(7.0 * M_PI * G0 / (12.0 * E * d));
+    } else if (c->mat.micromodulus == 1) {  // conic: bulk and crack energies matched
+        c->c = 90.0 * c->K / (M_PI * pow(d, 5));
+        c->s0 = sqrt(2.0 * G0 / (3.0 * c->K * d));
+    } else if (c->mat.constants == 1) {
         c->c = 12.0 * E / (M_PI * pow(d, 4) * (1.0 - nu));
         c->s0 = sqrt(5.0 * M_PI * G0 / (12.0 * E * d));
     } else {
@@ -238,6 +244,9 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.s0f = (float)c->s0;
     p.break_mode = c->mat.break_mode;
     p.beta_d = c->mat.beta_d;
+    p.conic = c->mat.micromodulus == 1;
+    p.delta = c->delta;
+    p.delta_f = (float)c->delta;
     p.cand_fd = c->cand_fd;
     p.mode = mode;
     p.walls = c->walls;
@@ -543,7 +552,8 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (n < 1 || n > 0x7fffffffLL || !x || !vol || !grain || !mat) return PD_EINVAL;
     if (!(mat->E > 0) || !(mat->rho > 0) || !(mat->G0 > 0) || !(mat->contact_radius > 0) ||
         !(mat->contact_factor >= 0) || (mat->constants != 0 && mat->constants != 1) ||
-        (mat->break_mode != 0 && mat->break_mode != 1) || !(mat->beta_d >= 0) || !isfinite(mat->beta_d))
+        (mat->break_mode != 0 && mat->break_mode != 1) || !(mat->beta_d >= 0) || !isfinite(mat->beta_d) ||
+        (mat->micromodulus != 0 && mat->micromodulus != 1))
         return PD_EINVAL;
     pd_ctx *c = new pd_ctx();
     if (opt) c->opt = *opt; else pd_default_options(&c->opt);
@@ -818,7 +828,8 @@ pd_status pd_stable_dt(pd_ctx *c, double *dt)
     if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_stable_dt before pd_build_bonds");
     CK(cudaSetDevice(c->opt.device));
     int nb = stable_dt_blocks(c->n);
-    stable_dt(c->x4, c->rowptr, c->col, c->n, c->c, c->mat.rho, c->dscratch, c->st);
+    stable_dt(c->x4, c->rowptr, c->col, c->n, c->c, c->mat.rho, c->delta, c->mat.micromodulus == 1, c->dscratch,
+              c->st);
     std::vector<double> h(nb);
     CK(cudaMemcpyAsync(h.data(), c->dscratch, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
     pd_status s = sync(c);

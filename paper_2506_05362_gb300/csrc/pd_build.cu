@@ -294,7 +294,8 @@ __global__ void k_damage(const int64_t *__restrict__ rowptr, const uint32_t *__r
 }
 
 __global__ void k_stable_dt(const dbl4 *__restrict__ x4, const int64_t *__restrict__ rowptr,
-                            const int32_t *__restrict__ col, int64_t n, double c, double rho, double *dt_out)
+                            const int32_t *__restrict__ col, int64_t n, double c, double rho, double delta,
+                            int conic, double *dt_out)
 {
     __shared__ double s_min[256];
     double best = INFINITY;
@@ -306,7 +307,7 @@ __global__ void k_stable_dt(const dbl4 *__restrict__ x4, const int64_t *__restri
         for (int64_t k = k0; k < k1; ++k) {
             const dbl4 b = x4[col[k]];
             const double L = sqrt(sq3(b.x - a.x, b.y - a.y, b.z - a.z));
-            sum += b.w * c / L;
+            sum += b.w * (conic ? c * (delta - L) : c) / L;
         }
         best = fmin(best, sqrt(2.0 * rho / sum));
     }
@@ -613,9 +614,9 @@ void damage(const int64_t *rowptr, const uint32_t *brk, const int32_t *perm, int
 int stable_dt_blocks(int64_t n) { return grid_of(n); }
 
 void stable_dt(const dbl4 *x4, const int64_t *rowptr, const int32_t *col, int64_t n, double c, double rho,
-               double *partial, cudaStream_t st)
+               double delta, int conic, double *partial, cudaStream_t st)
 {
-    k_stable_dt<<<grid_of(n), 256, 0, st>>>(x4, rowptr, col, n, c, rho, partial);
+    k_stable_dt<<<grid_of(n), 256, 0, st>>>(x4, rowptr, col, n, c, rho, delta, conic, partial);
 }
 
 void canon_keys(const int64_t *rowptr, const int32_t *col, const int32_t *perm, int64_t n, int sh, uint64_t *keys,

@@ -36,7 +36,7 @@ void damage(const int64_t *rowptr, const uint32_t *brk, const int32_t *perm, int
             cudaStream_t st);
 int stable_dt_blocks(int64_t n);
 void stable_dt(const dbl4 *x4, const int64_t *rowptr, const int32_t *col, int64_t n, double c, double rho,
-               double *partial, cudaStream_t st);
+               double delta, int conic, double *partial, cudaStream_t st);
 void canon_keys(const int64_t *rowptr, const int32_t *col, const int32_t *perm, int64_t n, int sh, uint64_t *keys,
                 uint32_t *vals, cudaStream_t st);
 void canon_invert(const uint32_t *vals, int64_t B, int32_t *kc_of, cudaStream_t st);

@@ -85,6 +85,9 @@ struct StepParams {
     double *react;                 // nw*3 final wall reactions
     double *impulse;               // nw*3 sum over steps of dt * react (not in MODE_FORCES)
     double beta_d;                 // normal contact damping (0 = none)
+    int conic;                     // conic micromodulus c (delta - |xi|)
+    double delta;                  // horizon
+    float delta_f;
     void *cand_fd;                 // damping force per candidate: float4 (mixed) / dbl4 (FP64)
     double *disp;                  // accumulated displacement bound since last rebuild
     double skin;

@@ -129,7 +129,8 @@ __device__ __forceinline__ void bond_mixed(const StepParams &p, int64_t k, const
         if (FLAG) atomicOr((unsigned int *)(p.lcol) + (k >> 1), 0x8000u << (16 * (int)(k & 1)));
         if (p.colf) atomicOr((unsigned int *)p.colf + k, 0x80000000u);
     } else {
-        const float g = a0.w * s * ry;  // a0.w holds c V_j
+        float g = a0.w * s * ry;  // a0.w holds c V_j
+        if (p.conic) g *= p.delta_f - L2 * rL;
         fbx = fmaf(g, yx, fbx);
         fby = fmaf(g, yy, fby);
         fbz = fmaf(g, yz, fbz);
@@ -171,8 +172,10 @@ __device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, i
         p.colf[k] = (int32_t)((uint32_t)raw | 0x80000000u);
         atomicOr(p.brk + (k >> 5), 1u << (k & 31));
     }
-    // a0.w holds c V_j (the record's volume slot is scaled at bond build)
-    const float g = (intact && !brk) ? a0.w * s * ry : 0.f;
+    // a0.w holds c V_j (the record's volume slot is scaled at bond build); the
+    // conic micromodulus multiplies by delta - |xi| (uniform branch)
+    float g = (intact && !brk) ? a0.w * s * ry : 0.f;
+    if (p.conic) g *= p.delta_f - L2 * rL;
     const float2 f = __ffma2_rn(make_float2(g, g), yxy, make_float2(fbx, fby));
     fbx = f.x;
     fby = f.y;
@@ -315,7 +318,7 @@ __device__ __forceinline__ bool contact_term(const StepParams &p, int64_t q, con
         mag = -p.Kn * (p.Rc - dn);
     } else {
         const double sr = (dn - L) / L;
-        mag = p.c * (sr < 0.0 ? sr : 0.0);
+        mag = (p.conic ? p.c * (p.delta - L) : p.c) * (sr < 0.0 ? sr : 0.0);
     }
     const double gm = mag * xj.w / dn;
     gx = gm * dx; gy = gm * dy; gz = gm * dz;
@@ -448,7 +451,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
                 if (brk) {
                     atomicOr(p.brk + (k >> 5), 1u << (k & 31));
                 } else {
-                    const double g = p.c * s * a.w / l;
+                    const double g = (p.conic ? p.c * (p.delta - L) : p.c) * s * a.w / l;
                     fdx += g * yx; fdy += g * yy; fdz += g * yz;
                 }
             }

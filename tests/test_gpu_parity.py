@@ -470,3 +470,30 @@ def test_damped_collision_trajectory(pd, precision, tol):
     assert rel_l2(v, ref.v) < 10 * tol
     ke1 = 0.5 * sc.material.rho * (sc.vol[:, None] * ref.v ** 2).sum()
     assert ke1 < ke0
+
+
+# --------------------------------------------------------------------------- conic micromodulus
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_FORCE_TOL), ("fp64", FP64_FORCE_TOL)])
+@pytest.mark.parametrize("name", ["sphere", "kalthoff_small", "aggregate_small"])
+def test_conic_micromodulus_forces_and_dt(pd, name, precision, tol):
+    """Conic micromodulus c (delta - |xi|): forces at a perturbed state (with
+    breaking) and the critical step against the oracle."""
+    sc = SCENARIOS[name]()
+    sc.material.micromodulus = 1
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=8)
+    ref = oracle.Model.from_scenario(sc)
+    assert ctx.stable_dt() == pytest.approx(ref.stable_dt(), rel=1e-12)
+    u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=4)
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    _, _, broken, _ = ctx.get_state()
+    ref.u = u.copy()
+    ref.forces()
+    s = stretches(sc.x, u, ref.rowptr, ref.col)
+    diff = broken.astype(bool) != ref.broken.astype(bool)
+    assert ref.broken.sum() > 0
+    assert np.all(np.abs(s[diff] - s0) < BAND * s0)
+    ref.broken[:] = broken
+    Fo = ref.forces(frozen=True).copy()
+    assert rel_l2(F, Fo) <= tol
+    ctx.close()
