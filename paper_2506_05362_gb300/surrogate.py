@@ -272,10 +272,11 @@ def baseline_error(train_runs, run: Run):
 
 
 def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate: float = 2.0e3,
-          records: int = 64, seed: int = 0, device: int = 0, log=print):
+          records: int = 64, seed: int = 0, device: int = 0, zeta: float = 0.0, log=print):
     """Generates runs_per_path runs per loading path (grain counts cycling through
-    grain_counts, seeds distinct), holds out the last run of every path, trains on
-    the rest and judges the held-out runs against their PD results."""
+    grain_counts, seeds distinct, contact damping ratio zeta), holds out the last
+    run of every path, trains on the rest and judges the held-out runs against
+    their PD results."""
     # the network runs on torch's current stream (its tensors are made there);
     # every PD context makes its own capturable stream and synchronises on return
     stream = None
@@ -285,7 +286,7 @@ def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate:
         for r in range(runs_per_path):
             ng = grain_counts[r % len(grain_counts)]
             runs.append(rve_run(path, n_grains=ng, seed=seed + 1000 * pi + r, rate=rate, records=records,
-                                device=device, stream=stream))
+                                device=device, stream=stream, zeta=zeta))
     t_data = time.perf_counter() - t0
     held = [runs[(pi + 1) * runs_per_path - 1] for pi in range(len(LOADING_PATHS))]
     train_runs = [r for r in runs if r not in held]
@@ -298,9 +299,12 @@ def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate:
         rows.append({"path": r.path, "grains": r.n_grains, "nodes": r.nodes, "steps": r.steps,
                      "err": err, "err_mean_history": baseline_error(train_runs, r),
                      "pd_seconds": r.pd_seconds, "net_seconds": t_net, "speedup": r.pd_seconds / max(t_net, 1e-9)})
-    net.close()
     errs = np.array([q["err"] for q in rows])
+    train_err = [judge(net, xs, ys, r, device=device)[0] for r in train_runs[:16]]
+    net.close()
     return {"runs": len(runs), "train_runs": len(train_runs), "held_out": len(held),
+            "train_err_median": float(np.median(train_err)),
+            "err_mean_history_median": float(np.median([q["err_mean_history"] for q in rows])),
             "samples": int(sum(windows(r)[0].shape[0] for r in train_runs)),
             "data_seconds": t_data, "train_seconds": t_train, "final_loss": losses[-1],
             "err_median": float(np.median(errs)), "err_max": float(errs.max()),
@@ -316,5 +320,13 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--records", type=int, default=64)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--zeta", type=float, default=0.0, help="contact damping ratio of the RVE runs")
+    ap.add_argument("--grains", type=int, nargs="+", default=[8, 12], help="grain counts, cycled over the runs")
+    ap.add_argument("--out", default=None, help="also write the full report (per held-out run) to this file")
     a = ap.parse_args()
-    print(json.dumps(study(a.runs_per_path, epochs=a.epochs, records=a.records, seed=a.seed)))
+    rep = study(a.runs_per_path, grain_counts=tuple(a.grains), epochs=a.epochs, records=a.records, seed=a.seed,
+                zeta=a.zeta)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(rep, f, indent=1)
+    print(json.dumps({k: v for k, v in rep.items() if k != "held"}))
