@@ -318,7 +318,10 @@ pd_status pd_mlp_forward_device(pd_mlp *m, const float *X, int64_t batch, float 
  * TMEM accumulators, activations kept in shared memory across layers) when
  * every layer is at most 256 wide on an sm_100+ GPU, else mma.sync GEMMs;
  * 1 = mma.sync GEMMs only; 2 = the tcgen05 kernel only (a forward that it
- * cannot run returns PD_EINVAL).  Training always uses the mma.sync kernels.
+ * cannot run returns PD_EINVAL).  The same switch selects the training kernels:
+ * 0 and 2 train on tcgen05 (the fused forward also stores the pre-activations
+ * and the transposed layer inputs; weight and data gradients are TMA-fed
+ * tcgen05 GEMMs, hidden widths multiples of 32), 1 on the mma.sync GEMMs.
  * PD_EINVAL for any other value. */
 pd_status pd_mlp_set_forward_path(pd_mlp *m, int path);
 /* One Adam step on the MSE loss of (X, T); *loss receives the loss before the

@@ -276,7 +276,7 @@ __global__ void k_to_bf16_pad(const float *__restrict__ X, int64_t rows, int col
 
 // dY = bf16(2 (Y - T) / (B * nout)), padded to ldo; per-block loss partials
 __global__ void k_loss(const float *__restrict__ Y, const float *__restrict__ T, int64_t rows, int nout, int ldo,
-                       bf16 *dY, float *partial)
+                       bf16 *dY, float *partial, bf16 *dYT, int64_t ldT)
 {
     __shared__ float s[256];
     float acc = 0.f;
@@ -291,6 +291,7 @@ __global__ void k_loss(const float *__restrict__ Y, const float *__restrict__ T,
             acc += d * d;
         }
         dY[q] = __float2bfloat16_rn(d * scale);
+        if (dYT) dYT[(int64_t)c * ldT + r] = dY[q];  // transposed copy for the weight gradient
     }
     s[threadIdx.x] = acc;
     __syncthreads();
@@ -354,12 +355,14 @@ __global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float
 
 // masters (layout W [out x in] then b) -> padded bf16 W [out_pad x in_pad] and fp32 bias [out_pad]
 __global__ void k_pack_layer(const float *__restrict__ W, const float *__restrict__ b, int out, int in, int out_pad,
-                             int in_pad, bf16 *Wb, float *bp)
+                             int in_pad, bf16 *Wb, float *bp, bf16 *WT)
 {
     const int64_t total = (int64_t)out_pad * in_pad;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(q / in_pad), c = (int)(q % in_pad);
-        Wb[q] = __float2bfloat16_rn((r < out && c < in) ? W[(int64_t)r * in + c] : 0.f);
+        const bf16 w = __float2bfloat16_rn((r < out && c < in) ? W[(int64_t)r * in + c] : 0.f);
+        Wb[q] = w;
+        if (WT) WT[(int64_t)c * out_pad + r] = w;  // [in_pad x out_pad], for the data gradient on tcgen05
         if (c == 0) bp[r] = r < out ? b[r] : 0.f;
     }
 }
@@ -378,12 +381,18 @@ struct pd_mlp {
     float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
     int64_t t = 0;
     bf16 *Wb[8] = {nullptr};
+    bf16 *WT[8] = {nullptr};  // W transposed (tcgen05 training)
     float *bias[8] = {nullptr};
     // activations (capacity in rows)
     int64_t cap = 0;
     bf16 *H[9] = {nullptr};   // H[0] input (padded), H[l+1] after layer l (hidden)
     float *Z[8] = {nullptr};  // pre-activations of hidden layers
     bf16 *dZ[9] = {nullptr};  // gradient w.r.t. pre-activation of layer l (dZ[L-1] = dY)
+    // tcgen05 training: HT[l] = layer l's input transposed [pad[l] x ldT], dZT[l] =
+    // dZ[l] transposed [pad[l+1] x ldT]
+    bf16 *HT[8] = {nullptr}, *dZT[8] = {nullptr};
+    int64_t ldT = 0;
+    int tc_train = -1;        // -1: untried; 1: tcgen05 training works here; 0: mma.sync
     float *Y = nullptr, *Xf = nullptr, *Tf = nullptr;
     float *part = nullptr;    // split-K partials
     int64_t part_cap = 0;
@@ -395,6 +404,13 @@ struct pd_mlp {
 
 int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
                    int64_t rows, float *Y, unsigned *err, int device, cudaStream_t st);
+int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
+                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         unsigned *err, int device, cudaStream_t st);
+int mlp_dgelu_tc(const void *dZ, const void *WT, const float *z, int64_t rows, int N, int K, void *out, void *outT,
+                 int64_t ldT, unsigned *err, int device, cudaStream_t st);
+int mlp_dw_tc(const void *dZT, const void *HT, int64_t rows, int64_t ldT, int M, int N, float *part, int max_splits,
+              unsigned *err, int device, cudaStream_t st);
 
 namespace {
 
@@ -455,7 +471,7 @@ pd_status pack_all(pd_mlp *m)
     for (int l = 0; l < m->L; ++l) {
         k_pack_layer<<<grid1((int64_t)m->pad[l + 1] * m->pad[l]), 256, 0, m->st>>>(
             m->master + m->woff[l], m->master + m->boff[l], m->dims[l + 1], m->dims[l], m->pad[l + 1], m->pad[l],
-            m->Wb[l], m->bias[l]);
+            m->Wb[l], m->bias[l], m->WT[l]);
     }
     MCK(cudaGetLastError());
     return PD_OK;
@@ -466,6 +482,7 @@ pd_status ensure_cap(pd_mlp *m, int64_t rows, bool train)
     if (rows <= m->cap && (!train || m->Z[0] || m->L == 1)) return PD_OK;
     int64_t cap = std::max<int64_t>(rows, m->cap);
     for (int l = 0; l <= m->L; ++l) { mfree(m, m->H[l]); m->H[l] = nullptr; mfree(m, m->dZ[l]); m->dZ[l] = nullptr; }
+    for (int l = 0; l < m->L; ++l) { mfree(m, m->HT[l]); m->HT[l] = nullptr; mfree(m, m->dZT[l]); m->dZT[l] = nullptr; }
     for (int l = 0; l < m->L; ++l) { mfree(m, m->Z[l]); m->Z[l] = nullptr; }
     mfree(m, m->Y); mfree(m, m->Xf); mfree(m, m->Tf); mfree(m, m->lpart);
     pd_status s;
@@ -476,6 +493,10 @@ pd_status ensure_cap(pd_mlp *m, int64_t rows, bool train)
             if ((s = malloc_(m, &m->Z[l], cap * m->pad[l + 1]))) return s;
         for (int l = 0; l < m->L; ++l)
             if ((s = malloc_(m, &m->dZ[l], cap * m->pad[l + 1]))) return s;
+        m->ldT = (cap + 7) / 8 * 8;  // transposed rows: 16-byte strides for TMA
+        for (int l = 0; l < m->L; ++l)
+            if ((s = malloc_(m, &m->HT[l], m->ldT * m->pad[l])) || (s = malloc_(m, &m->dZT[l], m->ldT * m->pad[l + 1])))
+                return s;
     }
     if ((s = malloc_(m, &m->Y, cap * m->dims[m->L]))) return s;
     if ((s = malloc_(m, &m->Xf, cap * m->dims[0]))) return s;
@@ -520,14 +541,66 @@ pd_status forward_dev(pd_mlp *m, const float *X, int64_t rows, float *Y, bool ke
     return PD_OK;
 }
 
+pd_status ensure_part(pd_mlp *m, int64_t need)
+{
+    if (need <= m->part_cap) return PD_OK;
+    mfree(m, m->part);
+    m->part = nullptr;
+    pd_status s = malloc_(m, &m->part, need);
+    if (s) return s;
+    m->part_cap = need;
+    return PD_OK;
+}
+
+// The same gradient on the tcgen05 kernels: the fused forward stores Z and the
+// transposed layer inputs; dW = dZ^T H and dZ_{l-1} = (dZ_l W_l) GELU'(Z_{l-1})
+// are tcgen05 GEMMs with K-major operands.  Returns -1 (nothing enqueued that
+// changes results) when the kernels cannot run this network.
+int backward_tc(pd_mlp *m, const float *X, const float *T, int64_t rows, float *dloss)
+{
+    const int L = m->L, nout = m->dims[L];
+    for (int l = 0; l + 1 < L; ++l)
+        if (m->pad[l + 1] % 32 != 0) return -1;
+    void *W[8], *HT[8];
+    const float *b[8];
+    float *Z[8];
+    for (int l = 0; l < L; ++l) { W[l] = m->Wb[l]; b[l] = m->bias[l]; HT[l] = m->HT[l]; Z[l] = m->Z[l]; }
+    if (mlp_forward_train_tc(L, m->dims, m->pad, W, b, X, rows, m->Y, Z, HT, m->ldT, m->tc_err, m->device, m->st))
+        return -1;
+    const int nb = std::min(grid1(rows * m->pad[L]), 8192);
+    k_loss<<<nb, 256, 0, m->st>>>(m->Y, T, rows, nout, m->pad[L], m->dZ[L - 1], m->lpart, m->dZT[L - 1], m->ldT);
+    k_loss_final<<<1, 32, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
+    const int max_splits = 128;
+    for (int l = L - 1; l >= 0; --l) {
+        const int N = m->pad[l + 1], K = m->pad[l];
+        if (ensure_part(m, (int64_t)max_splits * ((N + 127) / 128 * 128) * K)) return -2;
+        const int splits = mlp_dw_tc(m->dZT[l], m->HT[l], rows, m->ldT, N, K, m->part, max_splits, m->tc_err,
+                                     m->device, m->st);
+        if (splits <= 0) return -2;
+        k_reduce_dw<<<grid1((int64_t)m->dims[l + 1] * m->dims[l]), 256, 0, m->st>>>(
+            m->part, splits, N, K, m->dims[l + 1], m->dims[l], m->grad + m->woff[l]);
+        k_colsum<<<m->dims[l + 1], 256, 0, m->st>>>(m->dZ[l], rows, N, m->dims[l + 1], m->grad + m->boff[l]);
+        if (l > 0 && mlp_dgelu_tc(m->dZ[l], m->WT[l], m->Z[l - 1], rows, K, N, m->dZ[l - 1], m->dZT[l - 1], m->ldT,
+                                  m->tc_err, m->device, m->st))
+            return -2;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 // gradient of the MSE loss into m->grad (parameter layout); loss to dloss (device)
 pd_status backward_dev(pd_mlp *m, const float *X, const float *T, int64_t rows, float *dloss)
 {
+    if (m->path != 1) {
+        const int r = backward_tc(m, X, T, rows, dloss);
+        if (r == 0) return PD_OK;
+        if (r == -2) return mfail(m, PD_ECUDA, "tcgen05 training kernels failed to launch");
+        if (m->path == 2) return mfail(m, PD_EINVAL, "the tcgen05 kernels cannot train this network or GPU");
+    }
     pd_status s = forward_dev(m, X, rows, m->Y, true);
     if (s) return s;
     const int L = m->L, nout = m->dims[L];
     const int nb = std::min(grid1(rows * m->pad[L]), 8192);
-    k_loss<<<nb, 256, 0, m->st>>>(m->Y, T, rows, nout, m->pad[L], m->dZ[L - 1], m->lpart);
+    k_loss<<<nb, 256, 0, m->st>>>(m->Y, T, rows, nout, m->pad[L], m->dZ[L - 1], m->lpart, nullptr, 0);
     k_loss_final<<<1, 32, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
     for (int l = L - 1; l >= 0; --l) {
         const int N = m->pad[l + 1], K = m->pad[l];
@@ -606,6 +679,7 @@ pd_status pd_mlp_create(const int *dims, int nlayers, uint64_t seed, int device,
     }
     for (int l = 0; l < nlayers; ++l) {
         if ((s = malloc_(m, &m->Wb[l], (int64_t)m->pad[l + 1] * m->pad[l])) ||
+            (s = malloc_(m, &m->WT[l], (int64_t)m->pad[l + 1] * m->pad[l])) ||
             (s = malloc_(m, &m->bias[l], m->pad[l + 1]))) {
             pd_mlp_destroy(m);
             return s;

@@ -56,6 +56,11 @@ struct Params {
     int out_cols;
     int64_t rows;
     unsigned *err;    // error word (1 = a wait timed out)
+    // training forward (nullable otherwise): Z[l] pre-activations of hidden layer l
+    // [rows x N_l] FP32; HT[l] layer l's input transposed [K_l x ldT] BF16
+    float *Z[MAX_LAYERS];
+    __nv_bfloat16 *HT[MAX_LAYERS];
+    int64_t ldT;
 };
 
 // ---- PTX wrappers -------------------------------------------------------------
@@ -267,8 +272,15 @@ __device__ __forceinline__ void stage_input(const Params &P, int64_t t, unsigned
             const int k = k0 + e;
             xv[e] = (rr < P.rows && k < P.in_cols) ? P.X[rr * P.in_cols + k] : 0.f;
         }
-        *(uint4 *)(sA + sw128_offset(mm, k0)) = make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]),
-                                                           pack_bf16x2(xv[4], xv[5]), pack_bf16x2(xv[6], xv[7]));
+        const uint4 pk = make_uint4(pack_bf16x2(xv[0], xv[1]), pack_bf16x2(xv[2], xv[3]), pack_bf16x2(xv[4], xv[5]),
+                                    pack_bf16x2(xv[6], xv[7]));
+        *(uint4 *)(sA + sw128_offset(mm, k0)) = pk;
+        if (P.HT[0] && rr < P.rows) {  // training: the input transposed, for the first weight gradient
+            const __nv_bfloat16 *hb = (const __nv_bfloat16 *)&pk;
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (k0 + e < P.layer[0].K) P.HT[0][(int64_t)(k0 + e) * P.ldT + rr] = hb[e];
+        }
     }
 }
 
@@ -414,14 +426,26 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
 #pragma unroll
                             for (int c8 = 0; c8 < 32; c8 += 8) {
                                 uint32_t pk[4];
+                                float zs[8];
 #pragma unroll
                                 for (int e = 0; e < 8; e += 2) {
                                     const float2 zz = __fadd2_rn(make_float2(v[c8 + e], v[c8 + e + 1]),
                                                                  make_float2(bb[c8 + e], bb[c8 + e + 1]));
+                                    zs[e] = zz.x;
+                                    zs[e + 1] = zz.y;
                                     const float2 g2 = gelu2(zz);
                                     pk[e / 2] = pack_bf16x2(g2.x, g2.y);
                                 }
                                 *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                                if (P.Z[l] && row < P.rows) {  // training: Z for GELU', H^T for dW
+                                    float *zr = P.Z[l] + row * Ly.N + c0 + c8;
+                                    *(float4 *)zr = make_float4(zs[0], zs[1], zs[2], zs[3]);
+                                    *(float4 *)(zr + 4) = make_float4(zs[4], zs[5], zs[6], zs[7]);
+                                    const __nv_bfloat16 *hb = (const __nv_bfloat16 *)pk;
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e)
+                                        P.HT[l + 1][(int64_t)(c0 + c8 + e) * P.ldT + row] = hb[e];
+                                }
                             }
                         } else if (!last) {
 #pragma unroll
@@ -484,18 +508,274 @@ encode_fn_t encoder()
 
 }  // namespace
 
+// ---- generic GEMM for training: C[M x N] = A[M x K] * B[N x K]^T ---------------
+// Both operands K-major and fed by TMA (same 128-byte swizzle as above); one
+// 128-row tile of C per CTA and one split of K (blockIdx.y); N <= 256.
+//   GEMM_DGELU:   d = acc * GELU'(z) -> BF16 out[m][n] (ld N) and outT[n][m] (ld ldT)
+//   GEMM_PARTIAL: acc -> FP32 part[split][m][n] (split-K partial sums)
+namespace {
+
+constexpr int G_EPI = 256;  // 8 epilogue warps, 2 per TMEM lane quarter
+constexpr int G_THREADS = 64 + G_EPI;
+constexpr int G_A_STAGE = TILE_M * KCHUNK * 2;  // 16 KiB
+enum { GEMM_DGELU = 0, GEMM_PARTIAL = 1 };
+
+struct GemmP {
+    int M, N, kchunks, kcs;   // kcs: K chunks per split
+    int mode;
+    int64_t m_valid;          // rows of C that exist
+    const float *z;           // DGELU: pre-activation [M x N]
+    __nv_bfloat16 *out, *outT;
+    int64_t ldT;
+    float *part;              // PARTIAL
+    unsigned *err;
+};
+
+// GELU'(z) = Phi(z) + z phi(z); Phi from the same Abramowitz-Stegun erf as gelu2,
+// and exp(-z^2/2) is the exp(-x^2) of that erf
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = rcp_approx(fmaf(0.3275911f, x, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float ex = ex2_approx(-1.4426950408889634f * x * x);
+    const float e = 1.0f - poly * ex;
+    return 0.5f * (1.0f + copysignf(e, z)) + z * ex * 0.3989422804014327f;
+}
+
+__global__ void __launch_bounds__(G_THREADS, 1) k_gemm_tc(const __grid_constant__ CUtensorMap ma,
+                                                          const __grid_constant__ CUtensorMap mb, const GemmP P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;                                  // STAGES x 16 KiB
+    unsigned char *sB = base + STAGES * G_A_STAGE;             // STAGES x 32 KiB
+    uint64_t *full = (uint64_t *)(sB + STAGES * W_STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;
+    uint64_t *done = acc_full + 1;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(full + q, 1);
+            mbar_init(empty + q, 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(MAX_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int m0 = blockIdx.x * TILE_M;
+    const int kc0 = blockIdx.y * P.kcs, kc1 = min(P.kchunks, kc0 + P.kcs);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int last_ph[STAGES];
+            for (int q = 0; q < STAGES; ++q) last_ph[q] = -1;
+            for (int kc = kc0; kc < kc1; ++kc) {
+                if (!mbar_wait(empty + s, ph ^ 1)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                mbar_expect_tx(full + s, (uint32_t)(G_A_STAGE + P.N * KCHUNK * 2));
+                tma_load_2d(sA + s * G_A_STAGE, &ma, full + s, kc * KCHUNK, m0);
+                tma_load_2d(sB + s * W_STAGE_BYTES, &mb, full + s, kc * KCHUNK, 0);
+                last_ph[s] = (int)ph;
+                if (++s == STAGES) { s = 0; ph ^= 1; }
+            }
+            for (int q = 0; q < STAGES; ++q)
+                if (last_ph[q] >= 0 && !mbar_wait(full + q, (uint32_t)last_ph[q])) atomicOr(P.err, 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            const uint32_t idesc = idesc_bf16(TILE_M, P.N);
+            for (int kc = kc0; kc < kc1 && !s_abort; ++kc) {
+                if (!mbar_wait(full + s, ph)) { atomicOr(P.err, 1u); s_abort = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + s * G_A_STAGE);
+                const uint32_t b0 = smem_u32(sB + s * W_STAGE_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < KCHUNK / 16; ++kk)
+                    mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kc != kc0 || kk != 0));
+                mma_commit(empty + s);
+                if (++s == STAGES) { s = 0; ph ^= 1; }
+            }
+            mma_commit(acc_full);
+            mma_commit(done);
+            if (!mbar_wait(done, 0)) atomicOr(P.err, 1u);
+        }
+    } else {
+        const int q = warp & 3;
+        const int part = (warp - 2) >> 2;  // 0..1
+        const int m = q * 32 + lane;
+        const int64_t row = (int64_t)m0 + m;
+        __syncwarp();
+        const bool ok = mbar_wait(acc_full, 0);
+        if (!ok) { atomicOr(P.err, 1u); s_abort = 1; }
+        if (!__any_sync(0xffffffffu, !ok || s_abort)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int hw = ((P.N / 2 + 31) / 32) * 32;
+            const int cend = min(P.N, (part + 1) * hw);
+            for (int c0 = part * hw; c0 < cend; c0 += 32) {
+                float v[32];
+                __syncwarp();
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (row >= P.m_valid) continue;
+                if (P.mode == GEMM_PARTIAL) {
+                    float *dst = P.part + ((int64_t)blockIdx.y * P.M + row) * P.N + c0;
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4)
+                        if (c0 + e < P.N) *(float4 *)(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                } else {
+                    const float *zr = P.z + row * P.N + c0;
+#pragma unroll
+                    for (int e = 0; e < 32; e += 8) {
+                        if (c0 + e >= P.N) break;
+                        const float4 z0 = *(const float4 *)(zr + e), z1 = *(const float4 *)(zr + e + 4);
+                        const float d0 = v[e] * gelu_grad(z0.x), d1 = v[e + 1] * gelu_grad(z0.y);
+                        const float d2 = v[e + 2] * gelu_grad(z0.z), d3 = v[e + 3] * gelu_grad(z0.w);
+                        const float d4 = v[e + 4] * gelu_grad(z1.x), d5 = v[e + 5] * gelu_grad(z1.y);
+                        const float d6 = v[e + 6] * gelu_grad(z1.z), d7 = v[e + 7] * gelu_grad(z1.w);
+                        const uint4 pk = make_uint4(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3), pack_bf16x2(d4, d5),
+                                                    pack_bf16x2(d6, d7));
+                        *(uint4 *)(P.out + row * P.N + c0 + e) = pk;
+                        const __nv_bfloat16 *hb = (const __nv_bfloat16 *)&pk;
+#pragma unroll
+                        for (int w = 0; w < 8; ++w) P.outT[(int64_t)(c0 + e + w) * P.ldT + row] = hb[w];
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    __syncwarp();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MAX_N));
+}
+
+// K-major BF16 tensor map: rows x cols (cols = K, contiguous), row stride ld elements
+bool kmajor_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows)
+{
+    encode_fn_t enc = encoder();
+    if (!enc || (ld * 2) % 16 != 0 || ((uintptr_t)ptr & 15u) || box_rows > 256) return false;
+    const cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t gstride[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), gdim, gstride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t gemm_tc_smem() { return 1024 + STAGES * (G_A_STAGE + W_STAGE_BYTES) + 128; }
+
+int gemm_tc(const GemmP &P0, const void *A, int64_t a_rows, int64_t a_cols, int64_t a_ld, const void *B,
+            int64_t b_ld, int splits, int device, cudaStream_t st)
+{
+    GemmP P = P0;
+    if (P.N < 16 || P.N > MAX_N || P.N % 16 || splits < 1) return -1;
+    CUtensorMap ma, mb;
+    if (!kmajor_map(&ma, A, a_rows, a_cols, a_ld, TILE_M) || !kmajor_map(&mb, B, P.N, a_cols, b_ld, P.N)) return -1;
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_tc_smem());
+        configured = true;
+    }
+    const dim3 grid((unsigned)((P.M + TILE_M - 1) / TILE_M), (unsigned)splits);
+    k_gemm_tc<<<grid, G_THREADS, gemm_tc_smem(), st>>>(ma, mb, P);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+// dZ_prev = (dZ * W) . GELU'(Z): A = dZ [rows x K] (ld K), B = W^T [N x K] (ld K),
+// z = Z [rows x N]; writes out [rows x N] and outT [N x ldT].  N <= 256.
+int mlp_dgelu_tc(const void *dZ, const void *WT, const float *z, int64_t rows, int N, int K, void *out, void *outT,
+                 int64_t ldT, unsigned *err, int device, cudaStream_t st)
+{
+    GemmP P;
+    memset(&P, 0, sizeof(P));
+    P.M = (int)((rows + TILE_M - 1) / TILE_M) * TILE_M;
+    P.N = N;
+    P.kchunks = (K + KCHUNK - 1) / KCHUNK;
+    P.kcs = P.kchunks;
+    P.mode = GEMM_DGELU;
+    P.m_valid = rows;
+    P.z = z;
+    P.out = (__nv_bfloat16 *)out;
+    P.outT = (__nv_bfloat16 *)outT;
+    P.ldT = ldT;
+    P.err = err;
+    return gemm_tc(P, dZ, rows, K, K, WT, K, 1, device, st);
+}
+
+// split-K partials of dW = dZ^T H: A = dZ^T [M x rows] (ld ldT), B = H^T [N x rows]
+// (ld ldT); part [splits x M x N] FP32.  Returns the number of splits used
+// (<= 0 on failure).
+int mlp_dw_tc(const void *dZT, const void *HT, int64_t rows, int64_t ldT, int M, int N, float *part, int max_splits,
+              unsigned *err, int device, cudaStream_t st)
+{
+    GemmP P;
+    memset(&P, 0, sizeof(P));
+    P.M = M;
+    P.N = N;
+    P.kchunks = (int)((rows + KCHUNK - 1) / KCHUNK);
+    const int mt = (M + TILE_M - 1) / TILE_M;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int splits = std::max(1, std::min(max_splits, sms / std::max(1, mt)));
+    P.kcs = (P.kchunks + splits - 1) / splits;
+    splits = (P.kchunks + P.kcs - 1) / P.kcs;  // no empty split
+    P.mode = GEMM_PARTIAL;
+    P.m_valid = M;
+    P.part = part;
+    P.err = err;
+    return gemm_tc(P, dZT, M, rows, ldT, HT, ldT, splits, device, st) == 0 ? splits : -1;
+}
+
 size_t mlp_tc_smem() { return 1024 + 2 * A_BYTES + STAGES * W_STAGE_BYTES + 256; }
 
 // Forward of an MLP whose layers all fit the fused kernel (K, N <= 256).
 // W[l]: padded BF16 weights [pad_out x pad_in] row-major; bias[l]: pad_out
 // floats.  Returns 0 on success, -1 if the shape is unsupported or the tensor
 // maps cannot be made (the caller then uses the mma.sync kernels).
+// Training forward: the same kernel also stores Z[l] (FP32 [rows x pad[l+1]],
+// hidden layers) and HT[l] (BF16 [pad[l] x ldT], every layer's input
+// transposed).  Hidden widths must be multiples of 32.
+int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
+                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         unsigned *err, int device, cudaStream_t st);
+
 int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
                    int64_t rows, float *Y, unsigned *err, int device, cudaStream_t st)
+{
+    return mlp_forward_train_tc(L, dims, pad, W, bias, X, rows, Y, nullptr, nullptr, 0, err, device, st);
+}
+
+int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
+                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         unsigned *err, int device, cudaStream_t st)
 {
     if (L < 1 || L > MAX_LAYERS || rows < 1) return -1;
     for (int l = 0; l < L; ++l)
         if (pad[l] > MAX_K || pad[l + 1] > MAX_N || pad[l + 1] % 16 != 0) return -1;
+    if (Z)
+        for (int l = 0; l + 1 < L; ++l)
+            if (pad[l + 1] % 32 != 0) return -1;
     int major = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
     if (major < 10) return -1;
@@ -526,6 +806,13 @@ int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const
     P.out_cols = dims[L];
     P.rows = rows;
     P.err = err;
+    if (Z) {
+        for (int l = 0; l < L; ++l) {
+            P.Z[l] = (l + 1 < L) ? Z[l] : nullptr;
+            P.HT[l] = (__nv_bfloat16 *)HT[l];
+        }
+        P.ldT = ldT;
+    }
     const size_t smem = mlp_tc_smem();
     static bool configured = false;
     if (!configured) {

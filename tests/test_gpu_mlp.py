@@ -74,9 +74,12 @@ def test_forward_full_batch_sampled(pd, path):
     assert np.all(np.isfinite(Y))
 
 
+@pytest.mark.parametrize("path", [2, 1])
 @pytest.mark.parametrize("batch", [64, 999, 4096])
-def test_gradient_matches_oracle(pd, batch):
+def test_gradient_matches_oracle(pd, batch, path):
+    """path 2: tcgen05 forward and backward GEMMs (required); path 1: mma.sync."""
     net = pd.MLP(DIMS)
+    net.set_forward_path(path)
     th = theta(6, scale=1.7)
     net.set_params(th)
     X, T = inputs(batch, 7)
@@ -104,9 +107,11 @@ def test_adam_update_matches_oracle(pd):
     assert np.allclose(net.get_params(), opt.theta, rtol=1e-5, atol=1e-7)
 
 
-def test_training_reduces_loss(pd):
+@pytest.mark.parametrize("path", [2, 1])
+def test_training_reduces_loss(pd, path):
     """Fit a smooth map: the loss falls by an order of magnitude."""
     net = pd.MLP(DIMS, seed=3)
+    net.set_forward_path(path)
     rng = np.random.default_rng(10)
     X = rng.normal(0, 1, (8192, DIMS[0])).astype(np.float32)
     A = rng.normal(0, 0.2, (DIMS[0], DIMS[-1]))
@@ -115,3 +120,18 @@ def test_training_reduces_loss(pd):
     for _ in range(150):
         last = net.train_step(X, T, 1e-3)
     assert last < 0.1 * first
+
+
+def test_gradient_full_batch_sampled_tc(pd):
+    """The benchmark's batch (65,536) on the tcgen05 training path: gradient
+    against the oracle evaluated on the same batch (the oracle's FP64 forward
+    and backward over 65,536 rows take a few seconds)."""
+    net = pd.MLP(DIMS)
+    net.set_forward_path(2)
+    th = theta(11, scale=1.7)
+    net.set_params(th)
+    X, T = inputs(65536, 12)
+    loss, g = net.grad(X, T)
+    rl, rg = omlp.loss_and_grad(th.astype(np.float64), X, T, DIMS, bf16=True)
+    assert loss == pytest.approx(rl, rel=FWD_TOL)
+    assert rel_l2(g, rg) < GRAD_TOL
