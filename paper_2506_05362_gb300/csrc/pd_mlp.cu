@@ -302,13 +302,37 @@ __global__ void k_loss(const float *__restrict__ Y, const float *__restrict__ T,
     if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
 }
 
+// fixed-order tree over the block partials (one block of 256 threads)
 __global__ void k_loss_final(const float *__restrict__ partial, int nb, int64_t count, float *loss)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += partial[b];
-        *loss = (float)(s / (double)count);
+    __shared__ double s[256];
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 256) acc += partial[b];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *loss = (float)(s[0] / (double)count);
+}
+
+// row sums of dZ^T (bf16 [n x ld], first `rows` columns) into gb: the bias
+// gradient from the transposed copy, with coalesced reads; fixed order
+__global__ void k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld, int n_valid, float *gb)
+{
+    __shared__ float s[256];
+    const int c = blockIdx.x;
+    float acc = 0.f;
+    const bf16 *r = dZT + (int64_t)c * ld;
+    for (int64_t q = threadIdx.x; q < rows; q += blockDim.x) acc += __bfloat162float(r[q]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && c < n_valid) gb[c] = s[0];
 }
 
 // fixed-order sum of split-K partials into the gradient vector; rows < n_valid, cols < k_valid
@@ -569,7 +593,7 @@ int backward_tc(pd_mlp *m, const float *X, const float *T, int64_t rows, float *
         return -1;
     const int nb = std::min(grid1(rows * m->pad[L]), 8192);
     k_loss<<<nb, 256, 0, m->st>>>(m->Y, T, rows, nout, m->pad[L], m->dZ[L - 1], m->lpart, m->dZT[L - 1], m->ldT);
-    k_loss_final<<<1, 32, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
+    k_loss_final<<<1, 256, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
     const int max_splits = 128;
     for (int l = L - 1; l >= 0; --l) {
         const int N = m->pad[l + 1], K = m->pad[l];
@@ -579,7 +603,7 @@ int backward_tc(pd_mlp *m, const float *X, const float *T, int64_t rows, float *
         if (splits <= 0) return -2;
         k_reduce_dw<<<grid1((int64_t)m->dims[l + 1] * m->dims[l]), 256, 0, m->st>>>(
             m->part, splits, N, K, m->dims[l + 1], m->dims[l], m->grad + m->woff[l]);
-        k_colsum<<<m->dims[l + 1], 256, 0, m->st>>>(m->dZ[l], rows, N, m->dims[l + 1], m->grad + m->boff[l]);
+        k_rowsum<<<m->dims[l + 1], 256, 0, m->st>>>(m->dZT[l], rows, m->ldT, m->dims[l + 1], m->grad + m->boff[l]);
         if (l > 0 && mlp_dgelu_tc(m->dZ[l], m->WT[l], m->Z[l - 1], rows, K, N, m->dZ[l - 1], m->dZT[l - 1], m->ldT,
                                   m->tc_err, m->device, m->st))
             return -2;
@@ -601,7 +625,7 @@ pd_status backward_dev(pd_mlp *m, const float *X, const float *T, int64_t rows, 
     const int L = m->L, nout = m->dims[L];
     const int nb = std::min(grid1(rows * m->pad[L]), 8192);
     k_loss<<<nb, 256, 0, m->st>>>(m->Y, T, rows, nout, m->pad[L], m->dZ[L - 1], m->lpart, nullptr, 0);
-    k_loss_final<<<1, 32, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
+    k_loss_final<<<1, 256, 0, m->st>>>(m->lpart, nb, rows * nout, dloss);
     for (int l = L - 1; l >= 0; --l) {
         const int N = m->pad[l + 1], K = m->pad[l];
         // weight gradient: dW = dZ^T H, batch split across CTAs
