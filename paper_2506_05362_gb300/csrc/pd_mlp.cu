@@ -324,8 +324,18 @@ __global__ void k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld,
     __shared__ float s[256];
     const int c = blockIdx.x;
     float acc = 0.f;
-    const bf16 *r = dZT + (int64_t)c * ld;
-    for (int64_t q = threadIdx.x; q < rows; q += blockDim.x) acc += __bfloat162float(r[q]);
+    const bf16 *r = dZT + (int64_t)c * ld;  // ld is a multiple of 8: rows start 16-byte aligned
+    const int64_t r8 = rows / 8;
+    for (int64_t q = threadIdx.x; q < r8; q += blockDim.x) {
+        const uint4 w = *(const uint4 *)(r + 8 * q);
+        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&w;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(h[e]);
+            acc += f.x + f.y;
+        }
+    }
+    for (int64_t q = 8 * r8 + threadIdx.x; q < rows; q += blockDim.x) acc += __bfloat162float(r[q]);
     s[threadIdx.x] = acc;
     __syncthreads();
     for (int o = 128; o > 0; o >>= 1) {
