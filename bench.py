@@ -35,13 +35,19 @@ WORKLOADS = {
     "sphere": "glass sphere radius 1 mm, h=0.1 mm, 4,139 nodes, delta=3h, plates at 1 m/s, dt=0.8 dt_crit",
     "hollow": "glass hollow sphere R=1 mm, r=0.7 mm, h=0.02 mm, 343,846 nodes, delta=3h, plates at 5 m/s",
     "aggregate": "1000 star-shaped glass grains, h=R/12, ~7.6 M nodes, delta=3h, six walls, top wall at 10 m/s",
+    "shape-sphere": "shape study: 125 solid glass spheres R=1 mm, h=R/8 (262,875 nodes), delta=3h, top wall 10 m/s",
+    "shape-shell": "shape study: 125 glass shells R=1 mm, r=0.7R, h=R/8 (170,500 nodes), top wall 10 m/s",
+    "shape-jack": "shape study: 125 glass jacks R=1 mm (arms R/3), h=R/8 (93,375 nodes), top wall 10 m/s",
+    "double-hollow": "two stacked glass shells R=1 mm, r=0.7R, h=0.04 mm (85,084 nodes), top wall 10 m/s",
 }
 
 
 def make_workload(name):
     from paper_2506_05362_gb300 import scenarios as S
     return {"plate": S.kalthoff, "sphere": S.sphere, "hollow": S.hollow,
-            "aggregate": lambda: S.aggregate(n_grains=1000, seed=0)}[name]()
+            "aggregate": lambda: S.aggregate(n_grains=1000, seed=0),
+            "shape-sphere": lambda: S.shape_study("sphere"), "shape-shell": lambda: S.shape_study("shell"),
+            "shape-jack": lambda: S.shape_study("jack"), "double-hollow": S.double_hollow}[name]()
 BYTES_PER_NODE = 170.0      # x, V, u (r/w), v (r/w), F, row pointers per node and step
 BYTES_PER_BOND = 4.0 + 1.0 / 8.0  # neighbour index + broken bit per directed bond
 

@@ -307,6 +307,96 @@ def small_block(seed: int = 0, nx: int = 6, ny: int = 5, nz: int = 4, h: float =
                     v0=np.zeros((n, 3)), material=_glass(h), horizon=3 * h, h=h, steps=10)
 
 
+def shape_particle(shape: str, R: float, h: float) -> np.ndarray:
+    """Lattice nodes (spacing h, centred at 0) of one particle of the shape study
+    (Sec. 6.5): "sphere" (|x| < R), "shell" (0.7 R <= |x| < R, the hollow spheres
+    of Sec. 6.3), or "jack", a 3-D plus of three orthogonal cylinders reaching R from
+    the centre.  Reading: the paper gives no jack dimensions; the arm radius is R/3."""
+    k = int(math.ceil(R / h))
+    i = np.arange(-k, k + 1)
+    I, J, K = np.meshgrid(i, i, i, indexing="ij")
+    lat = np.stack([I.ravel(), J.ravel(), K.ravel()], axis=1).astype(np.float64) * h
+    r2 = (lat * lat).sum(1)
+    if shape == "sphere":
+        m = r2 < R * R
+    elif shape == "shell":
+        m = (r2 < R * R) & (r2 >= (0.7 * R) ** 2)
+    elif shape == "jack":
+        a2 = (R / 3.0) ** 2
+        m = np.zeros(len(lat), bool)
+        for ax in range(3):
+            o = [q for q in range(3) if q != ax]
+            m |= (np.abs(lat[:, ax]) < R) & ((lat[:, o] ** 2).sum(1) < a2)
+    else:
+        raise ValueError(f"unknown shape {shape!r}")
+    return lat[m]
+
+
+def _box_walls(x: np.ndarray, rc: float, top_speed: float):
+    """Six walls just out of reach of the extreme nodes; the top (+z) one moves down."""
+    lo = x.min(axis=0) - rc
+    hi = x.max(axis=0) + rc
+    return [Wall((1.0, 0.0, 0.0), (lo[0], 0.0, 0.0), (0.0, 0.0, 0.0)),
+            Wall((-1.0, 0.0, 0.0), (hi[0], 0.0, 0.0), (0.0, 0.0, 0.0)),
+            Wall((0.0, 1.0, 0.0), (0.0, lo[1], 0.0), (0.0, 0.0, 0.0)),
+            Wall((0.0, -1.0, 0.0), (0.0, hi[1], 0.0), (0.0, 0.0, 0.0)),
+            Wall((0.0, 0.0, 1.0), (0.0, 0.0, lo[2]), (0.0, 0.0, 0.0)),
+            Wall((0.0, 0.0, -1.0), (0.0, 0.0, hi[2]), (0.0, 0.0, -top_speed))], lo, hi
+
+
+def shape_study(shape: str = "sphere", n_side: int = 5, seed: int = 0, R: float = 1e-3, h: float = 1e-3 / 8,
+                gap_cells: float = 1.0, speed: float = 10.0, steps: int = 2000) -> Scenario:
+    """The shape study of Sec. 6.5: n_side^3 particles of one shape (radius R = 1 mm)
+    on a cubic grid (pitch 2R + gap), glass-like, in a box of six walls whose top wall
+    moves down at ``speed`` (10 m/s).  Bulk strength is the difference of the top and
+    bottom wall reactions over the top area.  Each particle is its own grain."""
+    rng = np.random.default_rng(seed)
+    nodes = shape_particle(shape, R, h)
+    pitch = 2 * R + gap_cells * h
+    xs, gs = [], []
+    g = 0
+    for a in range(n_side):
+        for b in range(n_side):
+            for c in range(n_side):
+                xs.append(nodes + np.array([a, b, c], np.float64) * pitch + _jitter(rng, len(nodes), h))
+                gs.append(np.full(len(nodes), g, np.int32))
+                g += 1
+    x = np.concatenate(xs)
+    n = x.shape[0]
+    mat = _glass(h)
+    walls, lo, hi = _box_walls(x, mat.contact_radius, speed)
+    return Scenario(name=f"shape_{shape}", x=x, vol=np.full(n, h ** 3), grain=np.concatenate(gs),
+                    v0=np.zeros((n, 3)), material=mat, horizon=3 * h, h=h, walls=walls, steps=steps,
+                    wall_area=float((hi[0] - lo[0]) * (hi[1] - lo[1])),
+                    info={"shape": shape, "particles": n_side ** 3, "nodes_per_particle": len(nodes)})
+
+
+def double_hollow(seed: int = 0, h: float = 4e-5, R: float = 1e-3, gap_cells: float = 1.0, speed: float = 10.0,
+                  steps: int = 5000) -> Scenario:
+    """Two hollow glass spheres (R = 1 mm, r = 0.7 R) stacked along z in a cubic
+    container with fixed lateral and bottom walls and a top wall descending at
+    ``speed`` (Sec. 6.3, double hollow sphere).  Reading: the paper gives no mesh
+    size; h = 0.04 mm (two grains of ~43,000 nodes)."""
+    rng = np.random.default_rng(seed)
+    shell = shape_particle("shell", R, h)
+    lower = shell + _jitter(rng, len(shell), h)
+    upper = shell + np.array([0.0, 0.0, 2 * R + gap_cells * h]) + _jitter(rng, len(shell), h)
+    x = np.concatenate([lower, upper])
+    grain = np.concatenate([np.zeros(len(shell), np.int32), np.ones(len(shell), np.int32)])
+    n = x.shape[0]
+    mat = _glass(h)
+    # cubic container: as wide as it is tall around the pair
+    walls, lo, hi = _box_walls(x, mat.contact_radius, speed)
+    half = 0.5 * float((hi - lo).max())
+    mid = 0.5 * (lo + hi)
+    lo_c, hi_c = mid - half, mid + half
+    lo_c[2], hi_c[2] = lo[2], hi[2]
+    walls = [Wall(w.normal, tuple(lo_c if sum(w.normal) > 0 else hi_c), w.velocity) for w in walls]
+    return Scenario(name="double_hollow", x=x, vol=np.full(n, h ** 3), grain=grain, v0=np.zeros((n, 3)),
+                    material=mat, horizon=3 * h, h=h, walls=walls, steps=steps,
+                    wall_area=float((hi_c[0] - lo_c[0]) * (hi_c[1] - lo_c[1])))
+
+
 def walls_array(walls) -> np.ndarray:
     """(nw, 9) float64 rows: normal, point, velocity."""
     if not walls:
@@ -324,4 +414,4 @@ def filters_array(filters):
 
 
 BY_NAME = {"sphere": sphere, "kalthoff": kalthoff, "hollow": hollow, "aggregate": aggregate,
-           "block": small_block}
+           "block": small_block, "shape_study": shape_study, "double_hollow": double_hollow}
