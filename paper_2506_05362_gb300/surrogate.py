@@ -62,6 +62,25 @@ class Run:
     sf_confine: float = 0.0 # solid fraction at the end of the pre-compression
 
 
+def save_runs(path: str, runs) -> None:
+    """Writes runs to one .npz file (arrays stacked per field, in run order)."""
+    import json
+    meta = [{k: getattr(r, k) for k in ("path", "n_grains", "seed", "pd_seconds", "steps", "nodes",
+                                        "precompress_steps", "p_confine", "sf_confine")} for r in runs]
+    arr = {}
+    for q, r in enumerate(runs):
+        arr[f"strain{q}"], arr[f"stress{q}"], arr[f"desc{q}"] = r.strain, r.stress, r.desc
+    np.savez_compressed(path, meta=np.array(json.dumps(meta)), **arr)
+
+
+def load_runs(path: str):
+    """Reads runs written by save_runs."""
+    import json
+    z = np.load(path)
+    meta = json.loads(str(z["meta"]))
+    return [Run(strain=z[f"strain{q}"], stress=z[f"stress{q}"], desc=z[f"desc{q}"], **m) for q, m in enumerate(meta)]
+
+
 def damping_coefficient(material, horizon: float, volume: float, zeta: float) -> float:
     """beta_d (Sec. 3.3) giving a damping ratio ``zeta`` to two nodes of ``volume`` in
     contact: their relative motion has stiffness K_n V^2 (K_n = f_c 18 K / (pi delta^5),
@@ -209,9 +228,11 @@ class Scaler:
         return A * self.sd + self.mu
 
 
-def train(runs, epochs=300, batch=4096, lr=1e-3, seed=0, device=0, stream=None):
+def train(runs, epochs=300, batch=4096, lr=1e-3, seed=0, device=0, stream=None, val_runs=None):
     """Trains the MLP on all windows of ``runs`` on the GPU; returns (net,
-    x_scaler, y_scaler, losses)."""
+    x_scaler, y_scaler, losses).  With ``val_runs`` (runs kept out of the training
+    set) the network is evaluated on them every 10 epochs and the parameters with
+    the lowest validation error are kept (early stopping)."""
     import torch
     from . import pd
     X = np.concatenate([windows(r)[0] for r in runs])
@@ -225,6 +246,7 @@ def train(runs, epochs=300, batch=4096, lr=1e-3, seed=0, device=0, stream=None):
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     losses = []
     m = Xd.shape[0]
+    best, best_params = math.inf, None
     for ep in range(epochs):
         perm = torch.randperm(m, generator=g).to(dev)
         lr_ep = lr * (0.5 * (1 + math.cos(math.pi * ep / epochs)) * 0.9 + 0.1)
@@ -236,6 +258,12 @@ def train(runs, epochs=300, batch=4096, lr=1e-3, seed=0, device=0, stream=None):
         if ep % 10 == 0 or ep == epochs - 1:
             torch.cuda.synchronize(dev)
             losses.append(float(loss.item()))
+            if val_runs:
+                err = float(np.mean([judge(net, xs, ys, r, device=device)[0] for r in val_runs]))
+                if err < best:
+                    best, best_params = err, net.get_params()
+    if best_params is not None:
+        net.set_params(best_params)
     return net, xs, ys, losses
 
 
@@ -272,26 +300,32 @@ def baseline_error(train_runs, run: Run):
 
 
 def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate: float = 2.0e3,
-          records: int = 64, seed: int = 0, device: int = 0, zeta: float = 0.0, log=print):
+          records: int = 64, seed: int = 0, device: int = 0, zeta: float = 0.0, runs=None, log=print):
     """Generates runs_per_path runs per loading path (grain counts cycling through
-    grain_counts, seeds distinct, contact damping ratio zeta), holds out the last
-    run of every path, trains on the rest and judges the held-out runs against
-    their PD results."""
+    grain_counts, seeds distinct, contact damping ratio zeta), or takes ``runs``
+    already generated in that order, holds out the last run of every path, trains
+    on the rest and judges the held-out runs against their PD results."""
     # the network runs on torch's current stream (its tensors are made there);
     # every PD context makes its own capturable stream and synchronises on return
     stream = None
-    runs = []
     t0 = time.perf_counter()
-    for pi, path in enumerate(LOADING_PATHS):
-        for r in range(runs_per_path):
-            ng = grain_counts[r % len(grain_counts)]
-            runs.append(rve_run(path, n_grains=ng, seed=seed + 1000 * pi + r, rate=rate, records=records,
-                                device=device, stream=stream, zeta=zeta))
+    if runs is None:
+        runs = []
+        for pi, path in enumerate(LOADING_PATHS):
+            for r in range(runs_per_path):
+                ng = grain_counts[r % len(grain_counts)]
+                runs.append(rve_run(path, n_grains=ng, seed=seed + 1000 * pi + r, rate=rate, records=records,
+                                    device=device, stream=stream, zeta=zeta))
+    else:
+        assert len(runs) == runs_per_path * len(LOADING_PATHS)
     t_data = time.perf_counter() - t0
     held = [runs[(pi + 1) * runs_per_path - 1] for pi in range(len(LOADING_PATHS))]
     train_runs = [r for r in runs if r not in held]
+    # early stopping on the second-last run of every path (not used for training)
+    val = [runs[(pi + 1) * runs_per_path - 2] for pi in range(len(LOADING_PATHS))] if runs_per_path >= 4 else []
+    fit = [r for r in train_runs if r not in val]
     t0 = time.perf_counter()
-    net, xs, ys, losses = train(train_runs, epochs=epochs, seed=seed, device=device, stream=stream)
+    net, xs, ys, losses = train(fit, epochs=epochs, seed=seed, device=device, stream=stream, val_runs=val)
     t_train = time.perf_counter() - t0
     rows = []
     for r in held:
@@ -302,10 +336,10 @@ def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate:
     errs = np.array([q["err"] for q in rows])
     train_err = [judge(net, xs, ys, r, device=device)[0] for r in train_runs[:16]]
     net.close()
-    return {"runs": len(runs), "train_runs": len(train_runs), "held_out": len(held),
+    return {"runs": len(runs), "train_runs": len(fit), "validation_runs": len(val), "held_out": len(held),
             "train_err_median": float(np.median(train_err)),
             "err_mean_history_median": float(np.median([q["err_mean_history"] for q in rows])),
-            "samples": int(sum(windows(r)[0].shape[0] for r in train_runs)),
+            "samples": int(sum(windows(r)[0].shape[0] for r in fit)),
             "data_seconds": t_data, "train_seconds": t_train, "final_loss": losses[-1],
             "err_median": float(np.median(errs)), "err_max": float(errs.max()),
             "frac_within_5pct": float((errs <= 0.05).mean()),
@@ -323,9 +357,20 @@ if __name__ == "__main__":
     ap.add_argument("--zeta", type=float, default=0.0, help="contact damping ratio of the RVE runs")
     ap.add_argument("--grains", type=int, nargs="+", default=[8, 12], help="grain counts, cycled over the runs")
     ap.add_argument("--out", default=None, help="also write the full report (per held-out run) to this file")
+    ap.add_argument("--runs-file", default=None,
+                    help="read the runs from this .npz if it exists, else generate them and write it")
     a = ap.parse_args()
+    import os
+    runs = load_runs(a.runs_file) if a.runs_file and os.path.exists(a.runs_file) else None
+    if runs is None and a.runs_file:
+        runs = []
+        for pi, path in enumerate(LOADING_PATHS):
+            for r in range(a.runs_per_path):
+                ng = a.grains[r % len(a.grains)]
+                runs.append(rve_run(path, n_grains=ng, seed=a.seed + 1000 * pi + r, records=a.records, zeta=a.zeta))
+        save_runs(a.runs_file, runs)
     rep = study(a.runs_per_path, grain_counts=tuple(a.grains), epochs=a.epochs, records=a.records, seed=a.seed,
-                zeta=a.zeta)
+                zeta=a.zeta, runs=runs)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(rep, f, indent=1)

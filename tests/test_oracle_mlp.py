@@ -93,3 +93,22 @@ def test_bf16_forward_rounds_only_where_stored():
     W, b = mlp.unpack(th, dims)[0]
     expect = mlp.bf16_round(X) @ mlp.bf16_round(W).T + b
     assert np.allclose(mlp.forward(th, X, dims, bf16=True), expect, rtol=1e-14, atol=0)
+
+
+def test_surrogate_runs_round_trip(tmp_path):
+    """Runs written by the study's save_runs come back field for field."""
+    from paper_2506_05362_gb300 import surrogate as SG
+    rng = np.random.default_rng(0)
+    runs = [SG.Run(path=p, n_grains=8 + q, seed=q, strain=rng.normal(size=(5, 6)), stress=rng.normal(size=(5, 6)),
+                   desc=rng.normal(size=(5, 13)), pd_seconds=0.5 * q, steps=100 + q, nodes=1000 + q,
+                   precompress_steps=7, p_confine=2e6, sf_confine=0.6) for q, p in enumerate(["uniaxial_x", "shear_xy"])]
+    f = str(tmp_path / "runs.npz")
+    SG.save_runs(f, runs)
+    back = SG.load_runs(f)
+    assert len(back) == 2
+    for a, b in zip(runs, back):
+        for k in ("path", "n_grains", "seed", "pd_seconds", "steps", "nodes", "precompress_steps", "p_confine",
+                  "sf_confine"):
+            assert getattr(a, k) == getattr(b, k)
+        for k in ("strain", "stress", "desc"):
+            assert np.array_equal(getattr(a, k), getattr(b, k))
