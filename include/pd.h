@@ -85,6 +85,31 @@ typedef struct {
                                s0 = sqrt(7 pi G0 / (12 E delta)).  The bond force, the self-contact
                                law and pd_stable_dt use c(|xi|); pd_stable_dt_noalloc takes a
                                constant micromodulus only. */
+    double mu;              /* stick-slip friction coefficient (>= 0; 0 = frictionless), Sec. 3.3
+                               (Eq. regularized-friction).  A contact pair adds
+                               -min(rho |v_t| / (dt (V_i + V_j)), mu f_r) V_j v_t / |v_t| to the force
+                               density of i, v_t the part of v_i - v_j across the contact normal and
+                               f_r the pair's repulsion per volume squared; a node within R_c of a
+                               wall adds -min(rho |v_t| / dt, mu K_n (R_c - zbar) |S|) v_t / |v_t|,
+                               v_t the part of v_i - v_wall along the wall, which the wall reaction
+                               includes.  Readings: the force opposes the slip; the printed stick
+                               branch rho |v_t| / dt is divided by V_i + V_j (a rigid wall: by |S|),
+                               which conserves momentum and stops an isolated pair's sliding in one
+                               step.  Velocities as for beta_d.  dt is that of the latest pd_step
+                               (pd_step with nsteps = 0 sets it; 0 before any: the Coulomb limit,
+                               slip at any speed); when it changes, pd_step first evaluates the
+                               acceleration again with the new dt. */
+    int wall_overlap;       /* 0 = the single-wall terms are summed (default); 1 = inclusion-
+                               exclusion of Sec. 4.1.1: for every pair of walls with orthogonal
+                               normals that a node touches, minus the repulsion of the region of
+                               its R_c ball beyond both, K_n (R_c - |c - p|) |S| away from that
+                               region's centroid c; plus the same for every mutually orthogonal
+                               triple.  Damping and friction stay single-wall sums; the wall
+                               reactions take each term's component along their own normal.
+                               Readings: the regions' volumes and centroids are computed (the paper
+                               gives the principle only), the triple term's stray V_x is dropped,
+                               and walls that are not orthogonal keep the plain sum.  A material
+                               with mu > 0 or wall_overlap = 1 runs without shared-memory tiles. */
 } pd_material;
 
 typedef struct {
@@ -173,7 +198,9 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
  * whose contact list went stale or overflowed is rolled back to its own start
  * and rerun with a shorter rebuild period or larger lists.  The contact list is
  * rebuilt often enough for the fastest node (or wall) to gain 50% in speed
- * (150% while speeds are growing).
+ * (150% while speeds are growing).  With friction (mu > 0) the call first
+ * records dt as the friction's time step and, if it changed, evaluates the
+ * acceleration at the current state again with it; nsteps = 0 does only that.
  * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL
  * (dt <= 0, nsteps < 0), PD_ENONFINITE / PD_EWALL (state restored to the start
  * of the segment in which it happened, so t tells how far the call got, and
@@ -234,7 +261,8 @@ pd_status pd_bonds(pd_ctx *ctx, int64_t *rowptr, int32_t *col);
 pd_status pd_contacts(pd_ctx *ctx, int64_t *npairs, int32_t *ij);
 
 /* Force density F (n*3, caller order) at the current state without stepping:
- * applies breaking exactly as a step does. */
+ * applies breaking exactly as a step does.  Damping and friction see the
+ * current velocity; friction the time step of the latest pd_step. */
 pd_status pd_forces(pd_ctx *ctx, double *F);
 
 /* State for checkpoints and parity: u, v (n*3), broken (B bytes, 1 = broken, in

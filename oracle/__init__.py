@@ -45,7 +45,8 @@ class Problem(ctypes.Structure):
                 ("Rc", ctypes.c_double), ("rho", ctypes.c_double),
                 ("break_mode", ctypes.c_int), ("contact", ctypes.c_int), ("nw", ctypes.c_int),
                 ("walls", ctypes.c_void_p), ("b", ctypes.c_double * 3), ("frozen", ctypes.c_int),
-                ("beta_d", ctypes.c_double), ("conic", ctypes.c_int), ("delta", ctypes.c_double)]
+                ("beta_d", ctypes.c_double), ("conic", ctypes.c_int), ("delta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("dt_f", ctypes.c_double), ("wall_overlap", ctypes.c_int)]
 
 
 def lib():
@@ -56,6 +57,8 @@ def lib():
             P = ctypes.c_void_p
             i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
             L.orc_constants.argtypes = [f64, f64, f64, f64, i32, i32, P]
+            L.orc_ball_cut.argtypes = [f64, f64, f64, f64, P]
+            L.orc_ball_cut.restype = None
             L.orc_bond_row.argtypes = [i64, P, P, f64, i32, P, P, i64, P]
             L.orc_bond_row.restype = i64
             L.orc_bonds_brute.argtypes = [i64, P, P, f64, i32, P, P, P, P]
@@ -82,6 +85,14 @@ def lib():
 
 def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def ball_cut(R, a, b, c=None):
+    """Volume and first moments (V, Mx, My, Mz) of the part of the ball |r| < R
+    beyond the planes X = a, Y = b and Z = c (c = None: no Z plane)."""
+    out = np.zeros(4)
+    lib().orc_ball_cut(float(R), float(a), float(b), -float(R) if c is None else float(c), _p(out))
+    return out
 
 
 def constants(E, G0, delta, contact_factor=5.0, mode=0, micromodulus=0):
@@ -172,6 +183,9 @@ class Model:
         self.P.break_mode = m.break_mode
         self.P.beta_d = getattr(m, "beta_d", 0.0)
         self.P.conic = getattr(m, "micromodulus", 0)
+        self.P.mu = getattr(m, "mu", 0.0)
+        self.P.wall_overlap = getattr(m, "wall_overlap", 0)
+        self.P.dt_f = 0.0  # friction's time step: that of the latest step (0: Coulomb limit)
         self.P.delta = horizon
         self.P.contact = 1 if contact else 0
         self.P.nw = self.walls.shape[0]
@@ -222,11 +236,16 @@ class Model:
         return self
 
     def step(self, dt, nsteps=1):
+        if self.P.mu != 0.0 and self.P.dt_f != dt:
+            # the friction's stick branch depends on dt: a(t) is evaluated again with it
+            self.P.dt_f = dt
+            self.init()
         self.err |= lib().orc_step(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.acc),
                                    _p(self.broken), _p(self.wall_pos), dt, nsteps, _p(self.F),
                                    _p(self.react), _p(self.impulse))
         self.t += dt * nsteps
         self.impulse_span += dt * nsteps
+        self.P.dt_f = dt
         return self
 
     def stable_dt(self):

@@ -309,6 +309,166 @@ int64_t orc_bonds_cells(int64_t n, const double *x, const int32_t *grain, double
 }
 
 /* ------------------------------------------------------------------------- */
+/* Ball cut by orthogonal planes (Sec. 4.1.1, contact with several walls).   */
+/* ------------------------------------------------------------------------- */
+/*
+ * In an orthonormal frame (X, Y, Z) centred on the node, the region of the
+ * ball |r| < R that lies beyond the planes X = a, Y = b and Z = c is
+ *   W(a, b, c) = { r : |r| < R, X > a, Y > b, Z > c }.
+ * A wall whose outward axis is X and which lies at distance d from the node
+ * cuts off W(d, -R, -R), its spherical cap; two orthogonal walls share
+ * W(d1, d2, -R) and three mutually orthogonal walls W(d1, d2, d3).  The paper
+ * gives no formula for the shared regions; here their volume and first moments
+ * are the iterated integrals of the definition, evaluated by adaptive Simpson
+ * quadrature: over Z, then over Y, with the X extent of W at (Y, Z) in closed
+ * form.  Every integrand is continuous; the quadrature splits each interval at
+ * the points where the integrand's formula changes.
+ */
+typedef struct { double R, a, b, s2; int what; } orc_wctx; /* s2: R^2 - Z^2 at the current Z */
+
+/* X extent of W at (Y, Z): the chord {X > a, X^2 < w^2}, w^2 = s2 - Y^2;
+ * what = 0: its length; 1: its X moment; 2: Y times its length */
+static double orc_chord(const orc_wctx *q, double Y)
+{
+    double w2 = q->s2 - Y * Y;
+    if (!(w2 > 0.0)) return 0.0;
+    double w = sqrt(w2);
+    double lo = q->a > -w ? q->a : -w;
+    if (!(lo < w)) return 0.0;
+    if (q->what == 0) return w - lo;
+    if (q->what == 1) return 0.5 * (w * w - lo * lo);
+    return Y * (w - lo);
+}
+
+typedef double (*orc_fn)(const void *, double);
+
+static double orc_simpson_rec(orc_fn f, const void *ctx, double x0, double x1, double f0, double fm, double f1,
+                              double whole, double eps, int depth)
+{
+    double m = 0.5 * (x0 + x1), l = 0.5 * (x0 + m), r = 0.5 * (m + x1);
+    double fl = f(ctx, l), fr = f(ctx, r);
+    double left = (m - x0) / 6.0 * (f0 + 4.0 * fl + fm), right = (x1 - m) / 6.0 * (fm + 4.0 * fr + f1);
+    double both = left + right;
+    if (depth <= 0 || fabs(both - whole) <= 15.0 * eps) return both + (both - whole) / 15.0;
+    return orc_simpson_rec(f, ctx, x0, m, f0, fl, fm, left, 0.5 * eps, depth - 1) +
+           orc_simpson_rec(f, ctx, m, x1, fm, fr, f1, right, 0.5 * eps, depth - 1);
+}
+
+/* adaptive Simpson over [x0, x1] split at the sorted break points inside it */
+static double orc_integrate(orc_fn f, const void *ctx, double x0, double x1, const double *brk, int nb, double eps)
+{
+    double pts[8];
+    int np = 0;
+    pts[np++] = x0;
+    for (int k = 0; k < nb; ++k)
+        if (brk[k] > pts[np - 1] && brk[k] < x1) pts[np++] = brk[k];
+    pts[np++] = x1;
+    double sum = 0.0;
+    for (int k = 0; k + 1 < np; ++k) {
+        double u = pts[k], v = pts[k + 1];
+        if (!(v > u)) continue;
+        double fu = f(ctx, u), fv = f(ctx, v), fm = f(ctx, 0.5 * (u + v));
+        double whole = (v - u) / 6.0 * (fu + 4.0 * fm + fv);
+        sum += orc_simpson_rec(f, ctx, u, v, fu, fm, fv, whole, eps, 40);
+    }
+    return sum;
+}
+
+static double orc_inner(const void *c, double Y) { return orc_chord((const orc_wctx *)c, Y); }
+
+/* integral over Y > b of the chord quantity at the current Z */
+static double orc_slice(orc_wctx *q)
+{
+    if (!(q->s2 > 0.0)) return 0.0;
+    double s = sqrt(q->s2);
+    double y0 = q->b > -s ? q->b : -s;
+    if (!(y0 < s)) return 0.0;
+    double brk[2];
+    int nb = 0;
+    if (q->a * q->a < q->s2) { /* the chord's lower end switches from -w to a at w = |a| */
+        double yk = sqrt(q->s2 - q->a * q->a);
+        brk[nb++] = -yk;
+        brk[nb++] = yk;
+    }
+    return orc_integrate(orc_inner, q, y0, s, brk, nb, 1e-13 * q->R * q->R);
+}
+
+typedef struct { orc_wctx w; double c; int zmom; } orc_octx;
+
+static double orc_outer(const void *c, double Z)
+{
+    orc_octx *o = (orc_octx *)c;
+    orc_wctx q = o->w;
+    q.s2 = q.R * q.R - Z * Z;
+    double v = orc_slice(&q);
+    return o->zmom ? Z * v : v;
+}
+
+/* Without the Z plane (c <= -R) the slice of W at fixed Y is the disk of
+ * radius r = sqrt(R^2 - Y^2) in (X, Z) beyond the chord X = a: the textbook
+ * circular segment, area r^2 acos(a/r) - a sqrt(r^2 - a^2) and X moment
+ * (2/3)(r^2 - a^2)^(3/2) for |a| < r (empty for a >= r, the whole disk, area
+ * pi r^2 and X moment 0, for a <= -r).  what = 0: area; 1: X moment; 2: Y area. */
+static double orc_segment(const void *c, double Y)
+{
+    const orc_wctx *q = (const orc_wctx *)c;
+    double r2 = q->R * q->R - Y * Y;
+    if (!(r2 > 0.0)) return 0.0;
+    double r = sqrt(r2), a = q->a, area, mx;
+    if (a >= r) return 0.0;
+    if (a <= -r) { area = ORC_PI * r2; mx = 0.0; }
+    else {
+        double h = sqrt(r2 - a * a);
+        area = r2 * acos(a / r) - a * h;
+        mx = (2.0 / 3.0) * h * h * h;
+    }
+    if (q->what == 0) return area;
+    if (q->what == 1) return mx;
+    return Y * area;
+}
+
+/* volume and first moments (about the node, along X, Y, Z) of W(a, b, c) */
+void orc_ball_cut(double R, double a, double b, double c, double out[4])
+{
+    double z0 = c > -R ? c : -R;
+    for (int k = 0; k < 4; ++k) out[k] = 0.0;
+    if (!(z0 < R)) return;
+    if (c <= -R) {
+        double y0 = b > -R ? b : -R, brk[2];
+        int nb = 0;
+        if (a * a < R * R) { brk[0] = -sqrt(R * R - a * a); brk[1] = -brk[0]; nb = 2; }
+        for (int k = 0; k < 3; ++k) {
+            orc_wctx q;
+            q.R = R; q.a = a; q.b = b; q.s2 = 0.0; q.what = k;
+            out[k] = orc_integrate(orc_segment, &q, y0, R, brk, nb, 1e-15 * R * R * R);
+        }
+        return;
+    }
+    /* break points in Z where the slice changes form: R^2 - Z^2 = a^2, b^2, a^2 + b^2 */
+    double brk[6];
+    int nb = 0;
+    double t[3] = {a * a, b * b, a * a + b * b};
+    for (int k = 0; k < 3; ++k)
+        if (t[k] < R * R) {
+            double zk = sqrt(R * R - t[k]);
+            brk[nb++] = -zk;
+            brk[nb++] = zk;
+        }
+    /* insertion sort of the break points */
+    for (int i = 1; i < nb; ++i)
+        for (int j = i; j > 0 && brk[j - 1] > brk[j]; --j) { double s = brk[j]; brk[j] = brk[j - 1]; brk[j - 1] = s; }
+    double eps = 1e-12 * R * R * R;
+    for (int k = 0; k < 4; ++k) {
+        orc_octx o;
+        o.w.R = R; o.w.a = a; o.w.b = b; o.w.s2 = 0.0;
+        o.w.what = k == 1 ? 1 : (k == 2 ? 2 : 0);
+        o.c = c;
+        o.zmom = k == 3;
+        out[k] = orc_integrate(orc_outer, &o, z0, R, brk, nb, eps);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* The problem description shared by the force, step and energy routines.   */
 /* ------------------------------------------------------------------------- */
 typedef struct {
@@ -328,6 +488,9 @@ typedef struct {
     double beta_d;          /* normal damping coefficient (Sec. 3.3), N s / m^7; 0 = none */
     int conic;              /* 1: conic micromodulus c (delta - |xi|) */
     double delta;           /* horizon (used by the conic micromodulus) */
+    double mu;              /* friction coefficient (Sec. 3.3, stick-slip friction); 0 = none */
+    double dt_f;            /* time step the friction's stick branch sees; 0 = the Coulomb limit */
+    int wall_overlap;       /* 1: inclusion-exclusion over orthogonal walls (Sec. 4.1.1) */
 } orc_problem;
 
 /* micromodulus of a bond of reference length L: c, or c (delta - L) when conic */
@@ -399,6 +562,62 @@ int64_t orc_contact_pairs(const orc_problem *P, const double *u, const uint8_t *
     return total;
 }
 
+/* A shared-region term of step 5 of orc_forces: the walls idx[0..m-1] at
+ * distances dist[] cut W; the term's force density (sign applied) is added to
+ * f and its components along each wall's normal go to that wall's reaction. */
+static void orc_overlap_term(const orc_problem *P, int m, const int *idx, const double *dist, double sign, double vol,
+                             double *f, double *react)
+{
+    double cut[4];
+    orc_ball_cut(P->Rc, dist[0], dist[1], m == 3 ? dist[2] : -P->Rc, cut);
+    double V = cut[0];
+    if (!(V > 0.0)) return;
+    double cbar[3] = {cut[1] / V, cut[2] / V, m == 3 ? cut[3] / V : 0.0}; /* along -n of each wall */
+    double rb = sqrt(sq3(cbar[0], cbar[1], cbar[2]));
+    if (!(rb > 0.0)) return;
+    /* F = -K_n (R_c - rb) V (c - p) / rb with c - p = -sum_k cbar[k] n_k */
+    double g = sign * P->Kn * (P->Rc - rb) * V / rb;
+    for (int k = 0; k < m; ++k) {
+        const double *nk = P->walls + 9 * idx[k];
+        for (int a = 0; a < 3; ++a) {
+            double fa = g * cbar[k] * nk[a];
+            f[a] += fa;
+            react[3 * idx[k] + a] -= fa * vol;
+        }
+    }
+}
+
+/* step 5 of orc_forces for the node at p */
+static int orc_wall_overlap(const orc_problem *P, const double *p, const double *wall_pos, double vol, double *f,
+                            double *react)
+{
+    int touch[6], nt = 0;
+    double dist[6];
+    for (int l = 0; l < P->nw && l < 6; ++l) {
+        const double *nl = P->walls + 9 * l;
+        const double *wl = wall_pos + 3 * l;
+        double d = ((p[0] - wl[0]) * nl[0] + (p[1] - wl[1]) * nl[1]) + (p[2] - wl[2]) * nl[2];
+        if (d < P->Rc && d > -P->Rc) { touch[nt] = l; dist[nt] = d; ++nt; }
+    }
+    for (int s = 0; s < nt; ++s)
+        for (int t = s + 1; t < nt; ++t) {
+            const double *ns = P->walls + 9 * touch[s], *nu = P->walls + 9 * touch[t];
+            if (fabs(ns[0] * nu[0] + ns[1] * nu[1] + ns[2] * nu[2]) > 1e-9) continue;
+            int idx[2] = {touch[s], touch[t]};
+            double dd[2] = {dist[s], dist[t]};
+            orc_overlap_term(P, 2, idx, dd, -1.0, vol, f, react);
+            for (int r = t + 1; r < nt; ++r) {
+                const double *nr = P->walls + 9 * touch[r];
+                if (fabs(ns[0] * nr[0] + ns[1] * nr[1] + ns[2] * nr[2]) > 1e-9) continue;
+                if (fabs(nu[0] * nr[0] + nu[1] * nr[1] + nu[2] * nr[2]) > 1e-9) continue;
+                int id3[3] = {touch[s], touch[t], touch[r]};
+                double d3[3] = {dist[s], dist[t], dist[r]};
+                orc_overlap_term(P, 3, id3, d3, 1.0, vol, f, react);
+            }
+        }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Force density at displacement u (Eq. motion: F_int + F_ext without b).    */
 /* ------------------------------------------------------------------------- */
@@ -439,9 +658,39 @@ int64_t orc_contact_pairs(const orc_problem *P, const double *u, const uint8_t *
  *    Damping at the wall (Sec. 4.1: e -> e_l, V_y -> |S|, p_y -> c_l, the cap
  *    moving with the wall velocity v_w): F_i += beta_d ((v_w - v_i) . n_l) n_l |S|,
  *    which the wall's reaction includes.
- * v (nullable) is the velocity the damping sees; orc_step passes the half-step
- * velocity v(t + dt/2) of velocity Verlet (the velocity at hand when F(t + dt)
- * is evaluated).
+ * 4. Stick-slip friction (Sec. 3.3, Eq. regularized-friction), when v is given
+ *    and mu != 0.  For a contact pair with e = d / |d| and the relative velocity
+ *    of i with respect to j, v_r = v_i - v_j, the tangential part is
+ *    v_t = v_r - (v_r . e) e.  With f_r the magnitude of the pair's repulsion of
+ *    step 2 (per volume squared):
+ *      F_i += -min(rho |v_t| / (dt (V_i + V_j)), mu f_r) V_j v_t / |v_t|.
+ *    Readings: the law acts against the slip of i relative to j, as the text
+ *    says (the printed e_perp(y, x) would push along it).  The printed stick
+ *    branch (1/eps_f)|v_t| = rho |v_t| / dt is a force density, not a density
+ *    per volume squared like f_r; dividing it by V_i + V_j keeps the pair law
+ *    antisymmetric (momentum is conserved) and stops the relative tangential
+ *    motion of an isolated pair in exactly one step, the property the paper
+ *    gives for eps_f = dt / rho.  The stick and slip branches then meet where
+ *    |v_t| = v_thr, so the law is min() of the two.  dt = 0 is the Coulomb
+ *    limit (v_thr -> 0, slip whenever |v_t| > 0).
+ *    At a wall (Sec. 4.1 substitution, the wall rigid): v_r = v_i - v_w,
+ *    v_t = v_r - (v_r . n_l) n_l, f_r |S| = K_n (R_c - zbar) |S|, and the stick
+ *    branch is the force density that stops v_t in one step:
+ *      F_i += -min(rho |v_t| / dt, mu K_n (R_c - zbar) |S|) v_t / |v_t|,
+ *    which the wall's reaction includes.
+ * 5. Several walls (Sec. 4.1.1), when wall_overlap is set: for every pair of
+ *    walls with orthogonal normals that both touch the node, the shared region
+ *    W(d_l, d_m, -R_c) of orc_ball_cut (X along -n_l, Y along -n_m) of volume
+ *    |S_lm| and centroid c_lm - p_i = -(Mx n_l + My n_m) / |S_lm| contributes
+ *    -F_lm with F_lm = -K_n (R_c - |c_lm - p_i|) |S_lm| (c_lm - p_i) / |c_lm - p_i|,
+ *    and every triple of mutually orthogonal touching walls contributes +F_lmk
+ *    of W(d_l, d_m, d_k), the same form.  Readings: the paper states the
+ *    principle without the regions' volumes and centroids, which are computed
+ *    here; its triple term carries a stray factor V_x, dropped so that all
+ *    terms have the single-wall form; walls that are not orthogonal keep the
+ *    plain sum; damping and friction stay single-wall sums (the shared region
+ *    has no single wall velocity); the component of a shared-region term along
+ *    n_l is the part wall l's reaction takes.
  * With P->frozen set, step 1 keeps the given bond memory (Eq. peri-damage with
  * gamma prescribed) so that two evaluations can be compared on one bond set.
  * Returns error bits.  react (nw*3) receives the total force on each wall.
@@ -450,6 +699,7 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
                double *F, double *react)
 {
     const int damp = v != NULL && P->beta_d != 0.0;
+    const int fric = v != NULL && P->mu != 0.0;
     int64_t n = P->n;
     int err = 0;
     double *p = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -514,6 +764,22 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
                     for (int a = 0; a < 3; ++a) w += (v[3 * j + a] - v[3 * i + a]) * e[a];
                     for (int a = 0; a < 3; ++a) F[3 * i + a] += P->beta_d * w * e[a] * P->vol[j];
                 }
+                if (fric) {
+                    double e[3], vr[3], vt[3], vn = 0.0;
+                    for (int a = 0; a < 3; ++a) {
+                        e[a] = d[a] / dn;
+                        vr[a] = v[3 * i + a] - v[3 * j + a];
+                        vn += vr[a] * e[a];
+                    }
+                    for (int a = 0; a < 3; ++a) vt[a] = vr[a] - vn * e[a];
+                    double vtn = sqrt(sq3(vt[0], vt[1], vt[2]));
+                    if (vtn > 0.0) {
+                        double slip = P->mu * fabs(mag);
+                        double stick = P->dt_f > 0.0 ? P->rho * vtn / (P->dt_f * (P->vol[i] + P->vol[j])) : INFINITY;
+                        double f = stick < slip ? stick : slip;
+                        for (int a = 0; a < 3; ++a) F[3 * i + a] -= f * (vt[a] / vtn) * P->vol[j];
+                    }
+                }
             }
         }
         orc_grid_free(&g);
@@ -545,7 +811,26 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
                 F[3 * i + a] += mag * nl[a];
                 react[3 * l + a] -= mag * nl[a] * P->vol[i];
             }
+            if (fric) {
+                double vr[3], vt[3], vn = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    vr[a] = v[3 * i + a] - P->walls[9 * l + 6 + a];
+                    vn += vr[a] * nl[a];
+                }
+                for (int a = 0; a < 3; ++a) vt[a] = vr[a] - vn * nl[a];
+                double vtn = sqrt(sq3(vt[0], vt[1], vt[2]));
+                if (vtn > 0.0) {
+                    double slip = P->mu * P->Kn * (P->Rc - zbar) * Vcap;
+                    double stick = P->dt_f > 0.0 ? P->rho * vtn / P->dt_f : INFINITY;
+                    double f = stick < slip ? stick : slip;
+                    for (int a = 0; a < 3; ++a) {
+                        F[3 * i + a] -= f * vt[a] / vtn;
+                        react[3 * l + a] += f * vt[a] / vtn * P->vol[i];
+                    }
+                }
+            }
         }
+        if (P->wall_overlap) err |= orc_wall_overlap(P, p + 3 * i, wall_pos, P->vol[i], F + 3 * i, react);
         for (int a = 0; a < 3; ++a)
             if (!isfinite(F[3 * i + a])) err |= ORC_ERR_NONFINITE;
     }
@@ -577,8 +862,11 @@ int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *b
         for (int l = 0; l < P->nw; ++l)
             for (int a = 0; a < 3; ++a)
                 wall_pos[3 * l + a] = wall_pos[3 * l + a] + dt * P->walls[9 * l + 6 + a];
-        /* velocity-dependent forces see the half-step velocity v(t + dt/2) */
-        err |= orc_forces(P, u, v, wall_pos, broken, F, react);
+        /* velocity-dependent forces see the half-step velocity v(t + dt/2);
+         * the friction's stick branch sees this step's dt */
+        orc_problem Q = *P;
+        Q.dt_f = dt;
+        err |= orc_forces(&Q, u, v, wall_pos, broken, F, react);
         if (impulse)
             for (int l = 0; l < 3 * P->nw; ++l) impulse[l] += dt * react[l];
         for (int64_t i = 0; i < n; ++i)

@@ -51,7 +51,9 @@ struct pd_ctx {
     int64_t *cand_ptr = nullptr, *cand_cnt = nullptr;
     int2 *cand = nullptr;
     int64_t cand_cap = 0;
-    dbl4 *cand_fd = nullptr;  // pair damping force per candidate (float4 view on the mixed path)
+    dbl4 *cand_fd = nullptr;  // pair damping + friction force per candidate (float4 view on the mixed path)
+    double fric_dt = 0;       // time step the friction's stick branch sees (that of the latest pd_step)
+    double *gl = nullptr;     // Gauss-Legendre table of the multi-wall overlap terms
     uint32_t *gk = nullptr, *gk2 = nullptr, *gv = nullptr, *gv2 = nullptr, *gstart = nullptr, *gend = nullptr;
     uint64_t *gcell = nullptr;
     float4 *gpf = nullptr;  // FP32 positions of the grid's nodes (distance prefilter)
@@ -125,6 +127,31 @@ void pd_dev_free(pd_ctx *c, void *p)
 }
 
 namespace {
+
+// n-point Gauss-Legendre rule mapped to [0, 1]: the roots of the Legendre
+// polynomial P_n by Newton's method from the asymptotic first guesses
+// cos(pi (i + 3/4) / (n + 1/2)), P_n and P_n' from the three-term recurrence;
+// weight 2 / ((1 - z^2) P_n'(z)^2), halved for the unit interval.
+void gauss_legendre01(int n, double *x, double *w)
+{
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int j = 1; j <= n; ++j) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2 * j - 1) * z * p1 - (j - 1) * p2) / j;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double z1 = z;
+            z = z1 - p0 / dp;
+            if (fabs(z - z1) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
 
 pd_status fail(pd_ctx *c, pd_status s, const std::string &msg)
 {
@@ -248,6 +275,13 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.delta = c->delta;
     p.delta_f = (float)c->delta;
     p.cand_fd = c->cand_fd;
+    p.mu = c->mat.mu;
+    p.dt_f = mode == MODE_FORCES ? c->fric_dt : dt;
+    p.pair_diss = (c->mat.beta_d > 0 || c->mat.mu > 0) ? 1 : 0;
+    p.wall_overlap = c->mat.wall_overlap;
+    p.wall_extra = (c->walls.nw > 0 && (c->mat.mu > 0 || (c->mat.wall_overlap && c->walls.nw >= 2))) ? 1 : 0;
+    p.wall_n = c->wall_pos + 2 * PD_MAX_WALLS * 3;
+    p.gl = c->gl;
     p.mode = mode;
     p.walls = c->walls;
     p.wall_pos = c->wall_pos;
@@ -307,7 +341,7 @@ pd_status grow_candidates(pd_ctx *c)
     int64_t cap = std::max<int64_t>(2 * c->cand_cap, need + need / 2 + 1024);
     release(c, c->cand);
     ALLOC(c->cand, int2, cap);
-    if (c->mat.beta_d > 0) {
+    if (c->mat.beta_d > 0 || c->mat.mu > 0) {
         release(c, c->cand_fd);
         ALLOC(c->cand_fd, dbl4, cap);
     }
@@ -511,14 +545,20 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     CK(cudaMemsetAsync(c->cand_ptr, 0, sizeof(int64_t) * (n + 1), c->st));
     c->cand_cap = std::max<int64_t>(1024, 8 * n);
     ALLOC(c->cand, int2, c->cand_cap);
-    if (c->mat.beta_d > 0) ALLOC(c->cand_fd, dbl4, c->cand_cap);  // damping force per candidate
+    if (c->mat.beta_d > 0 || c->mat.mu > 0) ALLOC(c->cand_fd, dbl4, c->cand_cap);  // damping + friction per candidate
     // reductions
     c->blocks_cap = 0;
     for (int g : {4, 8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device, mixed, false, 0));
     ALLOC(c->partials, double, (int64_t)c->blocks_cap * PART_STRIDE);
     ALLOC(c->react, double, PD_MAX_WALLS * 3);
     ALLOC(c->disp, double, 1);
-    ALLOC(c->wall_pos, double, PD_MAX_WALLS * 6);  // wall points, then the wall impulses
+    ALLOC(c->wall_pos, double, PD_MAX_WALLS * 9);  // wall points, the wall impulses, the wall normals
+    if (c->mat.wall_overlap) {
+        double tab[2 * PD_GL];
+        gauss_legendre01(PD_GL, tab, tab + PD_GL);
+        ALLOC(c->gl, double, 2 * PD_GL);
+        CK(cudaMemcpyAsync(c->gl, tab, sizeof(tab), cudaMemcpyHostToDevice, c->st));
+    }
     ALLOC(c->dscratch, double, 8192);
     ALLOC(c->counter, unsigned, 1);
     ALLOC(c->vmax_bits, unsigned, 1);
@@ -553,7 +593,8 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (!(mat->E > 0) || !(mat->rho > 0) || !(mat->G0 > 0) || !(mat->contact_radius > 0) ||
         !(mat->contact_factor >= 0) || (mat->constants != 0 && mat->constants != 1) ||
         (mat->break_mode != 0 && mat->break_mode != 1) || !(mat->beta_d >= 0) || !isfinite(mat->beta_d) ||
-        (mat->micromodulus != 0 && mat->micromodulus != 1))
+        (mat->micromodulus != 0 && mat->micromodulus != 1) || !(mat->mu >= 0) || !isfinite(mat->mu) ||
+        (mat->wall_overlap != 0 && mat->wall_overlap != 1))
         return PD_EINVAL;
     pd_ctx *c = new pd_ctx();
     if (opt) c->opt = *opt; else pd_default_options(&c->opt);
@@ -682,11 +723,12 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
         scan_exclusive_i64(cnt, c->crow, n, c->tmp, c->st);
     }
     // shared-memory tiles (mixed path): the largest tile (64, 32 or 16 rows) whose
-    // staging fits two blocks per SM
+    // staging fits two blocks per SM.  A material with friction or multi-wall terms
+    // runs the global-gather kernels that carry the wall extras, so it has no tiles.
     release(c, c->tile_ptr); release(c, c->ulist); release(c, c->lcol); release(c, c->lrow);
     c->tiled = false;
     c->tile_cap = 0;
-    if (c->opt.precision == PD_MIXED && c->opt.tiles >= 0) {
+    if (c->opt.precision == PD_MIXED && c->opt.tiles >= 0 && !(c->mat.mu > 0) && !c->mat.wall_overlap) {
         const int64_t m = B + n;
         const size_t smem_max = 110 * 1024;
         std::vector<int64_t> rp(n + 1);
@@ -774,7 +816,7 @@ pd_status pd_set_walls(pd_ctx *c, int nw, const pd_wall *w)
 {
     if (!c) return PD_EINVAL;
     if (nw < 0 || nw > PD_MAX_WALLS || (nw > 0 && !w)) return fail(c, PD_EINVAL, "0 <= nw <= 6 walls");
-    double pos[PD_MAX_WALLS * 3] = {0};
+    double pos[PD_MAX_WALLS * 3] = {0}, nrm[PD_MAX_WALLS * 3] = {0};
     WallSet ws;
     memset(&ws, 0, sizeof(ws));
     ws.nw = nw;
@@ -790,10 +832,12 @@ pd_status pd_set_walls(pd_ctx *c, int nw, const pd_wall *w)
             ws.n[l][a] = w[l].normal[a];
             ws.v[l][a] = w[l].velocity[a];
             pos[3 * l + a] = w[l].point[a];
+            nrm[3 * l + a] = w[l].normal[a];
         }
     }
     CK(cudaSetDevice(c->opt.device));
     CK(cudaMemcpyAsync(c->wall_pos, pos, sizeof(pos), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(c->wall_pos + 2 * PD_MAX_WALLS * 3, nrm, sizeof(nrm), cudaMemcpyHostToDevice, c->st));
     CK(reset_impulse(c));
     pd_status s = sync(c);
     if (s) return s;
@@ -1061,6 +1105,14 @@ pd_status pd_step(pd_ctx *c, double dt, int64_t nsteps)
     if (!c->bonds_ready) return fail(c, PD_ESTATE, "pd_step before pd_build_bonds");
     if (c->latched) return fail(c, PD_ESTATE, "a device error is latched; call pd_set_state");
     if (!(dt > 0) || !isfinite(dt) || nsteps < 0) return fail(c, PD_EINVAL, "dt must be > 0 and nsteps >= 0");
+    if (c->mat.mu > 0 && c->fric_dt != dt) {
+        // the friction's stick branch depends on dt: the acceleration that enters
+        // the first half-kick is evaluated again with this dt
+        CK(cudaSetDevice(c->opt.device));
+        c->fric_dt = dt;
+        pd_status s = eval_forces(c);
+        if (s) return s;
+    }
     if (nsteps == 0) return PD_OK;
     CK(cudaSetDevice(c->opt.device));
     c->last_ms = 0;

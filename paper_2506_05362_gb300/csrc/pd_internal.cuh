@@ -88,7 +88,14 @@ struct StepParams {
     int conic;                     // conic micromodulus c (delta - |xi|)
     double delta;                  // horizon
     float delta_f;
-    void *cand_fd;                 // damping force per candidate: float4 (mixed) / dbl4 (FP64)
+    void *cand_fd;                 // damping + friction force per candidate: float4 (mixed) / dbl4 (FP64)
+    double mu;                     // stick-slip friction coefficient (0 = none)
+    double dt_f;                   // time step of the friction's stick branch (0 = the Coulomb limit)
+    int pair_diss;                 // pair damping or friction on: k_pair_damping fills cand_fd
+    int wall_overlap;              // inclusion-exclusion over orthogonal walls
+    int wall_extra;                // walls with friction or inclusion-exclusion: the WX kernels run
+    const double *wall_n;          // nw*3 wall normals (device copy, read by the overlap terms)
+    const double *gl;              // Gauss-Legendre nodes, then weights, on [0, 1] (PD_GL each)
     double *disp;                  // accumulated displacement bound since last rebuild
     double skin;
     int *stale;                    // set when 2*disp >= skin
@@ -104,6 +111,7 @@ struct StepParams {
 };
 
 #define PART_STRIDE 20  // 18 reaction components + max|v| + spare
+#define PD_GL 32        // Gauss-Legendre points of the multi-wall overlap integrals
 
 // Radix sort of (key, value) pairs, LSD 8-bit digits, stable.  bits = number of
 // low key bits to sort.  Buffers are ping-ponged; the result is in (*k, *v)

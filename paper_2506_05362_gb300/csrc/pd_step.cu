@@ -62,11 +62,162 @@ __device__ __forceinline__ double group_sum(double v)
 }
 
 // Wall cap force on a node at p (Sec. 4.1).  Returns error bits.
+// ---- Several walls (Sec. 4.1.1) ------------------------------------------------
+// In a frame whose axes point out through each wall, the part of the ball
+// |r| < R beyond the planes X_k = t_k is W(t).  A negative threshold is turned
+// into a positive one by the mirror image: {X > t} = ball - mirror{X > -t}, so
+// W(t) is a signed sum (inclusion-exclusion over the negative thresholds) of
+// the whole ball, caps, and corners whose thresholds are all >= 0.
+
+// volume and first moments of {X > a, Y > b, Z > c} within |r| < R, a, b, c >= 0:
+// the slice at height Z is the disk of radius s = sqrt(R^2 - Z^2) beyond the
+// corner (a, b); its area Q and moments Qx, Qy are elementary, and the Z
+// integral runs from c to Zm = sqrt(R^2 - a^2 - b^2) with Z = Zm - (Zm - c) u^2,
+// which removes the square-root end point, by Gauss-Legendre in u.
+__device__ __forceinline__ void corner_cut(const double *gl, double R, double a, double b, double c, double out[4])
+{
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    const double R2 = R * R;
+    if (a * a + b * b + c * c >= R2) return;
+    const double Zm = sqrt(R2 - a * a - b * b), L = Zm - c;
+#pragma unroll 1
+    for (int q = 0; q < PD_GL; ++q) {
+        const double u = gl[q], w = gl[PD_GL + q];
+        const double Z = Zm - L * u * u;
+        const double s2 = R2 - Z * Z;
+        const double X1 = sqrt(fmax(s2 - b * b, 0.0)), Y1 = sqrt(fmax(s2 - a * a, 0.0));
+        if (X1 <= a || Y1 <= b) continue;
+        const double s = sqrt(s2);
+        // Q = int_a^X1 (sqrt(s^2 - X^2) - b) dX, Qx = int X (...) dX, Qy by symmetry
+        const double Q = 0.5 * (X1 * b + s2 * asin(fmin(X1 / s, 1.0))) - 0.5 * (a * Y1 + s2 * asin(a / s)) -
+                         b * (X1 - a);
+        const double Qx = (Y1 * Y1 * Y1 - b * b * b) / 3.0 - 0.5 * b * (X1 * X1 - a * a);
+        const double Qy = (X1 * X1 * X1 - a * a * a) / 3.0 - 0.5 * a * (Y1 * Y1 - b * b);
+        const double jw = 2.0 * L * u * w;
+        out[0] += jw * Q;
+        out[1] += jw * Qx;
+        out[2] += jw * Qy;
+        out[3] += jw * Z * Q;
+    }
+}
+
+// W with thresholds t[k] >= 0 on the axes in `has` (bit k) and none on the others
+__device__ void cut_term(const double *gl, double R, const double t[3], int has, double out[4])
+{
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    const int m = __popc(has);
+    if (m == 0) {
+        out[0] = (4.0 * M_PI / 3.0) * R * R * R;
+    } else if (m == 1) {
+        const int k = __ffs(has) - 1;
+        const double a = t[k];
+        if (a >= R) return;
+        out[0] = (M_PI / 3.0) * (R - a) * (R - a) * (2.0 * R + a);
+        out[1 + k] = (M_PI / 4.0) * (R * R - a * a) * (R * R - a * a);
+    } else if (m == 2) {
+        const int k = __ffs(has) - 1, l = __ffs(has & ~(1 << k)) - 1;
+        double c2[4];
+        corner_cut(gl, R, t[k], t[l], 0.0, c2);  // half of the two-plane region (Z > 0)
+        out[0] = 2.0 * c2[0];
+        out[1 + k] = 2.0 * c2[1];
+        out[1 + l] = 2.0 * c2[2];
+    } else {
+        corner_cut(gl, R, t[0], t[1], t[2], out);
+    }
+}
+
+// W beyond the thresholds th[k] (any sign above -R) on the axes in `has`
+__device__ void ball_cut(const double *gl, double R, const double th[3], int has, double out[4])
+{
+    int neg = 0;
+    for (int k = 0; k < 3; ++k)
+        if (((has >> k) & 1) && th[k] < 0.0) neg |= 1 << k;
+    const double t[3] = {fabs(th[0]), fabs(th[1]), fabs(th[2])};
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+#pragma unroll 1
+    for (int S = neg;; S = (S - 1) & neg) {  // every subset S of the negative axes
+        double r[4];
+        cut_term(gl, R, t, (has & ~neg) | S, r);
+        const double sg = (__popc(S) & 1) ? -1.0 : 1.0;
+        out[0] += sg * r[0];
+        for (int k = 0; k < 3; ++k) out[1 + k] += sg * (((S >> k) & 1) ? -r[1 + k] : r[1 + k]);
+        if (S == 0) break;
+    }
+}
+
+// One shared-region term: the walls w[0..m-1] at distances d[] cut W; the
+// repulsion K_n (R_c - |cbar|) |W| along the centroid's direction, signed,
+// goes to f, and its component along each wall's normal to that wall.
+__device__ void overlap_term(const double *wall_n, const double *gl, double Rc, double Kn, int m, const int *w,
+                             const double *d, double sign, double vol, double *f, double *react)
+{
+    const double th[3] = {d[0], d[1], m == 3 ? d[2] : 0.0};
+    double cut[4];
+    ball_cut(gl, Rc, th, m == 3 ? 7 : 3, cut);
+    const double V = cut[0];
+    if (!(V > 0.0)) return;
+    const double cb[3] = {cut[1] / V, cut[2] / V, m == 3 ? cut[3] / V : 0.0};  // along -n of each wall
+    const double rb = sqrt((cb[0] * cb[0] + cb[1] * cb[1]) + cb[2] * cb[2]);
+    if (!(rb > 0.0)) return;
+    const double g = sign * Kn * (Rc - rb) * V / rb;
+    for (int k = 0; k < m; ++k) {
+        const double *nk = wall_n + 3 * w[k];
+        for (int a = 0; a < 3; ++a) {
+            const double fa = g * cb[k] * nk[a];
+            f[a] += fa;
+            react[3 * w[k] + a] -= fa * vol;
+        }
+    }
+}
+
+// Inclusion-exclusion over the walls the node touches (Sec. 4.1.1): minus the
+// region shared by every orthogonal pair, plus the region shared by every
+// mutually orthogonal triple.  Out of line: few nodes ever touch two walls.
+__device__ __forceinline__ double3 wall_overlap_terms(const double *wall_pos, const double *wall_n, const double *gl,
+                                                   int nw, double Rc, double Kn, double px, double py, double pz,
+                                                   double vol, double *react)
+{
+    int w[PD_MAX_WALLS];
+    double d[PD_MAX_WALLS];
+    int nt = 0;
+    for (int l = 0; l < nw; ++l) {
+        const double *n = wall_n + 3 * l, *q = wall_pos + 3 * l;
+        const double dl = dadd(dadd(dmul(px - q[0], n[0]), dmul(py - q[1], n[1])), dmul(pz - q[2], n[2]));
+        if (dl < Rc && dl > -Rc) { w[nt] = l; d[nt] = dl; ++nt; }
+    }
+    double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+    for (int s = 0; s < nt; ++s)
+#pragma unroll 1
+        for (int t = s + 1; t < nt; ++t) {
+            const double *ns = wall_n + 3 * w[s], *nu = wall_n + 3 * w[t];
+            if (fabs(ns[0] * nu[0] + ns[1] * nu[1] + ns[2] * nu[2]) > 1e-9) continue;
+            const int w2[2] = {w[s], w[t]};
+            const double d2[2] = {d[s], d[t]};
+            overlap_term(wall_n, gl, Rc, Kn, 2, w2, d2, -1.0, vol, f, react);
+#pragma unroll 1
+            for (int r = t + 1; r < nt; ++r) {
+                const double *nr = wall_n + 3 * w[r];
+                if (fabs(ns[0] * nr[0] + ns[1] * nr[1] + ns[2] * nr[2]) > 1e-9) continue;
+                if (fabs(nu[0] * nr[0] + nu[1] * nr[1] + nu[2] * nr[2]) > 1e-9) continue;
+                const int w3[3] = {w[s], w[t], w[r]};
+                const double d3[3] = {d[s], d[t], d[r]};
+                overlap_term(wall_n, gl, Rc, Kn, 3, w3, d3, 1.0, vol, f, react);
+            }
+        }
+    return make_double3(f[0], f[1], f[2]);
+}
+
+// Wall forces on one node (Sec. 4.1): the cap repulsion and its damping; with
+// WX (the kernels launched when friction or inclusion-exclusion is on) also the
+// wall friction and the multi-wall terms, which other kernels do not carry.
+template <bool WX>
 __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, double py, double pz,
                                                double vol, double vx, double vy, double vz, double &fx,
                                                double &fy, double &fz, double *react)
 {
     unsigned e = 0;
+    int touching = 0;
     for (int l = 0; l < p.walls.nw; ++l) {
         const double nx = p.walls.n[l][0], ny = p.walls.n[l][1], nz = p.walls.n[l][2];
         const double *w = p.wall_pos + 3 * l;
@@ -85,6 +236,27 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
         react[3 * l + 0] -= mag * nx * vol;
         react[3 * l + 1] -= mag * ny * vol;
         react[3 * l + 2] -= mag * nz * vol;
+        if (WX && p.mu > 0.0) {  // stick-slip friction against the sliding of the node along the wall
+            const double rx = vx - p.walls.v[l][0], ry = vy - p.walls.v[l][1], rz = vz - p.walls.v[l][2];
+            const double vn = (rx * nx + ry * ny) + rz * nz;
+            const double tx = rx - vn * nx, ty = ry - vn * ny, tz = rz - vn * nz;
+            const double vt = sqrt((tx * tx + ty * ty) + tz * tz);
+            if (vt > 0.0) {
+                const double slip = p.mu * p.Kn * (p.Rc - zbar) * vcap;
+                const double stick = p.dt_f > 0.0 ? p.rho * vt / p.dt_f : INFINITY;
+                const double fm = stick < slip ? stick : slip;
+                fx -= fm * tx / vt; fy -= fm * ty / vt; fz -= fm * tz / vt;
+                react[3 * l + 0] += fm * tx / vt * vol;
+                react[3 * l + 1] += fm * ty / vt * vol;
+                react[3 * l + 2] += fm * tz / vt * vol;
+            }
+        }
+        ++touching;
+    }
+    if (WX && p.wall_overlap && touching >= 2) {
+        const double3 o = wall_overlap_terms(p.wall_pos, p.wall_n, p.gl, p.walls.nw, p.Rc, p.Kn, px, py, pz, vol,
+                                             react);
+        fx += o.x; fy += o.y; fz += o.z;
     }
     return e;
 }
@@ -243,7 +415,7 @@ __device__ __forceinline__ unsigned epilogue_component(const StepParams &p, int6
 // c of the node's acceleration, velocity and displacement.  Every lane of the
 // warp calls it (inactive rows included) so that the shuffles that broadcast a
 // wall force and sum |v|^2 are uniform.
-template <int G>
+template <int G, bool WX>
 __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t row, bool active, int gl, float Fx,
                                                    float Fy, float Fz, const float4 &oxh, const float4 &uh,
                                                    const float4 &ul, const float4 &vh, const float4 &vl,
@@ -270,7 +442,7 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
                 const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
                              uz = df_to_double(df{uh.z, ul.z});
                 double fx = 0.0, fy = 0.0, fz = 0.0;
-                err |= wall_force(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, df_to_double(df{vh.x, vl.x}),
+                err |= wall_force<WX>(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, df_to_double(df{vh.x, vl.x}),
                                   df_to_double(df{vh.y, vl.y}), df_to_double(df{vh.z, vl.z}), fx, fy, fz, react);
                 wx = (float)fx; wy = (float)fy; wz = (float)fz;
             }
@@ -322,7 +494,7 @@ __device__ __forceinline__ bool contact_term(const StepParams &p, int64_t q, con
     }
     const double gm = mag * xj.w / dn;
     gx = gm * dx; gy = gm * dy; gz = gm * dz;
-    if (p.beta_d > 0.0) {  // damping of this pair, computed before the step by k_pair_damping
+    if (p.pair_diss) {  // damping and friction of this pair, computed before the step by k_pair_damping
         if (MIXED) {
             const float4 f = ((const float4 *)p.cand_fd)[q];
             gx += f.x; gy += f.y; gz += f.z;
@@ -347,11 +519,18 @@ __device__ __forceinline__ void load_v_t(const StepParams &p, int64_t i, double 
     }
 }
 
-// Normal damping of every contact candidate (Sec. 3.3), read as the dissipative
-// linear law beta_d ((v_j - v_i) . e) e V_j.  Runs before the step kernel, while
-// no kernel writes velocities, so that the step kernel (which updates v in
-// place) reads a consistent half-step velocity field; candidates that do not
-// touch get zero, and the step kernel adds the term only to pairs it accepts.
+// The velocity-dependent pair forces of every contact candidate, summed:
+// - normal damping (Sec. 3.3), read as the dissipative linear law
+//   beta_d ((v_j - v_i) . e) e V_j;
+// - stick-slip friction (Sec. 3.3, Eq. regularized-friction), read as
+//   -min(rho |v_t| / (dt (V_i + V_j)), mu f_r) V_j v_t / |v_t| with v_t the part
+//   of v_i - v_j across e and f_r the pair's repulsion per volume squared: the
+//   slip branch opposes the slip, and the stick branch, divided by V_i + V_j,
+//   is antisymmetric and stops an isolated pair's sliding in one step.
+// Runs before the step kernel, while no kernel writes velocities, so that the
+// step kernel (which updates v in place) reads a consistent half-step velocity
+// field; candidates that do not touch get zero, and the step kernel adds the
+// term only to pairs it accepts.
 template <bool MIXED>
 __global__ void k_pair_damping(const StepParams p)
 {
@@ -361,6 +540,7 @@ __global__ void k_pair_damping(const StepParams p)
         if (c1 <= c0) continue;
         const dbl4 ox = p.x4[i], ou = load_u_t<MIXED>(p, i);
         const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
+        const int gi = p.grain[i];
         double vix, viy, viz;
         load_v_t<MIXED>(p, i, vix, viy, viz);
         for (int64_t q = c0; q < c1; ++q) {
@@ -376,9 +556,36 @@ __global__ void k_pair_damping(const StepParams p)
                 const double ex = dx / dn, ey = dy / dn, ez = dz / dn;
                 double vjx, vjy, vjz;
                 load_v_t<MIXED>(p, j, vjx, vjy, vjz);
-                const double w = (vjx - vix) * ex + (vjy - viy) * ey + (vjz - viz) * ez;
-                const double g = p.beta_d * w * xj.w;
-                fx = g * ex; fy = g * ey; fz = g * ez;
+                if (p.beta_d > 0.0) {
+                    const double w = (vjx - vix) * ex + (vjy - viy) * ey + (vjz - viz) * ez;
+                    const double g = p.beta_d * w * xj.w;
+                    fx = g * ex; fy = g * ey; fz = g * ez;
+                }
+                if (p.mu > 0.0) {
+                    // the repulsion of the contact law (spring, or the PD-repulsive
+                    // law of a once-bonded same-grain pair)
+                    const double xx = xj.x - ox.x, xy = xj.y - ox.y, xz = xj.z - ox.z;
+                    const double L = sqrt(dadd(dadd(dmul(xx, xx), dmul(xy, xy)), dmul(xz, xz)));
+                    double fr;
+                    if (p.grain[j] != gi || L >= p.Rc) {
+                        fr = p.Kn * (p.Rc - dn);
+                    } else {
+                        const double sr = (dn - L) / L;
+                        fr = sr < 0.0 ? -(p.conic ? p.c * (p.delta - L) : p.c) * sr : 0.0;
+                    }
+                    const double rx = vix - vjx, ry = viy - vjy, rz = viz - vjz;
+                    const double vn = (rx * ex + ry * ey) + rz * ez;
+                    const double tx = rx - vn * ex, ty = ry - vn * ey, tz = rz - vn * ez;
+                    const double vt = sqrt((tx * tx + ty * ty) + tz * tz);
+                    if (vt > 0.0) {
+                        const double slip = p.mu * fr;
+                        const double stick = p.dt_f > 0.0 ? p.rho * vt / (p.dt_f * (ox.w + xj.w)) : INFINITY;
+                        const double fm = stick < slip ? stick : slip;
+                        fx -= fm * (tx / vt) * xj.w;
+                        fy -= fm * (ty / vt) * xj.w;
+                        fz -= fm * (tz / vt) * xj.w;
+                    }
+                }
             }
             if (MIXED)
                 ((float4 *)p.cand_fd)[q] = make_float4((float)fx, (float)fy, (float)fz, 0.f);
@@ -396,7 +603,7 @@ struct TileView {
 
 // Steps 1-4 for one row owned by a group of G lanes (all lanes call; inactive
 // groups pass active = false and still join the shuffles).
-template <int G, bool MIXED>
+template <int G, bool MIXED, bool WX = false>
 __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bool active, int gl, int lrow,
                                             const TileView &tv, double *react, unsigned &err, float &vmax2f,
                                             double &vmax2)
@@ -490,7 +697,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             oxh = __ldg(p.xh4 + REC * row); ouh = __ldg(p.uh_in + REC * row); oul = __ldg(p.ul_in + REC * row);
             ovh = p.vh[row]; ovl = p.vl[row];
         }
-        err |= epilogue_lanes<G>(p, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
+        err |= epilogue_lanes<G, WX>(p, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
     }
     if (!MIXED && active && gl == 0) {
         const double hdt = 0.5 * p.dt;
@@ -498,7 +705,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
         const dbl4 ox = p.x4[row], ou = p.u_in[row];
         const dbl4 ov = p.v[row];
         if (p.walls.nw)
-            err |= wall_force(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, ov.x, ov.y, ov.z, Fx, Fy,
+            err |= wall_force<WX>(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, ov.x, ov.y, ov.z, Fx, Fy,
                               Fz, react);
         if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
         dbl4 a;
@@ -597,7 +804,7 @@ __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_rea
 
 // Rows in a grid-stride loop, neighbour records gathered from global memory
 // (FP64 path, and the mixed path without tiles).
-template <int G, bool MIXED>
+template <int G, bool MIXED, bool WX>
 __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_step(const StepParams p)
 {
     constexpr int GPB = STEP_THREADS / G;
@@ -620,7 +827,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_st
     const TileView tv{nullptr, nullptr, nullptr, false};
     for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
         const int64_t row = r0 + grp;
-        process_row<G, MIXED>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
+        process_row<G, MIXED, WX>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
     }
     if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
     block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
@@ -741,7 +948,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             }
             fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            err |= epilogue_lanes<G>(p, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
+            err |= epilogue_lanes<G, false>(p, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
                                      active ? o2 : z4, active ? vhs[rr] : z4, active ? vls[rr] : z4, s_react[grp],
                                      vmax2f);
         }
@@ -844,13 +1051,18 @@ __global__ void k_fill_record_x(const float4 *__restrict__ xh4, int64_t n, float
 template <int G>
 void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 {
-    if (mixed && p.tile_cap > 0) {
+    if (p.wall_extra) {  // contexts with wall extras never take the tiled path
+        if (mixed)
+            k_step<G, true, true><<<blocks, STEP_THREADS, 0, st>>>(p);
+        else
+            k_step<G, false, true><<<blocks, STEP_THREADS, 0, st>>>(p);
+    } else if (mixed && p.tile_cap > 0) {
         const size_t smem = tiled_smem(p.tile_cap, p.tile_rows, p.tile_slot_cap);
         k_step_tiled<G><<<blocks, STEP_THREADS, smem, st>>>(p);
     } else if (mixed) {
-        k_step<G, true><<<blocks, STEP_THREADS, 0, st>>>(p);
+        k_step<G, true, false><<<blocks, STEP_THREADS, 0, st>>>(p);
     } else {
-        k_step<G, false><<<blocks, STEP_THREADS, 0, st>>>(p);
+        k_step<G, false, false><<<blocks, STEP_THREADS, 0, st>>>(p);
     }
 }
 
@@ -862,9 +1074,9 @@ int blocks_g(int sms, bool mixed, bool tiled, size_t smem)
         cudaFuncSetAttribute(k_step_tiled<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step_tiled<G>, STEP_THREADS, smem);
     } else if (mixed) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, true>, STEP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, true, false>, STEP_THREADS, 0);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, false>, STEP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_step<G, false, false>, STEP_THREADS, 0);
     }
     if (per < 1) per = 1;
     return sms * per;
@@ -897,7 +1109,7 @@ int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem)
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st)
 {
     const bool mixed = p.xh4 != nullptr;
-    if (p.beta_d > 0.0 && p.contact && p.cand_fd) {
+    if (p.pair_diss && p.contact && p.cand_fd) {
         const int db = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (p.n + 127) / 128));
         if (mixed)
             k_pair_damping<true><<<db, 128, 0, st>>>(p);

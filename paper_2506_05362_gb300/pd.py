@@ -38,7 +38,7 @@ class Material(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("rho", ctypes.c_double), ("G0", ctypes.c_double),
                 ("contact_radius", ctypes.c_double), ("contact_factor", ctypes.c_double),
                 ("constants", ctypes.c_int), ("break_mode", ctypes.c_int), ("beta_d", ctypes.c_double),
-                ("micromodulus", ctypes.c_int)]
+                ("micromodulus", ctypes.c_int), ("mu", ctypes.c_double), ("wall_overlap", ctypes.c_int)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -352,7 +352,8 @@ class Context:
         import torch
         m = material
         self.material = Material(m.E, m.rho, m.G0, m.contact_radius, m.contact_factor, m.constants,
-                                 m.break_mode, getattr(m, "beta_d", 0.0), getattr(m, "micromodulus", 0))
+                                 m.break_mode, getattr(m, "beta_d", 0.0), getattr(m, "micromodulus", 0),
+                                 getattr(m, "mu", 0.0), getattr(m, "wall_overlap", 0))
         o = pd_default_options()
         o.device = device
         if stream is None:  # a stream of its own: graphs cannot capture the legacy stream

@@ -43,6 +43,8 @@ class Material:
     break_mode: int = 0     # 0 = tension s > s0; 1 = |s| > s0
     beta_d: float = 0.0     # normal contact damping (Sec. 3.3), N s / m^7; 0 = none
     micromodulus: int = 0   # 0 = constant, 1 = conic c (delta - |xi|) (table of Sec. 3.1.1)
+    mu: float = 0.0         # stick-slip friction coefficient (Sec. 3.3); 0 = frictionless
+    wall_overlap: int = 0   # 1 = inclusion-exclusion over orthogonal walls (Sec. 4.1.1); 0 = sum
 
 
 @dataclass
