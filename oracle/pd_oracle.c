@@ -16,8 +16,10 @@
  *   Eq. (peri-damage)                                      -> breaking, damage
  *   Sec. 3.2, Eq. (repulsive-force)                        -> inter-grain contact
  *   Sec. 3.3, Eq. (damping-force)                          -> normal contact damping
+ *   Sec. 3.3, Eq. (regularized-friction)                   -> stick-slip friction
  *   Sec. 5 "Self-contact forces", Eq. (peri-damage-self)    -> same-grain contact
  *   Sec. 4.1 "Contact between peridynamic body and wall"    -> wall force
+ *   Sec. 4.1.1 "Contact with multiple wall boundaries"      -> inclusion-exclusion
  *   Sec. 3.5 Eq. (motion), Sec. 5.2 velocity-Verlet        -> time integration
  *   Sec. 5.3.1 / 5.3.2                                     -> bond removal filters
  *   Sec. 1 (split-off particles), no algorithm given        -> fragments
