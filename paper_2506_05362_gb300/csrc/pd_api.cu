@@ -62,7 +62,7 @@ struct pd_ctx {
 
     // reductions and device scalars
     double *partials = nullptr, *react = nullptr, *disp = nullptr, *wall_pos = nullptr, *dscratch = nullptr;
-    unsigned *counter = nullptr, *derr = nullptr, *vmax_bits = nullptr;
+    unsigned *counter = nullptr, *derr = nullptr, *vmax_bits = nullptr, *dflag = nullptr;
     int *stale = nullptr;
     int blocks = 0, lanes = 0, blocks_cap = 0;
     double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -564,13 +564,14 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->vmax_bits, unsigned, 1);
     CK(cudaMemsetAsync(c->vmax_bits, 0, sizeof(unsigned), c->st));
     ALLOC(c->derr, unsigned, 1);
+    ALLOC(c->dflag, unsigned, 1);
     ALLOC(c->stale, int, 1);
     CK(cudaMemsetAsync(c->react, 0, sizeof(double) * PD_MAX_WALLS * 3, c->st));
     CK(cudaMemsetAsync(c->disp, 0, sizeof(double), c->st));
     CK(cudaMemsetAsync(c->counter, 0, sizeof(unsigned), c->st));
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
     CK(cudaMemsetAsync(c->stale, 0, sizeof(int), c->st));
-    ALLOC(c->stage, double, 3 * n);
+    ALLOC(c->stage, double, 6 * n);  // staging of u and v (pd_set_state checks both before applying)
     ALLOC(c->snap_u, dbl4, n);
     ALLOC(c->snap_v, dbl4, n);
     ALLOC(c->snap_acc, dbl4, n);
@@ -1037,8 +1038,9 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
 static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out, int64_t *launches, double *ms_out,
                              double *force_ms_out)
 {
-    int k;
-    pd_status s = rebuild_period(c, dt, &k);
+    // a one-step segment rebuilds at its start whatever the period: no speed readback
+    int k = 1;
+    pd_status s = left == 1 ? PD_OK : rebuild_period(c, dt, &k);
     if (s) return s;
     // a rollback costs at most one segment of work
     int64_t m = std::min<int64_t>(left, (int64_t)PD_SEGMENT_CHUNKS * chunk_for(c, k));
@@ -1397,11 +1399,10 @@ pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double 
         to_caller(upos(c, c->cur), c->perm, c->n, c->stage, c->st);
         CK(cudaMemcpyAsync(u, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
     }
-    if (v) {
-        if (u) { pd_status s = sync(c); if (s) return s; }
+    if (v) {  // a second staging area: no wait for the copy of u
         if (mixed) materialize_df(c->vh, c->vl, 1, c->n, c->v, c->st);
-        to_caller(c->v, c->perm, c->n, c->stage, c->st);
-        CK(cudaMemcpyAsync(v, c->stage, nb, cudaMemcpyDeviceToHost, c->st));
+        to_caller(c->v, c->perm, c->n, c->stage + 3 * c->n, c->st);
+        CK(cudaMemcpyAsync(v, c->stage + 3 * c->n, nb, cudaMemcpyDeviceToHost, c->st));
     }
     if (broken) {
         if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
@@ -1419,27 +1420,36 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
     if (!c) return PD_EINVAL;
     CK(cudaSetDevice(c->opt.device));
     const size_t nb = sizeof(double) * 3 * c->n;
-    if (u) {
-        for (int64_t q = 0; q < 3 * c->n; ++q)
-            if (!isfinite(u[q])) return fail(c, PD_EINVAL, "u contains a non-finite value");
-        CK(cudaMemcpyAsync(c->stage, u, nb, cudaMemcpyHostToDevice, c->st));
-        if (c->opt.precision == PD_MIXED) {
-            from_caller(c->stage, c->perm, c->n, c->u[0], c->st);
-            split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], REC, c->st);
-        } else {
-            from_caller(c->stage, c->perm, c->n, c->u[c->cur], c->st);
+    if (u || v) {
+        // stage both, check both on the device, apply only if both are finite
+        double *su = c->stage, *sv = c->stage + 3 * c->n;
+        CK(cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
+        if (u) {
+            CK(cudaMemcpyAsync(su, u, nb, cudaMemcpyHostToDevice, c->st));
+            check_finite(su, 3 * c->n, 1u, c->dflag, c->st);
         }
+        if (v) {
+            CK(cudaMemcpyAsync(sv, v, nb, cudaMemcpyHostToDevice, c->st));
+            check_finite(sv, 3 * c->n, 2u, c->dflag, c->st);
+        }
+        unsigned bad = 0;
+        CK(cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
         pd_status s = sync(c);
         if (s) return s;
-    }
-    if (v) {
-        for (int64_t q = 0; q < 3 * c->n; ++q)
-            if (!isfinite(v[q])) return fail(c, PD_EINVAL, "v contains a non-finite value");
-        CK(cudaMemcpyAsync(c->stage, v, nb, cudaMemcpyHostToDevice, c->st));
-        from_caller(c->stage, c->perm, c->n, c->v, c->st);
-        if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
-        pd_status s = sync(c);
-        if (s) return s;
+        if (bad & 1u) return fail(c, PD_EINVAL, "u contains a non-finite value");
+        if (bad & 2u) return fail(c, PD_EINVAL, "v contains a non-finite value");
+        if (u) {
+            if (c->opt.precision == PD_MIXED) {
+                from_caller(su, c->perm, c->n, c->u[0], c->st);
+                split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], REC, c->st);
+            } else {
+                from_caller(su, c->perm, c->n, c->u[c->cur], c->st);
+            }
+        }
+        if (v) {
+            from_caller(sv, c->perm, c->n, c->v, c->st);
+            if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
+        }
     }
     if (broken) {
         if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");

@@ -459,6 +459,15 @@ __global__ void k_to_caller(const dbl4 *__restrict__ in, const int32_t *__restri
     }
 }
 
+// flag |= bit when any of a[0..m) is not finite (one atomic per warp that saw one)
+__global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bit, unsigned *flag)
+{
+    bool bad = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[k]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
+}
+
 __global__ void k_from_caller(const double *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, dbl4 *out)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -654,6 +663,11 @@ void bytes_to_bits(const uint8_t *in, const int32_t *kc_of, int64_t B, uint32_t 
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st)
 {
     k_to_caller<<<grid_of(n), 256, 0, st>>>(in, perm, n, out);
+}
+
+void check_finite(const double *a, int64_t m, unsigned bit, unsigned *flag, cudaStream_t st)
+{
+    k_nonfinite<<<grid_of(m), 256, 0, st>>>(a, m, bit, flag);
 }
 
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st)

@@ -47,6 +47,8 @@ void bits_to_bytes(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint8_t
 void bytes_to_bits(const uint8_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st);
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st);
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st);
+// *flag |= bit when any of the m doubles at a is not finite
+void check_finite(const double *a, int64_t m, unsigned bit, unsigned *flag, cudaStream_t st);
 void split_hilo(const dbl4 *u, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);
 int vmax_blocks(int64_t n);
 void vmax(const dbl4 *v, int64_t n, double *partial, cudaStream_t st);

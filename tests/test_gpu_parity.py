@@ -368,6 +368,14 @@ def test_error_paths(pd):
     with pytest.raises(pd.PDError) as e:
         ctx.set_state(u=np.full((sc.n, 3), np.nan))
     assert e.value.status == pd.PD_EINVAL
+    # one non-finite entry of v rejects the call, and the (finite) u is not applied either
+    before = ctx.get_state()[0]
+    v_bad = np.zeros((sc.n, 3))
+    v_bad[sc.n // 2, 1] = np.inf
+    with pytest.raises(pd.PDError) as e:
+        ctx.set_state(u=before + 1e-7, v=v_bad)
+    assert e.value.status == pd.PD_EINVAL
+    assert np.array_equal(ctx.get_state()[0], before)
     # a wall driven through the body within one step puts nodes a whole contact
     # radius behind it: the device flags it, the call restores the state of its
     # start and latches the error until pd_set_state
