@@ -119,22 +119,9 @@ def _areas(L):
     return np.array([L[1] * L[2]] * 2 + [L[0] * L[2]] * 2 + [L[0] * L[1]] * 2)
 
 
-def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.04,
-            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8,
-            p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 40000,
-            G0: float = None, zeta: float = 0.0) -> Run:
-    """One RVE run: an aggregate in a box of six rigid walls is first compressed
-    isotropically at strain rate ``rate`` until the mean wall stress reaches the
-    confining pressure ``p_confine`` (a connected contact network; the solid
-    fraction is capped at ``sf_max``), then strained along ``path`` at ``rate`` up
-    to ``strain_end`` on the dominant axis, recorded ``records`` times.  ``zeta`` > 0
-    turns on the normal contact damping at that fraction of critical.  Strain is
-    measured from the box at the end of the pre-compression; the recorded stress
-    is that of the wall forces averaged over each record interval.
-
-    The step kernel's configuration is fixed (``lanes`` per node, no tiles) so
-    that a run is reproducible: the autotuner's choice would change the order of
-    the force sums, and a granular packing amplifies rounding differences."""
+def _rve_setup(n_grains, seed, h, G0, zeta, rate, device, stream, lanes):
+    """Aggregate, box walls moving inward at ``rate`` (isotropic pre-compression)
+    and a context with a fixed kernel configuration."""
     from . import pd
     sc = S.aggregate(n_grains=n_grains, seed=seed, h=h, gap_cells=0.5)
     if G0 is not None:  # fracture energy of the grains (glass: 135 J/m^2)
@@ -142,7 +129,6 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
     if zeta > 0:  # normal contact damping (Sec. 3.3) at this ratio of critical for a node pair
         sc.material = dataclasses.replace(sc.material, beta_d=damping_coefficient(sc.material, sc.horizon,
                                                                                   float(sc.vol.mean()), zeta))
-    mult = np.array(LOADING_PATHS[path])
     walls = S.walls_array(sc.walls)
     lo, hi = _box(walls[:, 3:6])
     L0 = hi - lo
@@ -152,9 +138,13 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
         walls[2 * k + 1, 6 + k] = -0.5 * rate * L0[k]
     sc.walls = [S.Wall(tuple(w[0:3]), tuple(w[3:6]), tuple(w[6:9])) for w in walls]
     ctx = pd.Context.from_scenario(sc, device=device, stream=stream, lanes=lanes, tiles=-1)
-    dt = 0.8 * ctx.stable_dt()
+    return sc, walls, ctx
+
+
+def _precompress(ctx, sc, dt, p_confine, sf_max, max_precompress):
+    """Steps until the mean wall stress reaches p_confine or the solid fraction
+    sf_max; returns (steps, mean wall stress, solid fraction)."""
     vol_sum = sc.vol.sum()
-    t0 = time.perf_counter()
     chunk, pc_steps, p_mean, sf = 64, 0, 0.0, 0.0
     while pc_steps < max_precompress:
         ctx.step(dt, chunk)
@@ -166,9 +156,17 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
         sf = vol_sum / np.prod(L)
         if p_mean >= p_confine or sf >= sf_max:
             break
-    # loading path from the compacted box
+    return pc_steps, p_mean, sf
+
+
+def _load(ctx, sc, walls, path, dt, rate, strain_end, records, n_grains):
+    """Strains the compacted box along ``path`` (walls move from their current
+    points) and records strain, time-averaged stress and descriptors; returns
+    (strain, stress, desc, steps)."""
+    mult = np.array(LOADING_PATHS[path])
     lo, hi = _box(ctx.get_walls())
     Lp = hi - lo
+    walls = walls.copy()
     walls[:, 3:6] = ctx.get_walls()
     walls[:, 6:9] = 0.0
     for k in range(3):
@@ -181,6 +179,7 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
     stride = max(1, steps_total // records)
     req, sph, asp = grain_shape_stats(sc.x, sc.grain, sc.vol)
     static = [req.mean(), req.std(), sph.mean(), sph.std(), math.log(n_grains), asp.mean(), asp.std()]
+    vol_sum = sc.vol.sum()
     strain = np.zeros((records, 6))
     stress = np.zeros((records, 6))
     desc = np.zeros((records, N_DESC))
@@ -199,10 +198,65 @@ def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, st
         desc[r] = [vol_sum / np.prod(L), static[0], static[1], static[2], static[3], phi.mean(),
                    float((phi * nb0).sum()) / B, static[4], ncont / n_grains, static[5], static[6],
                    L.max() / L.min(), rate * abs(mult).max()]
+    return strain, stress, desc, stride * records
+
+
+def rve_run(path: str, n_grains: int = 8, seed: int = 0, rate: float = 2.0e3, strain_end: float = 0.04,
+            records: int = 64, h: float = 0.5e-3 / 6, device: int = 0, stream=None, lanes: int = 8,
+            p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 40000,
+            G0: float = None, zeta: float = 0.0) -> Run:
+    """One RVE run: an aggregate in a box of six rigid walls is first compressed
+    isotropically at strain rate ``rate`` until the mean wall stress reaches the
+    confining pressure ``p_confine`` (a connected contact network; the solid
+    fraction is capped at ``sf_max``), then strained along ``path`` at ``rate`` up
+    to ``strain_end`` on the dominant axis, recorded ``records`` times.  ``zeta`` > 0
+    turns on the normal contact damping at that fraction of critical.  Strain is
+    measured from the box at the end of the pre-compression; the recorded stress
+    is that of the wall forces averaged over each record interval.
+
+    The step kernel's configuration is fixed (``lanes`` per node, no tiles) so
+    that a run is reproducible: the autotuner's choice would change the order of
+    the force sums, and a granular packing amplifies rounding differences."""
+    sc, walls, ctx = _rve_setup(n_grains, seed, h, G0, zeta, rate, device, stream, lanes)
+    dt = 0.8 * ctx.stable_dt()
+    t0 = time.perf_counter()
+    pc_steps, p_mean, sf = _precompress(ctx, sc, dt, p_confine, sf_max, max_precompress)
+    strain, stress, desc, steps = _load(ctx, sc, walls, path, dt, rate, strain_end, records, n_grains)
     pd_seconds = time.perf_counter() - t0
     ctx.close()
-    return Run(path, n_grains, seed, strain, stress, desc, pd_seconds, pc_steps + stride * records, sc.n,
-               pc_steps, p_mean, sf)
+    return Run(path, n_grains, seed, strain, stress, desc, pd_seconds, pc_steps + steps, sc.n, pc_steps, p_mean, sf)
+
+
+def rve_aggregate(n_grains: int = 50, seed: int = 0, paths=None, rate: float = 2.0e3, strain_end: float = 0.04,
+                  records: int = 64, h: float = 0.5e-3 / 12, device: int = 0, stream=None, lanes: int = 8,
+                  p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 80000,
+                  G0: float = None, zeta: float = 0.0):
+    """The runs of one aggregate along several loading paths (all eight by
+    default): one pre-compression as in ``rve_run``, its end state (u, v, bond
+    memory, time, wall points) saved, and every path loaded from that state.  A
+    run's ``pd_seconds`` counts the pre-compression plus its own loading, the
+    cost of producing that run alone."""
+    paths = list(LOADING_PATHS) if paths is None else list(paths)
+    sc, walls, ctx = _rve_setup(n_grains, seed, h, G0, zeta, rate, device, stream, lanes)
+    dt = 0.8 * ctx.stable_dt()
+    t0 = time.perf_counter()
+    pc_steps, p_mean, sf = _precompress(ctx, sc, dt, p_confine, sf_max, max_precompress)
+    u, v, broken, t = ctx.get_state()
+    wall_pts = ctx.get_walls()
+    t_pc = time.perf_counter() - t0
+    runs = []
+    for path in paths:
+        t1 = time.perf_counter()
+        w = walls.copy()
+        w[:, 3:6] = wall_pts
+        w[:, 6:9] = 0.0
+        ctx.set_walls(w)
+        ctx.set_state(u=u, v=v, broken=broken, t=t)
+        strain, stress, desc, steps = _load(ctx, sc, walls, path, dt, rate, strain_end, records, n_grains)
+        runs.append(Run(path, n_grains, seed, strain, stress, desc, t_pc + time.perf_counter() - t1,
+                        pc_steps + steps, sc.n, pc_steps, p_mean, sf))
+    ctx.close()
+    return runs
 
 
 def windows(run: Run):
@@ -324,17 +378,23 @@ def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate:
     # early stopping on the second-last run of every path (not used for training)
     val = [runs[(pi + 1) * runs_per_path - 2] for pi in range(len(LOADING_PATHS))] if runs_per_path >= 4 else []
     fit = [r for r in train_runs if r not in val]
+    return _fit_and_judge(runs, fit, val, held, train_runs, t_data, epochs, seed, device, stream)
+
+
+def _fit_and_judge(runs, fit, val, held, known, t_data, epochs, seed, device, stream):
+    """Trains on ``fit`` (early stopping on ``val``), judges every ``held`` run by
+    its own PD result and the mean-history baseline of the ``known`` runs."""
     t0 = time.perf_counter()
     net, xs, ys, losses = train(fit, epochs=epochs, seed=seed, device=device, stream=stream, val_runs=val)
     t_train = time.perf_counter() - t0
     rows = []
     for r in held:
         err, t_net = judge(net, xs, ys, r, device=device)
-        rows.append({"path": r.path, "grains": r.n_grains, "nodes": r.nodes, "steps": r.steps,
-                     "err": err, "err_mean_history": baseline_error(train_runs, r),
+        rows.append({"path": r.path, "grains": r.n_grains, "seed": r.seed, "nodes": r.nodes, "steps": r.steps,
+                     "err": err, "err_mean_history": baseline_error(known, r),
                      "pd_seconds": r.pd_seconds, "net_seconds": t_net, "speedup": r.pd_seconds / max(t_net, 1e-9)})
     errs = np.array([q["err"] for q in rows])
-    train_err = [judge(net, xs, ys, r, device=device)[0] for r in train_runs[:16]]
+    train_err = [judge(net, xs, ys, r, device=device)[0] for r in fit[:16]]
     net.close()
     return {"runs": len(runs), "train_runs": len(fit), "validation_runs": len(val), "held_out": len(held),
             "train_err_median": float(np.median(train_err)),
@@ -344,6 +404,28 @@ def study(runs_per_path: int = 4, grain_counts=(8, 12), epochs: int = 300, rate:
             "err_median": float(np.median(errs)), "err_max": float(errs.max()),
             "frac_within_5pct": float((errs <= 0.05).mean()),
             "speedup_median": float(np.median([q["speedup"] for q in rows])), "held": rows}
+
+
+def study_aggregates(n_aggregates: int = 25, grain_counts=(50, 100), epochs: int = 400, rate: float = 2.0e3,
+                     records: int = 64, h: float = 0.5e-3 / 12, seed: int = 0, device: int = 0, zeta: float = 0.5,
+                     held: int = 3, val: int = 2, runs=None):
+    """Every aggregate loaded along all eight paths from one shared pre-compression
+    (``rve_aggregate``); grain counts cycle through ``grain_counts``.  The last
+    ``held`` aggregates are held out with all their paths (no held-out run shares
+    its packing with a training run), the ``val`` aggregates before them stop the
+    training early, the rest train."""
+    P = len(LOADING_PATHS)
+    t0 = time.perf_counter()
+    if runs is None:
+        runs = []
+        for a in range(n_aggregates):
+            runs += rve_aggregate(grain_counts[a % len(grain_counts)], seed=seed + a, rate=rate, records=records,
+                                  h=h, device=device, zeta=zeta)
+    assert len(runs) == n_aggregates * P and n_aggregates > held + val
+    t_data = time.perf_counter() - t0
+    n_fit = n_aggregates - held - val
+    fit, vr, hr = runs[:n_fit * P], runs[n_fit * P:(n_fit + val) * P], runs[(n_fit + val) * P:]
+    return _fit_and_judge(runs, fit, vr, hr, fit + vr, t_data, epochs, seed, device, None)
 
 
 if __name__ == "__main__":
@@ -359,8 +441,31 @@ if __name__ == "__main__":
     ap.add_argument("--out", default=None, help="also write the full report (per held-out run) to this file")
     ap.add_argument("--runs-file", default=None,
                     help="read the runs from this .npz if it exists, else generate them and write it")
+    ap.add_argument("--aggregates", type=int, default=0,
+                    help="> 0: this many aggregates, each loaded along all eight paths from one shared "
+                         "pre-compression; whole aggregates held out (--held) and used for early stopping (--val)")
+    ap.add_argument("--h", type=float, default=None, help="lattice spacing of the grains, m")
+    ap.add_argument("--held", type=int, default=3)
+    ap.add_argument("--val", type=int, default=2)
     a = ap.parse_args()
     import os
+    if a.aggregates > 0:
+        h = a.h if a.h is not None else 0.5e-3 / 12
+        P = len(LOADING_PATHS)
+        # a runs file is extended aggregate by aggregate, so a cut-off job resumes
+        runs = load_runs(a.runs_file) if a.runs_file and os.path.exists(a.runs_file) else []
+        for ag in range(len(runs) // P, a.aggregates):
+            runs += rve_aggregate(a.grains[ag % len(a.grains)], seed=a.seed + ag, records=a.records, h=h,
+                                  zeta=a.zeta)
+            if a.runs_file:
+                save_runs(a.runs_file, runs)
+        rep = study_aggregates(a.aggregates, grain_counts=tuple(a.grains), epochs=a.epochs, records=a.records, h=h,
+                               seed=a.seed, zeta=a.zeta, held=a.held, val=a.val, runs=runs[:a.aggregates * P])
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump(rep, f, indent=1)
+        print(json.dumps({k: v for k, v in rep.items() if k != "held"}))
+        raise SystemExit(0)
     runs = load_runs(a.runs_file) if a.runs_file and os.path.exists(a.runs_file) else None
     if runs is None and a.runs_file:
         runs = []

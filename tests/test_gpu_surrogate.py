@@ -27,6 +27,22 @@ def test_rve_runs_are_reproducible_and_compacted():
     assert a.strain[-1, 2] < -0.03                 # the loaded axis shortened
 
 
+def test_paths_branch_from_one_shared_precompression():
+    """Loading paths from one saved pre-compressed state: a path run again after
+    another path gives the same record bit for bit (no state leaks between
+    branches), and every branch starts from the same compacted box."""
+    from paper_2506_05362_gb300 import surrogate as SG
+    runs = SG.rve_aggregate(8, seed=5, paths=["uniaxial_z", "isotropic", "uniaxial_z"], records=24, h=0.5e-3 / 6,
+                            zeta=0.5, max_precompress=40000)
+    a, b, c = runs
+    assert np.array_equal(a.stress, c.stress) and np.array_equal(a.strain, c.strain)
+    assert np.array_equal(a.desc, c.desc)
+    assert a.precompress_steps == b.precompress_steps and a.p_confine == b.p_confine
+    assert not np.array_equal(a.stress, b.stress)
+    assert a.strain[-1, 2] < -0.03 and b.strain[-1, 0] < -0.03 and abs(a.strain[-1, 0]) < 1e-12
+    assert np.all(np.isfinite(b.stress)) and b.stress[:, :3].mean() < 0
+
+
 def test_surrogate_trains_and_is_judged_by_pd():
     from paper_2506_05362_gb300 import surrogate as SG
     runs = []
