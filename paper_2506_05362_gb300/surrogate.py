@@ -408,7 +408,7 @@ def _fit_and_judge(runs, fit, val, held, known, t_data, epochs, seed, device, st
 
 def study_aggregates(n_aggregates: int = 25, grain_counts=(50, 100), epochs: int = 400, rate: float = 2.0e3,
                      records: int = 64, h: float = 0.5e-3 / 12, seed: int = 0, device: int = 0, zeta: float = 0.5,
-                     held: int = 3, val: int = 2, runs=None):
+                     held: int = 3, val: int = 2, runs=None, p_confine: float = 2.0e6):
     """Every aggregate loaded along all eight paths from one shared pre-compression
     (``rve_aggregate``); grain counts cycle through ``grain_counts``.  The last
     ``held`` aggregates are held out with all their paths (no held-out run shares
@@ -420,7 +420,7 @@ def study_aggregates(n_aggregates: int = 25, grain_counts=(50, 100), epochs: int
         runs = []
         for a in range(n_aggregates):
             runs += rve_aggregate(grain_counts[a % len(grain_counts)], seed=seed + a, rate=rate, records=records,
-                                  h=h, device=device, zeta=zeta)
+                                  h=h, device=device, zeta=zeta, p_confine=p_confine)
     assert len(runs) == n_aggregates * P and n_aggregates > held + val
     t_data = time.perf_counter() - t0
     n_fit = n_aggregates - held - val
@@ -445,6 +445,8 @@ if __name__ == "__main__":
                     help="> 0: this many aggregates, each loaded along all eight paths from one shared "
                          "pre-compression; whole aggregates held out (--held) and used for early stopping (--val)")
     ap.add_argument("--h", type=float, default=None, help="lattice spacing of the grains, m")
+    ap.add_argument("--p-confine", type=float, default=2.0e6,
+                    help="confining pressure that ends the isotropic pre-compression, Pa")
     ap.add_argument("--held", type=int, default=3)
     ap.add_argument("--val", type=int, default=2)
     a = ap.parse_args()
@@ -456,11 +458,12 @@ if __name__ == "__main__":
         runs = load_runs(a.runs_file) if a.runs_file and os.path.exists(a.runs_file) else []
         for ag in range(len(runs) // P, a.aggregates):
             runs += rve_aggregate(a.grains[ag % len(a.grains)], seed=a.seed + ag, records=a.records, h=h,
-                                  zeta=a.zeta)
+                                  zeta=a.zeta, p_confine=a.p_confine)
             if a.runs_file:
                 save_runs(a.runs_file, runs)
         rep = study_aggregates(a.aggregates, grain_counts=tuple(a.grains), epochs=a.epochs, records=a.records, h=h,
-                               seed=a.seed, zeta=a.zeta, held=a.held, val=a.val, runs=runs[:a.aggregates * P])
+                               seed=a.seed, zeta=a.zeta, held=a.held, val=a.val, runs=runs[:a.aggregates * P],
+                               p_confine=a.p_confine)
         if a.out:
             with open(a.out, "w") as f:
                 json.dump(rep, f, indent=1)
