@@ -270,7 +270,10 @@ pd_status pd_forces(pd_ctx *ctx, double *F);
 pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, double *t);
 
 /* Sets the state (any input may be NULL to keep it), clears a latched device
- * error and re-evaluates the forces (which may break bonds). */
+ * error and re-evaluates the forces (which may break bonds).  u and v are
+ * checked on the device before anything is applied: a non-finite value in
+ * either returns PD_EINVAL and leaves the whole state unchanged.  The wall
+ * impulses of pd_bulk_stress_mean are zeroed. */
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
 
