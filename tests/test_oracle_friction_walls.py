@@ -279,3 +279,48 @@ def test_overlap_only_for_orthogonal_touching_walls():
                       walls=walls)
         f.append(m.forces()[0].copy())
     assert np.abs(f[0] - f[1]).max() < 1e-6 * np.abs(f[1]).max()
+
+
+def test_friction_dissipates_over_a_sliding_collision():
+    """Two unbreakable jittered blocks meet obliquely (normal approach plus a
+    tangential slip) and separate again.  Without friction the energy after the
+    contact equals the energy before (velocity Verlet, spring contact).  With
+    friction it drops by a clear amount, and the blocks leave with less slip than
+    without friction (rough contact alone changes the slip; friction opposes it).
+    Momentum is conserved in both runs."""
+    h = 1e-4
+    rng = np.random.default_rng(6)
+    a = rng.uniform(-0.02, 0.02, (4 * 4 * 3, 3)) * h + np.stack(np.meshgrid(
+        np.arange(4), np.arange(4), np.arange(3), indexing="ij"), -1).reshape(-1, 3) * h
+    b = a + np.array([0.0, 0.0, 2.0 * h + 0.65 * h])
+    x = np.concatenate([a, b])
+    grain = np.repeat(np.array([0, 1], np.int32), len(a))
+    vol = np.full(len(x), h ** 3)
+    v0 = np.zeros_like(x)
+    v0[grain == 1] = [5.0, 0.0, -5.0]
+    v0[grain == 0] = [-5.0, 0.0, 5.0]
+    out = {}
+    for mu in (0.0, 0.5):
+        m = model_for(x, S.Material(E=72e9, rho=2440.0, G0=1e30, contact_radius=0.6 * h, mu=mu), 3 * h,
+                      grain=grain, vol=vol, v0=v0.copy())
+        dt = 0.2 * m.stable_dt()
+        m.P.dt_f = dt
+        m.init()
+        e0 = m.energy()
+        p0 = (vol[:, None] * m.v).sum(0)
+        touched = 0
+        for _ in range(400):
+            m.step(dt, 1)
+            touched += len(m.contact_pairs()) > 0
+        assert touched > 50
+        assert len(m.contact_pairs()) == 0  # the blocks have separated again
+        p1 = (vol[:, None] * m.v).sum(0)
+        assert np.abs(p1 - p0).max() <= 1e-12 * np.abs(vol[:, None] * v0).sum()
+        slip = m.v[grain == 1, 0].mean() - m.v[grain == 0, 0].mean()
+        out[mu] = (e0, m.energy(), slip)
+    e0, e1, slip0 = out[0.0]
+    assert abs(e1 - e0) < 1e-3 * e0
+    e0f, e1f, slipf = out[0.5]
+    assert e0f == pytest.approx(e0, rel=1e-12)
+    assert e1f < 0.9 * e0f
+    assert 0.0 < slipf < 0.5 * slip0
