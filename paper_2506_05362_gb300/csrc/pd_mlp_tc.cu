@@ -168,6 +168,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// 16 accumulator columns of this thread's TMEM lane, issued without waiting:
+// the registers hold the values only after tmem_wait16 on them
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+
+// waits for this thread's TMEM loads; the registers pass through the wait, so
+// no use of the loaded values can be scheduled before it
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -238,6 +257,31 @@ __device__ __forceinline__ uint32_t sw128_offset(int m, int k)
 {
     const int atom = k >> 6, c = (k & 63) >> 3, r = m & 7, g = m >> 3;
     return (uint32_t)(atom * (TILE_M * 128) + g * 1024 + r * 128 + ((c ^ r) << 4) + ((k & 7) << 1));
+}
+
+// bias + GELU + BF16 of the 16 accumulator columns [c, c + 16) of row m, written
+// to the next layer's swizzled A tile: the arithmetic of the whole-chunk path,
+// element for element (c is a multiple of 16, so the bias loads are aligned)
+__device__ __forceinline__ void epi16(const float *bias, const uint32_t (&r)[16], int c, unsigned char *sA, int m)
+{
+    float bb[16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 t4 = __ldg((const float4 *)(bias + c) + i);
+        bb[4 * i] = t4.x; bb[4 * i + 1] = t4.y; bb[4 * i + 2] = t4.z; bb[4 * i + 3] = t4.w;
+    }
+#pragma unroll
+    for (int c8 = 0; c8 < 16; c8 += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const float2 zz = __fadd2_rn(make_float2(__uint_as_float(r[c8 + e]), __uint_as_float(r[c8 + e + 1])),
+                                         make_float2(bb[c8 + e], bb[c8 + e + 1]));
+            const float2 g2 = gelu2(zz);
+            pk[e / 2] = pack_bf16x2(g2.x, g2.y);
+        }
+        *(uint4 *)(sA + sw128_offset(m, c + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
 }
 
 }  // namespace tc
@@ -410,7 +454,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                     const int hw = ((Ly.N / 4 + 31) / 32) * 32;  // columns per part, whole 32-column loads
                     const int cend = min(Ly.N, (part + 1) * hw);
                     const uint32_t tacc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * MAX_N);
-                    for (int c0 = part * hw; c0 < cend; c0 += 32) {
+                    // inference on whole 32-column chunks: the TMEM load of the next
+                    // 16 columns is in flight while the current 16 go through GELU
+                    const bool piped = !last && (Ly.N % 32) == 0 && !P.Z[l];
+                    if (piped && part * hw < cend) {
+                        uint32_t ra[16], rb[16];
+                        __syncwarp();  // tcgen05.ld is warp-collective
+                        tmem_ld16_issue(tacc + (uint32_t)(part * hw), ra);
+                        tmem_wait16(ra);
+                        for (int c0 = part * hw; c0 < cend; c0 += 32) {  // bounds uniform in the warp
+                            __syncwarp();
+                            tmem_ld16_issue(tacc + (uint32_t)(c0 + 16), rb);
+                            epi16(Ly.bias, ra, c0, sA, m);
+                            tmem_wait16(rb);
+                            const bool more = c0 + 32 < cend;
+                            if (more) {
+                                __syncwarp();
+                                tmem_ld16_issue(tacc + (uint32_t)(c0 + 32), ra);
+                            }
+                            epi16(Ly.bias, rb, c0 + 16, sA, m);
+                            if (more) tmem_wait16(ra);
+                        }
+                    }
+                    for (int c0 = part * hw; c0 < cend && !piped; c0 += 32) {
                         float v[32];
                         __syncwarp();  // tcgen05.ld is warp-collective
                         tmem_ld32(tacc + (uint32_t)c0, v);
