@@ -284,27 +284,30 @@ def main():
         except Exception:
             pass
 
-    # ---- end to end through the C ABI with pinned host buffers: per step the state
-    # goes host -> device, one step runs, and the new state comes back
+    # ---- end to end through the C ABI with pinned host buffers: per step the whole
+    # state (u, v and the bond memory, packed one bit per bond) goes host -> device,
+    # one step runs, and the new state comes back
+    nwords = (B + 31) // 32
     u_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     v_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
-    b_h = torch.empty(max(B, 1), dtype=torch.uint8, pin_memory=True).numpy()
-    u0, v0, b0, t0 = ctx.get_state()
-    u_h[:] = u0; v_h[:] = v0; b_h[:B] = b0
+    b_h = torch.empty(max(nwords, 1), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+    u0, v0, b0, t0 = pd.pd_get_state_packed(ctx.h, n, B)
+    u_h[:] = u0; v_h[:] = v0; b_h[:nwords] = b0
     barrier()
     te = time.perf_counter()
     for _ in range(args.e2e_steps):
-        pd.pd_set_state(ctx.h, u_h, v_h, b_h[:B])
+        pd.pd_set_state_packed(ctx.h, u_h, v_h, b_h[:nwords])
         ctx.step(dt, 1)
-        pd.pd_get_state(ctx.h, n, B, u_h, v_h, b_h)
+        pd.pd_get_state_packed(ctx.h, n, B, u_h, v_h, b_h)
     barrier()
     e2e_s = time.perf_counter() - te
     e2e = None
     if args.e2e_steps > 0:
         e2e = {"value": ws * n * args.e2e_steps / e2e_s, "unit": "node-steps/s",
-               "h2d_bytes_per_step": 48 * n + B, "d2h_bytes_per_step": 48 * n + B,
+               "h2d_bytes_per_step": 48 * n + 4 * nwords, "d2h_bytes_per_step": 48 * n + 4 * nwords,
                "steps": args.e2e_steps,
-               "path": "pd_set_state + pd_step(dt,1) + pd_get_state, pinned host buffers"}
+               "path": "pd_set_state_packed + pd_step(dt,1) + pd_get_state_packed (u, v, bond memory at one "
+                       "bit per bond), pinned host buffers"}
 
     # ---- all-FP64 GPU path on the same workload (comparison the metric asks for)
     fp64 = None

@@ -277,6 +277,15 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
 
+/* pd_get_state and pd_set_state with the bond memory packed: broken_bits holds
+ * ceil(B/32) words, bit (c % 32) of word (c / 32) set when slot c of the
+ * pd_bonds order is broken (bits past B are 0 on output and ignored on input).
+ * The same state in an eighth of the bytes, for checkpoints and host round
+ * trips; otherwise identical (NULL keeps, errors, re-evaluation). */
+pd_status pd_get_state_packed(pd_ctx *ctx, double *u, double *v, uint32_t *broken_bits, double *t);
+pd_status pd_set_state_packed(pd_ctx *ctx, const double *u, const double *v, const uint32_t *broken_bits,
+                              const double *t);
+
 /* Autotuning record of the bond loop: lanes per node chosen, whether the
  * shared-memory tiles were chosen, and the measured time (ms) of one force
  * evaluation per candidate: ms[0..3] global gathers with 4, 8, 16, 32 lanes,

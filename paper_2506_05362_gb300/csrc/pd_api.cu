@@ -1389,7 +1389,7 @@ pd_status pd_forces(pd_ctx *c, double *F)
     return sync(c);
 }
 
-pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double *t)
+static pd_status get_state_impl(pd_ctx *c, double *u, double *v, uint8_t *broken, uint32_t *bits, double *t)
 {
     if (!c) return PD_EINVAL;
     CK(cudaSetDevice(c->opt.device));
@@ -1404,18 +1404,24 @@ pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double 
         to_caller(c->v, c->perm, c->n, c->stage + 3 * c->n, c->st);
         CK(cudaMemcpyAsync(v, c->stage + 3 * c->n, nb, cudaMemcpyDeviceToHost, c->st));
     }
-    if (broken) {
+    if (broken || bits) {
         if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
-        if (c->B) {
+        if (c->B && broken) {
             bits_to_bytes(c->brk, c->kc_of, c->B, c->stage_b, c->st);
             CK(cudaMemcpyAsync(broken, c->stage_b, c->B, cudaMemcpyDeviceToHost, c->st));
+        } else if (c->B) {  // packed: ceil(B/32) words staged in the byte buffer (B + 16 bytes)
+            uint32_t *sw = (uint32_t *)c->stage_b;
+            bits_to_packed(c->brk, c->kc_of, c->B, sw, c->st);
+            CK(cudaMemcpyAsync(bits, sw, sizeof(uint32_t) * (size_t)((c->B + 31) / 32), cudaMemcpyDeviceToHost,
+                               c->st));
         }
     }
     if (t) *t = c->t;
     return sync(c);
 }
 
-pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_t *broken, const double *t)
+static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, const uint8_t *broken,
+                                const uint32_t *bits, const double *t)
 {
     if (!c) return PD_EINVAL;
     CK(cudaSetDevice(c->opt.device));
@@ -1451,11 +1457,18 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
             if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
         }
     }
-    if (broken) {
+    if (broken || bits) {
         if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
         if (c->B) {
-            CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
-            bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
+            if (broken) {
+                CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
+                bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
+            } else {
+                uint32_t *sw = (uint32_t *)c->stage_b;
+                CK(cudaMemcpyAsync(sw, bits, sizeof(uint32_t) * (size_t)((c->B + 31) / 32), cudaMemcpyHostToDevice,
+                                   c->st));
+                packed_to_bits(sw, c->kc_of, c->B, c->brk, c->st);
+            }
             if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
             if (c->colf) sync_colf_flags(c->brk, c->col, c->B, c->colf, c->st);
         }
@@ -1468,6 +1481,27 @@ pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_
     if (s) return s;
     if (c->bonds_ready) return eval_forces(c);
     return PD_OK;
+}
+
+pd_status pd_get_state(pd_ctx *c, double *u, double *v, uint8_t *broken, double *t)
+{
+    return get_state_impl(c, u, v, broken, nullptr, t);
+}
+
+pd_status pd_set_state(pd_ctx *c, const double *u, const double *v, const uint8_t *broken, const double *t)
+{
+    return set_state_impl(c, u, v, broken, nullptr, t);
+}
+
+pd_status pd_get_state_packed(pd_ctx *c, double *u, double *v, uint32_t *broken_bits, double *t)
+{
+    return get_state_impl(c, u, v, nullptr, broken_bits, t);
+}
+
+pd_status pd_set_state_packed(pd_ctx *c, const double *u, const double *v, const uint32_t *broken_bits,
+                              const double *t)
+{
+    return set_state_impl(c, u, v, nullptr, broken_bits, t);
 }
 
 pd_status pd_tuning(pd_ctx *c, int *lanes, int *tiled, double ms[8])

@@ -377,6 +377,45 @@ __global__ void k_bytes_to_bits(const uint8_t *__restrict__ in, const int32_t *_
     }
 }
 
+// Canonical packed bits (bit c % 32 of word c / 32 for canonical slot c) from the
+// internal bitset: the words are cleared first, then every broken internal slot
+// ORs its canonical bit (breaks are sparse, so the atomics are few).
+__global__ void k_bits_to_packed(const uint32_t *__restrict__ brk, const int32_t *__restrict__ kc_of, int64_t B,
+                                 uint32_t *out)
+{
+    const int64_t nw = (B + 31) >> 5;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = brk[w];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int64_t k = (w << 5) + b;
+            if (k < B) {
+                const int32_t c = kc_of[k];
+                atomicOr(out + (c >> 5), 1u << (c & 31));
+            }
+        }
+    }
+}
+
+// the internal bitset from canonical packed bits
+__global__ void k_packed_to_bits(const uint32_t *__restrict__ in, const int32_t *__restrict__ kc_of, int64_t B,
+                                 uint32_t *brk)
+{
+    const int64_t nw = (B + 31) >> 5;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t k = (w << 5) + b;
+            if (k < B) {
+                const int32_t c = kc_of[k];
+                if ((in[c >> 5] >> (c & 31)) & 1u) word |= 1u << b;
+            }
+        }
+        brk[w] = word;
+    }
+}
+
 // ---- shared-memory tiles -----------------------------------------------------------
 // Tile t = rows [t*T, (t+1)*T).  Keys (t << sh | node) for every bond target and
 // for every row itself; sorted and de-duplicated they give the tile's node list.
@@ -658,6 +697,18 @@ void bits_to_bytes(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint8_t
 void bytes_to_bits(const uint8_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st)
 {
     k_bytes_to_bits<<<grid_of((B + 31) / 32), 256, 0, st>>>(in, kc_of, B, brk);
+}
+
+void bits_to_packed(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint32_t *out, cudaStream_t st)
+{
+    const int64_t nw = (B + 31) / 32;
+    cudaMemsetAsync(out, 0, sizeof(uint32_t) * (size_t)nw, st);
+    k_bits_to_packed<<<grid_of(nw), 256, 0, st>>>(brk, kc_of, B, out);
+}
+
+void packed_to_bits(const uint32_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st)
+{
+    k_packed_to_bits<<<grid_of((B + 31) / 32), 256, 0, st>>>(in, kc_of, B, brk);
 }
 
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st)

@@ -45,6 +45,9 @@ void col_caller(const int32_t *col, const int32_t *perm, const int32_t *kc_of, i
                 cudaStream_t st);
 void bits_to_bytes(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint8_t *out, cudaStream_t st);
 void bytes_to_bits(const uint8_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st);
+// the same in packed form: bit c % 32 of word c / 32 for canonical slot c (ceil(B/32) words)
+void bits_to_packed(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint32_t *out, cudaStream_t st);
+void packed_to_bits(const uint32_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st);
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st);
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st);
 // *flag |= bit when any of the m doubles at a is not finite

@@ -94,6 +94,8 @@ def lib():
                 "pd_contacts": (i32, [P, P, P]),
                 "pd_forces": (i32, [P, P]),
                 "pd_get_state": (i32, [P, P, P, P, P]),
+                "pd_get_state_packed": (i32, [P, P, P, P, P]),
+                "pd_set_state_packed": (i32, [P, P, P, P, P]),
                 "pd_set_state": (i32, [P, P, P, P, P]),
                 "pd_tuning": (i32, [P, P, P, P]),
                 "pd_last_step_stats": (i32, [P, P, P, P]),
@@ -306,6 +308,33 @@ def pd_set_state(h, u=None, v=None, broken=None, t=None):
     broken = None if broken is None else np.ascontiguousarray(broken, np.uint8)
     tt = None if t is None else ctypes.byref(ctypes.c_double(t))
     _check(lib().pd_set_state(h, _ptr(u), _ptr(v), _ptr(broken), tt), h)
+
+
+def pd_get_state_packed(h, n, B, u=None, v=None, bits=None):
+    """State with the bond memory as ceil(B/32) uint32 words (bit c % 32 of word c // 32)."""
+    u = np.zeros((n, 3)) if u is None else u
+    v = np.zeros((n, 3)) if v is None else v
+    bits = np.zeros(max((B + 31) // 32, 1), np.uint32) if bits is None else bits
+    t = ctypes.c_double()
+    _check(lib().pd_get_state_packed(h, _ptr(u), _ptr(v), _ptr(bits), ctypes.byref(t)), h)
+    return u, v, bits[:(B + 31) // 32], t.value
+
+
+def pd_set_state_packed(h, u=None, v=None, bits=None, t=None):
+    u = None if u is None else _f64(u, (-1, 3))
+    v = None if v is None else _f64(v, (-1, 3))
+    bits = None if bits is None else np.ascontiguousarray(bits, np.uint32)
+    tt = None if t is None else ctypes.byref(ctypes.c_double(t))
+    _check(lib().pd_set_state_packed(h, _ptr(u), _ptr(v), _ptr(bits), tt), h)
+
+
+def pack_broken(broken):
+    """uint8 flags per slot -> packed uint32 words (the layout of pd_get_state_packed)."""
+    b = np.asarray(broken, np.uint8).astype(bool)
+    words = np.zeros((len(b) + 31) // 32, np.uint32)
+    idx = np.nonzero(b)[0]
+    np.bitwise_or.at(words, idx // 32, (np.uint32(1) << (idx % 32).astype(np.uint32)))
+    return words
 
 
 def pd_tuning(h):

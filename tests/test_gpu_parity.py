@@ -332,6 +332,39 @@ def test_determinism_and_checkpoint(pd):
         assert ta == to
 
 
+def test_packed_state_equals_byte_state(pd):
+    """The packed bond memory (pd_get/set_state_packed) holds the same state as
+    the byte form: identical flags after breaking, and a context restored from
+    either form steps to the same bits."""
+    sc = S.small_block(nx=9, ny=7, nz=5, jitter=0.05)
+    ref = oracle.Model.from_scenario(sc)
+    u, _ = perturbed_state(sc, ref.rowptr, ref.col, seed=9, strain=1.2)
+    a = pd.Context.from_scenario(sc, lanes=8)
+    a.set_state(u=u)
+    ua, va, ba, ta = a.get_state()
+    assert 0 < ba.sum() < len(ba)
+    up, vp, bits, tp = pd.pd_get_state_packed(a.h, a.n, a.B)
+    assert np.array_equal(bits, pd.pack_broken(ba))
+    assert np.array_equal(up, ua) and np.array_equal(vp, va) and tp == ta
+    # restore a fresh context from each form, then step both
+    b = pd.Context.from_scenario(sc, lanes=8)
+    c = pd.Context.from_scenario(sc, lanes=8)
+    b.set_state(u=ua, v=va, broken=ba, t=ta)
+    pd.pd_set_state_packed(c.h, ua, va, bits, ta)
+    dt = 0.5 * a.stable_dt()
+    b.step(dt, 20)
+    c.step(dt, 20)
+    sb, sc_ = b.get_state(), c.get_state()
+    for x, y in zip(sb[:3], sc_[:3]):
+        assert np.array_equal(x, y)
+    # bits past B are ignored on input
+    if a.B % 32:
+        bits2 = bits.copy()
+        bits2[-1] |= np.uint32(0xffffffff) << np.uint32(a.B % 32)
+        pd.pd_set_state_packed(c.h, None, None, bits2)
+        assert np.array_equal(c.get_state()[2], ba)
+
+
 def test_damage_and_stable_dt_match(pd):
     sc = S.small_block(nx=9, ny=7, nz=5, jitter=0.05)
     ctx = pd.Context.from_scenario(sc, contact=False)

@@ -3,6 +3,9 @@ exports every entry point that include/pd.h declares.  No compute calls."""
 import ctypes
 import os
 import re
+import sys
+
+import numpy as np
 
 import pytest
 
@@ -26,6 +29,17 @@ def test_header_declares_the_boundary():
     for required in ["pd_create", "pd_build_bonds", "pd_step", "pd_damage", "pd_bulk_stress",
                      "pd_forces", "pd_get_state", "pd_set_state", "pd_mlp_forward", "pd_mlp_train_step"]:
         assert required in names
+
+
+def test_pack_broken_layout():
+    """Bit c % 32 of word c // 32 for slot c, as pd_get_state_packed writes it."""
+    sys.path.insert(0, ROOT)
+    from paper_2506_05362_gb300 import pd
+    b = np.zeros(70, np.uint8)
+    b[[0, 31, 32, 69]] = 1
+    w = pd.pack_broken(b)
+    assert w.dtype == np.uint32 and len(w) == 3
+    assert w.tolist() == [(1 << 0) | (1 << 31), 1 << 0, 1 << 5]
 
 
 def test_library_exports_every_declared_symbol(libpath):
