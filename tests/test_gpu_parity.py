@@ -357,12 +357,14 @@ def test_packed_state_equals_byte_state(pd):
     sb, sc_ = b.get_state(), c.get_state()
     for x, y in zip(sb[:3], sc_[:3]):
         assert np.array_equal(x, y)
-    # bits past B are ignored on input
-    if a.B % 32:
-        bits2 = bits.copy()
-        bits2[-1] |= np.uint32(0xffffffff) << np.uint32(a.B % 32)
-        pd.pd_set_state_packed(c.h, None, None, bits2)
-        assert np.array_equal(c.get_state()[2], ba)
+    # bits past B are ignored on input (a fresh context restored at the first state,
+    # where re-evaluating the forces breaks nothing new)
+    assert a.B % 32
+    bits2 = bits.copy()
+    bits2[-1] |= np.uint32(0xffffffff) << np.uint32(a.B % 32)
+    d = pd.Context.from_scenario(sc, lanes=8)
+    pd.pd_set_state_packed(d.h, ua, va, bits2, ta)
+    assert np.array_equal(d.get_state()[2], ba)
 
 
 def test_damage_and_stable_dt_match(pd):
