@@ -63,3 +63,28 @@ def test_oracle_and_library_share_no_code():
     for f in ["pd_oracle.c", "__init__.py", "mlp.py"]:
         txt = open(os.path.join(ROOT, "oracle", f)).read()
         assert "paper_2506_05362_gb300" not in txt and "libpd" not in txt
+
+
+def test_binding_fails_loudly_without_the_library():
+    """No CPU fallback: with the library missing, the binding raises at its first
+    call instead of computing anything another way."""
+    import subprocess
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2506_05362_gb300 import pd\n"
+            "try:\n"
+            "    pd.lib()\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', 'not built' in str(e))\n" % ROOT)
+    env = dict(os.environ, PD_LIB=os.path.join(ROOT, "no_such_dir", "libpd.so"))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-1000:]
+    assert r.stdout.strip() == "raised: True"
+
+
+def test_product_package_never_imports_the_oracle():
+    """The package (binding, scenarios, surrogate) has no path into oracle/."""
+    pkg = os.path.join(ROOT, "paper_2506_05362_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            txt = open(os.path.join(pkg, f)).read()
+            assert "import oracle" not in txt and "from oracle" not in txt, f
