@@ -601,3 +601,85 @@ def test_conic_bond_force_by_hand():
     K, c, s0, _ = oracle.constants(mat.E, mat.G0, delta, micromodulus=1)
     assert F[0, 0] == pytest.approx(c * (delta - L) * s * V, rel=1e-12)
     assert F[1, 0] == pytest.approx(-F[0, 0], rel=1e-15)
+
+
+# --------------------------------------------------------------------------- self-contact (PD-repulsive branch)
+def _self_contact_pair(micromodulus, L=0.4e-4, h=1e-4, V1=2e-12):
+    """Two nodes of one grain closer than the contact radius (R_c = 0.6 h), bonded
+    (horizon 3 h), unequal volumes."""
+    mat = S.Material(E=72e9, rho=2440, G0=135, contact_radius=0.6 * h, micromodulus=micromodulus)
+    x = np.array([[0.0, 0, 0], [L, 0, 0]])
+    m = model_for(x, mat, 3 * h, vol=np.array([1e-12, V1]))
+    assert len(m.col) == 2
+    return m, mat
+
+
+@pytest.mark.parametrize("micromodulus", [0, 1])
+@pytest.mark.parametrize("dfrac", [0.3, 0.75, 1.3])
+def test_self_contact_repulsive_branch_by_hand(micromodulus, dfrac):
+    """Self-contact (Sec. 5, same-grain law): a once-bonded pair of one grain with
+    |xi| < R_c whose bond is broken repels only in compression, with the PD law
+    c(|xi|) (|d| - |xi|)/|xi| e V_j -- not the inter-grain spring K_n (R_c - |d|).
+    Hand values: |xi| = 0.4 h, |d| = dfrac |xi| along x; in tension (|d| > |xi|, still
+    inside R_c = 0.6 h) the pair exerts nothing.  Unequal volumes: F_i V_i = -F_j V_j."""
+    L = 0.4e-4
+    m, mat = _self_contact_pair(micromodulus, L=L)
+    delta = 3e-4
+    K, c, s0, Kn = oracle.constants(mat.E, mat.G0, delta, micromodulus=micromodulus)
+    cw = c * (delta - L) if micromodulus else c
+    m.broken[:] = 1
+    d = dfrac * L
+    m.u = np.array([[0.0, 0, 0], [d - L, 0, 0]])
+    F = m.forces(frozen=True)
+    expect0 = cw * min(0.0, (d - L) / L) * m.vol[1]  # along +x (e points from node 0 to node 1)
+    if dfrac < 1:
+        assert expect0 < 0  # node 0 is pushed away from node 1
+        assert F[0, 0] == pytest.approx(expect0, rel=1e-12)
+        # a spring of the inter-grain law would give -K_n (R_c - |d|) V_j: a different value
+        assert abs(-Kn * (mat.contact_radius - d) * m.vol[1] - expect0) > 1e-3 * abs(expect0)
+    else:
+        assert F[0, 0] == 0.0
+    assert np.all(F[:, 1:] == 0.0)
+    assert F[0, 0] * m.vol[0] == pytest.approx(-F[1, 0] * m.vol[1], rel=1e-14, abs=0)
+
+
+@pytest.mark.parametrize("micromodulus", [0, 1])
+def test_self_contact_equals_the_intact_bond_in_compression(micromodulus):
+    """The self-contact law is the bond law restricted to repulsion: a compressed
+    once-bonded pair feels the same force whether its bond is intact or broken,
+    and a stretched one only while the bond is intact.  Off the bond axis too."""
+    L = 0.4e-4
+    m, _ = _self_contact_pair(micromodulus, L=L)
+    rng = np.random.default_rng(5)
+    for trial in range(6):
+        direction = rng.normal(size=3)
+        direction /= np.linalg.norm(direction)
+        compress = trial % 2 == 0
+        d = (0.6 if compress else 1.2) * L
+        m.u = np.vstack([np.zeros(3), d * direction - np.array([L, 0, 0])])
+        m.broken[:] = 0
+        Fb = m.forces(frozen=True).copy()
+        m.broken[:] = 1
+        Fc = m.forces(frozen=True).copy()
+        if compress:
+            assert np.allclose(Fc, Fb, rtol=1e-12, atol=0)
+            assert np.dot(Fc[0], direction) < 0
+        else:
+            assert np.all(Fc == 0.0)
+            assert np.dot(Fb[0], direction) > 0  # the intact bond pulls
+
+
+def test_self_contact_spring_branch_beyond_contact_radius():
+    """Same grain with |xi| >= R_c (never closer than R_c in the reference): once
+    unbonded and pushed inside R_c the pair takes the spring -K_n (R_c - |d|) V_j."""
+    h = 1e-4
+    mat = S.Material(E=72e9, rho=2440, G0=135, contact_radius=0.6 * h)
+    L = 0.9 * h
+    m = model_for(np.array([[0.0, 0, 0], [L, 0, 0]]), mat, 3 * h, vol=np.full(2, 1e-12))
+    K, c, s0, Kn = oracle.constants(mat.E, mat.G0, 3 * h)
+    m.broken[:] = 1
+    d = 0.5 * h
+    m.u = np.array([[0.0, 0, 0], [d - L, 0, 0]])
+    F = m.forces(frozen=True)
+    assert F[0, 0] == pytest.approx(-Kn * (mat.contact_radius - d) * 1e-12, rel=1e-12)
+    assert F[1, 0] == pytest.approx(-F[0, 0], rel=1e-15)
