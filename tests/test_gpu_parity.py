@@ -84,7 +84,8 @@ def test_bond_lists_full_size(pd, name):
 # --------------------------------------------------------------------------- forces
 def perturbed_state(sc, rp, col, seed, strain=0.9, noise=0.5):
     """Affine stretch of about `strain` s0 plus noise, so that some bonds break."""
-    K, c, s0, Kn = oracle.constants(sc.material.E, sc.material.G0, sc.horizon, sc.material.contact_factor)
+    m = sc.material
+    K, c, s0, Kn = oracle.constants(m.E, m.G0, sc.horizon, m.contact_factor, m.constants, m.micromodulus)
     rng = np.random.default_rng(seed)
     A = np.diag([strain * s0, -0.3 * strain * s0, 0.5 * strain * s0]) + rng.normal(0, 0.2 * s0, (3, 3))
     u = (sc.x - sc.x.mean(0)) @ A.T + rng.normal(0, noise * s0 * sc.h, sc.x.shape)
@@ -110,6 +111,44 @@ def test_forces_same_state(pd, name, precision, tol, tiles, lanes):
     assert ref.broken.sum() > 0, "test state should break some bonds"
     assert np.all(np.abs(s[diff] - s0) < BAND * s0), "broken sets differ outside the tolerance band"
     # evaluate the oracle with the GPU's decisions on band bonds, then compare F
+    ref.broken[:] = broken
+    Fo = ref.forces(frozen=True).copy()
+    assert rel_l2(F, Fo) <= tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", MIXED_FORCE_TOL), ("fp64", FP64_FORCE_TOL)])
+@pytest.mark.parametrize("name", ["sphere", "kalthoff_small"])
+@pytest.mark.parametrize("break_mode,constants", [(1, 0), (0, 1), (1, 1)])
+def test_forces_breaking_modes(pd, name, precision, tol, break_mode, constants):
+    """The |s| > s0 criterion (break_mode 1, the sentence before the table of
+    Sec. 3.1.1) and the table's printed constants (constants 1): forces and broken
+    sets at a perturbed state.  Under break_mode 1 the state is compressive, so
+    that bonds break in compression, which the default criterion never does."""
+    sc = SCENARIOS[name]()
+    sc.material.break_mode = break_mode
+    sc.material.constants = constants
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=8)
+    ref = oracle.Model.from_scenario(sc)
+    assert ctx.stable_dt() == pytest.approx(ref.stable_dt(), rel=1e-12)
+    u, s0 = perturbed_state(sc, ref.rowptr, ref.col, seed=5, strain=1.1)
+    assert s0 == pytest.approx(ref.s0, rel=1e-15)
+    if break_mode:
+        u = -u
+    ctx.set_state(u=u)
+    F = ctx.forces()
+    _, _, broken, _ = ctx.get_state()
+    ref.u = u.copy()
+    ref.forces()
+    s = stretches(sc.x, u, ref.rowptr, ref.col)
+    b = ref.broken.astype(bool)
+    assert b.sum() > 0
+    if break_mode:
+        assert (b & (s < -s0)).sum() > 0, "no bond broke in compression"
+    else:
+        assert np.all(s[b] > s0 * (1 - BAND))
+    diff = broken.astype(bool) != b
+    assert np.all(np.abs(np.abs(s[diff]) - s0) < BAND * s0)
     ref.broken[:] = broken
     Fo = ref.forces(frozen=True).copy()
     assert rel_l2(F, Fo) <= tol
@@ -144,9 +183,13 @@ def test_forces_full_size_sampled(pd):
 # forces in different orders; near equilibrium the net force is a small residual
 # of terms ~1e4-1e5 times larger, and 200 steps accumulate it: ~1e-10 observed.
 @pytest.mark.parametrize("precision,tol,tiles", [("mixed", 1e-5, 1), ("mixed", 1e-5, -1), ("fp64", 1e-9, 0)])
-def test_sphere_trajectory_200_steps(pd, precision, tol, tiles):
-    """Glass sphere between plates, 200 steps at 0.8 dt_crit: u, v, wall force."""
+@pytest.mark.parametrize("break_mode,constants", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_sphere_trajectory_200_steps(pd, precision, tol, tiles, break_mode, constants):
+    """Glass sphere between plates, 200 steps at 0.8 dt_crit: u, v, wall force;
+    under both breaking criteria and both sets of constants (Sec. 3.1.1)."""
     sc = S.sphere()
+    sc.material.break_mode = break_mode
+    sc.material.constants = constants
     ctx = pd.Context.from_scenario(sc, precision=precision, tiles=tiles)
     ref = oracle.Model.from_scenario(sc)
     dtc = ref.stable_dt()
@@ -177,12 +220,16 @@ def test_sphere_trajectory_200_steps(pd, precision, tol, tiles):
     ctx.close()
 
 
-def test_breaking_trajectory_block(pd):
-    """A block torn apart by opposing initial velocities: damage appears, and the
-    step-by-step comparison from a shared state holds through the damage."""
+@pytest.mark.parametrize("break_mode,sign", [(0, 1.0), (1, -1.0)])
+def test_breaking_trajectory_block(pd, break_mode, sign):
+    """A block torn apart (sign +1) or crushed (sign -1, with the |s| > s0
+    criterion, so that bonds break in compression) by opposing initial velocities:
+    damage appears, and the step-by-step comparison from a shared state holds
+    through the damage."""
     sc = S.small_block(nx=10, ny=6, nz=5, jitter=0.05)
+    sc.material.break_mode = break_mode
     sc.v0 = np.zeros_like(sc.x)
-    sc.v0[:, 0] = np.where(sc.x[:, 0] > sc.x[:, 0].mean(), 40.0, -40.0)
+    sc.v0[:, 0] = sign * np.where(sc.x[:, 0] > sc.x[:, 0].mean(), 40.0, -40.0)
     ctx = pd.Context.from_scenario(sc, lanes=16)
     ref = oracle.Model.from_scenario(sc)
     dt = 0.5 * ref.stable_dt()
@@ -195,7 +242,7 @@ def test_breaking_trajectory_block(pd):
         # resynchronise the oracle on the GPU's band decisions (chaos after damage)
         s = stretches(sc.x, u, ref.rowptr, ref.col)
         diff = broken.astype(bool) != ref.broken.astype(bool)
-        assert np.all(np.abs(s[diff] - ref.s0) < 1e-3 * ref.s0)
+        assert np.all(np.abs(np.abs(s[diff]) - ref.s0) < 1e-3 * ref.s0)
         ref.broken[:] = broken
     assert broken.sum() > 0
     phi = ctx.damage()
@@ -539,4 +586,99 @@ def test_conic_micromodulus_forces_and_dt(pd, name, precision, tol):
     ref.broken[:] = broken
     Fo = ref.forces(frozen=True).copy()
     assert rel_l2(F, Fo) <= tol
+    ctx.close()
+
+
+# --------------------------------------------------------------------------- self-contact (PD-repulsive branch)
+def self_contact_block():
+    """A jittered block of one grain plus one extra node 0.4 h from an interior
+    node, i.e. inside the contact radius R_c = 0.6 h of a node of its own grain:
+    once their bond is broken, the pair takes the PD-repulsive self-contact law
+    c (|d| - |xi|)/|xi| (Sec. 5), which no lattice reaches (nodes start >= 0.98 h
+    apart)."""
+    sc = S.small_block(nx=6, ny=5, nz=5, jitter=0.05)
+    k = int(np.argmin(np.linalg.norm(sc.x - sc.x.mean(0), axis=1)))
+    extra = sc.x[k] + np.array([0.38, 0.1, 0.05]) * sc.h
+    sc.x = np.vstack([sc.x, extra])
+    sc.vol = np.append(sc.vol, 0.5 * sc.h ** 3)
+    sc.grain = np.append(sc.grain, np.int32(0)).astype(np.int32)
+    sc.v0 = np.zeros_like(sc.x)
+    # a tough material (s0 ~ 0.7) so that no bond but the planted one is broken
+    sc.material.G0 *= 1e6
+    return sc, k, sc.n - 1
+
+
+def pair_slots(rp, col, i, j):
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return ((rows == i) & (col == j)) | ((rows == j) & (col == i))
+
+
+@pytest.mark.parametrize("precision,tol,tiles", [("mixed", MIXED_FORCE_TOL, -1), ("mixed", MIXED_FORCE_TOL, 1),
+                                                ("fp64", FP64_FORCE_TOL, 0)])
+@pytest.mark.parametrize("micromodulus", [0, 1])
+def test_self_contact_repulsion_forces(pd, precision, tol, tiles, micromodulus):
+    """The broken pair pushed to |d| = 0.25 h: forces against the oracle, and the
+    contact part alone (forces with contact minus without) against the oracle's,
+    so that the branch cannot hide under the bond forces."""
+    sc, k, e = self_contact_block()
+    sc.material.micromodulus = micromodulus
+    ref = oracle.Model.from_scenario(sc)
+    brk = pair_slots(ref.rowptr, ref.col, k, e).astype(np.uint8)
+    assert brk.sum() == 2
+    u = np.zeros_like(sc.x)
+    d0 = sc.x[e] - sc.x[k]
+    u[e] = -d0 + 0.25 * sc.h * d0 / np.linalg.norm(d0)
+    outs = []
+    for contact in (True, False):
+        ctx = pd.Context.from_scenario(sc, precision=precision, lanes=8, tiles=tiles, contact=contact)
+        ctx.set_state(u=u, broken=brk)
+        F = ctx.forces()
+        _, _, broken, _ = ctx.get_state()
+        ref.P.contact = 1 if contact else 0
+        ref.u = u.copy()
+        ref.broken[:] = brk
+        ref.forces()
+        assert np.array_equal(broken, ref.broken)
+        outs.append((F, ref.F.copy()))
+        if contact:
+            assert rel_l2(F, ref.F) <= tol
+            pairs = ctx.contacts()
+            assert [k, e] in pairs.tolist() and [e, k] in pairs.tolist()
+        ctx.close()
+    Fc, Fco = outs[0][0] - outs[1][0], outs[0][1] - outs[1][1]
+    K, c, s0, Kn = oracle.constants(sc.material.E, sc.material.G0, sc.horizon, micromodulus=micromodulus)
+    L = np.linalg.norm(d0)
+    cw = c * (sc.horizon - L) if micromodulus else c
+    # hand value on the extra node: c (|d| - |xi|)/|xi| V_k, directed away from node k
+    hand = -cw * (0.25 * sc.h - L) / L * sc.vol[k]
+    assert np.dot(Fco[e], d0 / L) == pytest.approx(hand, rel=1e-9)
+    assert rel_l2(Fc, Fco) <= (1e-4 if precision == "mixed" else 1e-9)
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-9)])
+def test_self_contact_repulsion_trajectory(pd, precision, tol):
+    """The extra node driven into its broken partner at 30 m/s: it is turned back
+    by the PD-repulsive law; 60 steps against the oracle."""
+    sc, k, e = self_contact_block()
+    ref = oracle.Model.from_scenario(sc)
+    brk = pair_slots(ref.rowptr, ref.col, k, e).astype(np.uint8)
+    d0 = sc.x[e] - sc.x[k]
+    v = np.zeros_like(sc.x)
+    v[e] = -30.0 * d0 / np.linalg.norm(d0)
+    ctx = pd.Context.from_scenario(sc, precision=precision, lanes=8)
+    ctx.set_state(u=np.zeros_like(sc.x), v=v, broken=brk)
+    ref.v = v.copy()
+    ref.broken[:] = brk
+    ref.init()
+    dt = 0.5 * ref.stable_dt()
+    assert ctx.stable_dt() == pytest.approx(ref.stable_dt(), rel=1e-12)
+    closest = np.inf
+    for _ in range(12):
+        ctx.step(dt, 5)
+        ref.step(dt, 5)
+        closest = min(closest, np.linalg.norm((sc.x[e] + ref.u[e]) - (sc.x[k] + ref.u[k])))
+    u, vg, broken, _ = ctx.get_state()
+    assert closest < np.linalg.norm(d0)
+    assert rel_l2(u, ref.u) < tol
+    assert rel_l2(vg, ref.v) < 10 * tol
     ctx.close()
