@@ -174,7 +174,8 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
 pd_status pd_build_bonds(pd_ctx *ctx, double horizon, int nfilt, const pd_bond_filter *filt);
 
 /* Replaces the wall set (0 <= nw <= 6).  Wall forces sum the single-wall cap
- * terms (Sec. 4.1); the inclusion-exclusion of Sec. 4.1.1 is not applied. */
+ * terms (Sec. 4.1); with pd_material.wall_overlap = 1 the inclusion-exclusion
+ * of Sec. 4.1.1 over orthogonal walls that a node touches is applied on top. */
 pd_status pd_set_walls(pd_ctx *ctx, int nw, const pd_wall *walls);
 
 /* Current wall points (nw*3), after the walls moved with their velocity. */
@@ -242,8 +243,9 @@ pd_status pd_fragments(pd_ctx *ctx, int32_t *label, int64_t *nfrag);
  * order: node count (size), summed nodal volume, and damage read as the broken
  * fraction of the fragment's initial bond slots (1 - intact / initial, 0 without
  * bonds).  nfrag must equal pd_fragments' count for this state (PD_EINVAL
- * otherwise); each output (nfrag entries) is nullable.  Volumes are summed with
- * atomics, so their last bits may vary between calls. */
+ * otherwise); each output (nfrag entries) is nullable.  A fragment's volume is
+ * summed in a fixed order (its nodes by caller index, strided over one warp,
+ * then a fixed butterfly), so repeated calls on one state agree bit for bit. */
 pd_status pd_fragment_stats(pd_ctx *ctx, int64_t nfrag, int64_t *size, double *volume, double *damage);
 
 /* Number of directed bonds B (each undirected bond counted twice). */
@@ -328,11 +330,18 @@ void pd_destroy(pd_ctx *ctx);
  * holds until the process exits.  Hence n <= 16,777,216; larger n gives
  * PD_EINVAL.  The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  All calls on a device share the array, so calls that
- * overlap on the GPU (other streams, other threads) race; each call writes every
- * partial it reads, so nothing needs clearing between calls.
+ * any stream capture.  The address is kept with the process-unique ID of the
+ * context it was looked up in: after cudaDeviceReset (or any other teardown of
+ * the context) the next call finds a new context ID and looks the address up
+ * again, so that call, too, belongs outside a capture.  All calls on a device
+ * share the array, so calls that overlap on the GPU (other streams, other
+ * threads) race; each call writes every partial it reads, so nothing needs
+ * clearing between calls.
  * Errors: PD_EINVAL (null pointer, n < 1, n too large, c or rho <= 0),
- * PD_ECUDA (no current device, symbol lookup or launch failed). */
+ * PD_ECUDA (no current device, symbol lookup or launch failed; taken from the
+ * calls' own return codes).  A runtime error that an earlier call left pending
+ * is neither reported by this call nor cleared by it; an error this call raises
+ * is cleared when none was pending. */
 pd_status pd_stable_dt_noalloc(int64_t n, const double *x, const double *vol, const int64_t *rowptr,
                                const int32_t *col, double c, double rho, void *stream, double *dt_out);
 

@@ -63,8 +63,49 @@ __global__ void k_dt_final(const double *__restrict__ partial, int nb, double *o
     if (threadIdx.x == 0) *out = s_min[0];
 }
 
+// Driver-API entry points, fetched through the runtime (no link against
+// libcuda): the current context and its process-unique ID.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
 std::mutex g_lock;
-double *g_addr[256];  // device address of g_dt_partial, per device ordinal (set up once)
+bool g_fns_tried = false;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// Device address of g_dt_partial per device ordinal, with the ID of the context
+// it was looked up in.  A context made again after cudaDeviceReset (or after the
+// primary context was released) has another ID, and the address is looked up
+// again, because the module, and with it the array, may then sit elsewhere.
+struct SymbolSlot {
+    unsigned long long ctx_id;
+    double *addr;
+};
+SymbolSlot g_slot[256];
+
+// ID of the calling thread's current context (0 when it has none or the driver
+// cannot say).
+unsigned long long current_ctx_id()
+{
+    if (!g_fns_tried) {
+        g_fns_tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (CtxGetIdFn)f;
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx) return 0;
+    if (g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -73,30 +114,45 @@ extern "C" pd_status pd_stable_dt_noalloc(int64_t n, const double *x, const doub
 {
     if (n < 1 || !x || !vol || !rowptr || !col || !dt_out || !(c > 0) || !(rho > 0)) return PD_EINVAL;
     if (n > (int64_t)PD_NOALLOC_MAX_BLOCKS * PD_NOALLOC_ROWS_PER_BLOCK) return PD_EINVAL;  // scratch too small
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
-        cudaGetLastError();
+    // an error some earlier call left pending is the caller's: it is neither
+    // reported as this call's failure nor cleared by it
+    const bool pending = cudaPeekAtLastError() != cudaSuccess;
+    auto failed = [&]() {
+        if (!pending) cudaGetLastError();  // clear only what this call raised
         return PD_ECUDA;
-    }
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return failed();
     double *partial;
     {
         std::lock_guard<std::mutex> guard(g_lock);
-        if (!g_addr[dev]) {
+        unsigned long long id = current_ctx_id();
+        SymbolSlot &slot = g_slot[dev];
+        if (!slot.addr || id == 0 || id != slot.ctx_id) {
             // host code cannot use the array's name as a device address: ask the
-            // runtime for this device's copy (first call on each device)
+            // runtime for this device's copy (first call on a device, first call in
+            // a new context, or every call where the context ID is unknown).  This
+            // also makes the runtime create the primary context if there is none.
             void *ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_dt_partial) != cudaSuccess || !ptr) {
-                cudaGetLastError();
-                return PD_ECUDA;
-            }
-            g_addr[dev] = (double *)ptr;
+            if (cudaGetSymbolAddress(&ptr, g_dt_partial) != cudaSuccess || !ptr) return failed();
+            if (id == 0) id = current_ctx_id();
+            slot.addr = (double *)ptr;
+            slot.ctx_id = id;
         }
-        partial = g_addr[dev];
+        partial = slot.addr;
     }
     const int nb = (int)((n + PD_NOALLOC_ROWS_PER_BLOCK - 1) / PD_NOALLOC_ROWS_PER_BLOCK);
     cudaStream_t st = (cudaStream_t)stream;
-    k_dt_partial<<<nb, PD_NOALLOC_ROWS_PER_BLOCK, 0, st>>>(x, vol, rowptr, col, n, c, rho, partial);
-    k_dt_final<<<1, 256, 0, st>>>(partial, nb, dt_out);
-    if (cudaGetLastError() != cudaSuccess) return PD_ECUDA;
+    // launch status from the launch calls themselves, not from the thread's last
+    // error (which may hold the caller's)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nb);
+    cfg.blockDim = dim3(PD_NOALLOC_ROWS_PER_BLOCK);
+    cfg.stream = st;
+    if (cudaLaunchKernelEx(&cfg, k_dt_partial, x, vol, rowptr, col, n, c, rho, partial) != cudaSuccess)
+        return failed();
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(256);
+    if (cudaLaunchKernelEx(&cfg, k_dt_final, (const double *)partial, nb, dt_out) != cudaSuccess) return failed();
     return PD_OK;
 }

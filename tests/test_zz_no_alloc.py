@@ -1,4 +1,4 @@
-"""The allocation-free critical-step entry point against pd_stable_dt.
+"""The allocation-free critical-step entry point against pd_stable_dt and the oracle.
 
 It serves callers that cannot allocate device memory when they need the step
 (a frozen memory pool, a runtime that owns all device memory, a host callback).
@@ -13,33 +13,65 @@ from paper_2506_05362_gb300 import scenarios as S
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_stable_dt_matches_context_twice():
+def _device_inputs(sc, rp, col):
     import torch
-    from paper_2506_05362_gb300 import pd
-    assert torch.cuda.is_available()
-    sc = S.sphere()
-    ctx = pd.Context.from_scenario(sc, contact=False)
-    ref = ctx.stable_dt()
-    rp, col = ctx.bonds()
-    K, c, s0, Kn = oracle.constants(sc.material.E, sc.material.G0, sc.horizon, sc.material.contact_factor)
     dev = torch.device("cuda", 0)
-    x = torch.from_numpy(np.ascontiguousarray(sc.x)).to(dev)
-    vol = torch.from_numpy(np.ascontiguousarray(sc.vol)).to(dev)
-    rowptr = torch.from_numpy(rp).to(dev)
-    colt = torch.from_numpy(col).to(dev)
+    return (torch.from_numpy(np.ascontiguousarray(sc.x)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(sc.vol)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(rp, np.int64)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(col, np.int32)).to(dev))
+
+
+def _two_calls(pd, n, x, vol, rowptr, col, c, rho):
+    """Two calls in a row on the current stream, into two device doubles."""
+    import torch
+    dev = torch.device("cuda", 0)
     out = torch.full((2,), -1.0, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize()
-    for call in range(2):  # two calls in a row share the scratch array
-        st = pd.pd_stable_dt_noalloc(sc.n, x.data_ptr(), vol.data_ptr(), rowptr.data_ptr(), colt.data_ptr(),
-                                     c, sc.material.rho, stream.cuda_stream, out[call:].data_ptr())
+    for call in range(2):  # the calls share the scratch array
+        st = pd.pd_stable_dt_noalloc(n, x.data_ptr(), vol.data_ptr(), rowptr.data_ptr(), col.data_ptr(),
+                                     c, rho, stream.cuda_stream, out[call:].data_ptr())
         assert st == pd.PD_OK
     torch.cuda.synchronize()
-    got = out.cpu().numpy()
-    # same terms, summed in caller instead of internal column order
-    assert got[0] == pytest.approx(ref, rel=1e-12)
-    assert got[1] == got[0]
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["sphere", "kalthoff"])
+def test_noalloc_stable_dt_matches_context_and_oracle_twice(name):
+    """The sphere (4,139 nodes, 17 partial blocks) and the full notched plate
+    (178,200 nodes, 697 partial blocks, so the final reduction strides over more
+    partials than it has threads): the step from the oracle's bond lists against
+    the context's pd_stable_dt and the oracle's own bound, on two calls in a row."""
+    import torch
+    from paper_2506_05362_gb300 import pd
+    assert torch.cuda.is_available()
+    sc = S.BY_NAME[name]()
+    kinds, params = S.filters_array(sc.filters)
+    rp, col = oracle.bonds(sc.x, sc.grain, sc.horizon, kinds, params)
+    model = oracle.Model(sc.x, sc.vol, sc.grain, rp, col, sc.material, sc.horizon)
+    want = model.stable_dt()
+    ctx = pd.Context.from_scenario(sc, contact=False)
+    ctx_dt = ctx.stable_dt()
     ctx.close()
+    x, vol, rowptr, colt = _device_inputs(sc, rp, col)
+    got = _two_calls(pd, sc.n, x, vol, rowptr, colt, model.c, sc.material.rho)
+    # same terms, summed in caller order on both sides but with other roundings
+    assert got[0] == pytest.approx(want, rel=1e-12)
+    assert got[0] == pytest.approx(ctx_dt, rel=1e-12)
+    assert got[1] == got[0]
+
+
+def test_noalloc_without_bonds_gives_infinity():
+    """Rows without bonds do not bound the step: all-zero row pointers give inf."""
+    import torch
+    from paper_2506_05362_gb300 import pd
+    sc = S.small_block()
+    rp = np.zeros(sc.n + 1, np.int64)
+    col = np.zeros(1, np.int32)
+    x, vol, rowptr, colt = _device_inputs(sc, rp, col)
+    got = _two_calls(pd, sc.n, x, vol, rowptr, colt, 1.0, sc.material.rho)
+    assert np.all(np.isinf(got)) and np.all(got > 0)
 
 
 def test_noalloc_rejects_sizes_beyond_the_scratch():
