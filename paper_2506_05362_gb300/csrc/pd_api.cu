@@ -1273,16 +1273,24 @@ pd_status pd_fragment_stats(pd_ctx *c, int64_t nfrag, int64_t *size, double *vol
     if (!s && have != nfrag) s = fail(c, PD_EINVAL, "nfrag does not match the current number of fragments");
     unsigned long long *dsize = nullptr, *dslots = nullptr, *dintact = nullptr;
     double *dvol = nullptr, *ddmg = nullptr;
+    FragSortScratch w = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (!s && nfrag > 0) {
-        const int64_t m = nfrag;
-        if (!(dsize = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
+        const int64_t m = nfrag, n = c->n;
+        const int64_t tmpn = std::max(radix_tmp_size(n), scan_tmp_size(m + 1) + 8);
+        if (!(dsize = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * (m + 1))) ||
             !(dslots = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
             !(dintact = (unsigned long long *)pd_dev_alloc(c, sizeof(unsigned long long) * m)) ||
-            !(dvol = (double *)pd_dev_alloc(c, sizeof(double) * m)) || !(ddmg = (double *)pd_dev_alloc(c, sizeof(double) * m))) {
+            !(dvol = (double *)pd_dev_alloc(c, sizeof(double) * m)) || !(ddmg = (double *)pd_dev_alloc(c, sizeof(double) * m)) ||
+            !(w.k1 = (uint64_t *)pd_dev_alloc(c, sizeof(uint64_t) * n)) ||
+            !(w.k2 = (uint64_t *)pd_dev_alloc(c, sizeof(uint64_t) * n)) ||
+            !(w.v1 = (uint32_t *)pd_dev_alloc(c, sizeof(uint32_t) * n)) ||
+            !(w.v2 = (uint32_t *)pd_dev_alloc(c, sizeof(uint32_t) * n)) ||
+            !(w.start = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (m + 1))) ||
+            !(w.tmp = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * tmpn))) {
             s = fail(c, PD_ENOMEM, "device allocation failed: fragment statistics");
         } else {
             fragment_stats_device(c->rowptr, c->brk, c->perm, c->x4, f.label, f.fidx, c->n, m, dsize, dvol, dslots,
-                                  dintact, ddmg, c->st);
+                                  dintact, ddmg, w, c->st);
             bool ok = true;
             if (size) ok &= cudaMemcpyAsync(size, dsize, sizeof(int64_t) * m, cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
             if (volume) ok &= cudaMemcpyAsync(volume, dvol, sizeof(double) * m, cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
@@ -1292,6 +1300,7 @@ pd_status pd_fragment_stats(pd_ctx *c, int64_t nfrag, int64_t *size, double *vol
         }
     }
     release(c, dsize); release(c, dslots); release(c, dintact); release(c, dvol); release(c, ddmg);
+    release(c, w.k1); release(c, w.k2); release(c, w.v1); release(c, w.v2); release(c, w.start); release(c, w.tmp);
     frag_release(c, f);
     return s;
 }

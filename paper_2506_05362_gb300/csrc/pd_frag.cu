@@ -83,22 +83,44 @@ __global__ void k_frag_label(const int32_t *__restrict__ parent, const int32_t *
     }
 }
 
-// per-fragment sums; fidx[c] = fragment index of label c (exclusive scan of is_label)
+// per-fragment integer sums (exact whatever the order of the atomics); fidx[c] =
+// fragment index of label c (exclusive scan of is_label).  Also the sort key of
+// every node, fragment index then caller index, for the fixed-order volume sums.
 __global__ void k_frag_stats(const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ brk,
-                             const int32_t *__restrict__ perm, const dbl4 *__restrict__ x4,
-                             const int32_t *__restrict__ label, const int64_t *__restrict__ fidx, int64_t n,
-                             unsigned long long *size, double *volume, unsigned long long *slots,
-                             unsigned long long *intact)
+                             const int32_t *__restrict__ perm, const int32_t *__restrict__ label,
+                             const int64_t *__restrict__ fidx, int64_t n, unsigned long long *size,
+                             unsigned long long *slots, unsigned long long *intact, uint64_t *key, uint32_t *node)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = fidx[label[perm[i]]];
+        const int32_t c = perm[i];
+        const int64_t q = fidx[label[c]];
         const int64_t k0 = rowptr[i], k1 = rowptr[i + 1];
         unsigned long long ok = 0;
         for (int64_t k = k0; k < k1; ++k) ok += ((brk[k >> 5] >> (k & 31)) & 1u) ? 0ull : 1ull;
         atomicAdd(size + q, 1ull);
-        atomicAdd(volume + q, x4[i].w);
         atomicAdd(slots + q, (unsigned long long)(k1 - k0));
         atomicAdd(intact + q, ok);
+        key[i] = ((uint64_t)q << 31) | (uint64_t)(uint32_t)c;
+        node[i] = (uint32_t)i;
+    }
+}
+
+// Volume of each fragment, one warp per fragment over its nodes in caller order
+// (the sorted keys): lanes stride the segment, then a fixed xor butterfly, so the
+// FP64 sum is the same on every run.
+__global__ void k_frag_volume(const uint32_t *__restrict__ node, const int64_t *__restrict__ start,
+                              const dbl4 *__restrict__ x4, int64_t nfrag, double *volume)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = w0; q < nfrag; q += nw) {
+        const int64_t a = start[q], b = start[q + 1];
+        double s = 0.0;
+        for (int64_t t = a + lane; t < b; t += 32) s += x4[node[t]].w;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) volume[q] = s;
     }
 }
 
@@ -129,12 +151,19 @@ void fragments_device(const int64_t *rowptr, const int32_t *col, const uint32_t 
 void fragment_stats_device(const int64_t *rowptr, const uint32_t *brk, const int32_t *perm, const dbl4 *x4,
                            const int32_t *label, const int64_t *fidx, int64_t n, int64_t nfrag,
                            unsigned long long *size, double *volume, unsigned long long *slots,
-                           unsigned long long *intact, double *damage, cudaStream_t st)
+                           unsigned long long *intact, double *damage, FragSortScratch &w, cudaStream_t st)
 {
     cudaMemsetAsync(size, 0, sizeof(unsigned long long) * nfrag, st);
-    cudaMemsetAsync(volume, 0, sizeof(double) * nfrag, st);
     cudaMemsetAsync(slots, 0, sizeof(unsigned long long) * nfrag, st);
     cudaMemsetAsync(intact, 0, sizeof(unsigned long long) * nfrag, st);
-    k_frag_stats<<<grid_for(n, 256), 256, 0, st>>>(rowptr, brk, perm, x4, label, fidx, n, size, volume, slots, intact);
+    k_frag_stats<<<grid_for(n, 256), 256, 0, st>>>(rowptr, brk, perm, label, fidx, n, size, slots, intact, w.k1,
+                                                   w.v1);
+    int qbits = 1;
+    while (qbits < 32 && ((int64_t)1 << qbits) <= nfrag) ++qbits;
+    uint64_t *k = w.k1, *ka = w.k2;
+    uint32_t *v = w.v1, *va = w.v2;
+    radix_sort_u64(&k, &ka, &v, &va, n, 31 + qbits, w.tmp, st);
+    scan_exclusive_i64((const int64_t *)size, w.start, nfrag, w.tmp, st);
+    k_frag_volume<<<grid_for(nfrag * 32, 256), 256, 0, st>>>(v, w.start, x4, nfrag, volume);
     k_frag_damage<<<grid_for(nfrag, 256), 256, 0, st>>>(slots, intact, nfrag, damage);
 }

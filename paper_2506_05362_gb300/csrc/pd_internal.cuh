@@ -126,10 +126,18 @@ void radix_sort_u32(uint32_t **k, uint32_t **kalt, uint32_t **v, uint32_t **valt
 // is_label are in caller order; parent and minc are n-element scratch.
 void fragments_device(const int64_t *rowptr, const int32_t *col, const uint32_t *brk, const int32_t *perm,
                       int64_t n, int32_t *parent, int32_t *minc, int32_t *label, int64_t *is_label, cudaStream_t st);
+// Scratch of the fragment statistics: sort keys and node indices (n each, two
+// buffers), segment starts (nfrag + 1), and radix/scan workspace
+// (max(radix_tmp_size(n), scan_tmp_size(nfrag + 1))).
+struct FragSortScratch {
+    uint64_t *k1, *k2;
+    uint32_t *v1, *v2;
+    int64_t *start, *tmp;
+};
 void fragment_stats_device(const int64_t *rowptr, const uint32_t *brk, const int32_t *perm, const dbl4 *x4,
                            const int32_t *label, const int64_t *fidx, int64_t n, int64_t nfrag,
                            unsigned long long *size, double *volume, unsigned long long *slots,
-                           unsigned long long *intact, double *damage, cudaStream_t st);
+                           unsigned long long *intact, double *damage, FragSortScratch &w, cudaStream_t st);
 
 // Exclusive scan of n int64 values (in may equal out); out[n] receives the total.
 // tmp must hold scan_tmp_size(n) int64.

@@ -59,6 +59,9 @@ def test_fragments_match_oracle(pd, name, frac, cut):
     assert np.array_equal(size, osize)
     assert np.array_equal(dmg, odmg)
     assert np.allclose(vol, ovol, rtol=1e-12, atol=0)
+    # volumes are summed in a fixed order: a second call agrees bit for bit
+    size2, vol2, dmg2 = ctx.fragment_stats()
+    assert np.array_equal(vol2, vol) and np.array_equal(size2, size) and np.array_equal(dmg2, dmg)
     ctx.close()
 
 
