@@ -332,7 +332,7 @@ def main():
     cpu = None if args.no_cpu_baseline else cpu_baseline(sc, args.workload)
     line = {"metric": METRIC, "value": value, "unit": "node-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "vs_baseline": None, "dtype": "f32+df64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "nodes": n, "directed_bonds": B, "precision": args.precision,
                        "l2": "inputs larger than L2: ~0.18 GB streamed from HBM per step (129 MB L2)",

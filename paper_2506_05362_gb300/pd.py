@@ -18,8 +18,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-# PD_LIB selects another build of the library (e.g. a tuning variant)
-LIB_PATH = os.environ.get("PD_LIB") or os.path.join(_HERE, "_lib", "libpd.so")
+# the in-tree build of the library (no override: tests and benchmark always load it)
+LIB_PATH = os.path.join(_HERE, "_lib", "libpd.so")
 
 PD_OK, PD_EINVAL, PD_ENOMEM, PD_ECUDA, PD_ESTATE = 0, -1, -2, -3, -4
 PD_ECAPACITY, PD_ENONFINITE, PD_ETIMEOUT, PD_EWALL = -5, -6, -7, -8

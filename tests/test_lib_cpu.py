@@ -71,14 +71,21 @@ def test_binding_fails_loudly_without_the_library():
     import subprocess
     code = ("import sys; sys.path.insert(0, %r)\n"
             "from paper_2506_05362_gb300 import pd\n"
+            "pd.LIB_PATH = %r\n"
             "try:\n"
             "    pd.lib()\n"
             "except RuntimeError as e:\n"
-            "    print('raised:', 'not built' in str(e))\n" % ROOT)
-    env = dict(os.environ, PD_LIB=os.path.join(ROOT, "no_such_dir", "libpd.so"))
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+            "    print('raised:', 'not built' in str(e))\n" % (ROOT, os.path.join(ROOT, "no_such_dir", "libpd.so")))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr[-1000:]
     assert r.stdout.strip() == "raised: True"
+
+
+def test_binding_has_no_library_override():
+    """The binding always loads the in-tree build: no environment variable can
+    point the tests or the benchmark at another library."""
+    txt = open(os.path.join(ROOT, "paper_2506_05362_gb300", "pd.py")).read()
+    assert "environ" not in txt
 
 
 def test_product_package_never_imports_the_oracle():
