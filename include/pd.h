@@ -126,6 +126,9 @@ typedef struct {
     int graph_chunk;                     /* steps per captured CUDA graph; 0 = 64 */
     int tiles;                           /* mixed path: shared-memory tiles 1 = on, -1 = off,
                                             0 = chosen by the autotuner (on when lanes are fixed) */
+    int64_t cand_capacity;               /* initial capacity of the contact-candidate list
+                                            (entries); 0 = max(1024, 8 n).  A rebuild that
+                                            overflows it rolls its segment back and grows it. */
 } pd_options;
 
 /* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */
@@ -274,8 +277,14 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
 /* Sets the state (any input may be NULL to keep it), clears a latched device
  * error and re-evaluates the forces (which may break bonds).  u and v are
  * checked on the device before anything is applied: a non-finite value in
- * either returns PD_EINVAL and leaves the whole state unchanged.  The wall
- * impulses of pd_bulk_stress_mean are zeroed. */
+ * either returns PD_EINVAL and leaves the whole state unchanged.  Every given
+ * part is also compared on the device with the current state; when all of them
+ * equal it (a state that pd_get_state returned, sent back unchanged), nothing
+ * is applied and the force evaluation is skipped: the acceleration stored with
+ * the current state is kept, so the call leaves the trajectory bit for bit as
+ * if it had not been made.  The wall impulses of pd_bulk_stress_mean are zeroed
+ * in either case.  Errors: PD_EINVAL (non-finite u or v), PD_ESTATE (bond
+ * memory before pd_build_bonds), PD_ECUDA, and those of the force evaluation. */
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
 
@@ -310,6 +319,11 @@ pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, in
  * rebuilds of those steps, and segments rolled back and rerun because the list
  * went stale or overflowed (see pd_step). */
 pd_status pd_step_counters(pd_ctx *ctx, int64_t *steps, int64_t *rebuilds, int64_t *rollbacks);
+
+/* pd_set_state / pd_set_state_packed calls since pd_create (each pointer
+ * nullable): applied (the state differed and the forces were evaluated again)
+ * and unchanged (the state equalled the current one; nothing was applied). */
+pd_status pd_state_counters(pd_ctx *ctx, int64_t *applied, int64_t *unchanged);
 
 const char *pd_last_error(const pd_ctx *ctx);
 void pd_destroy(pd_ctx *ctx);

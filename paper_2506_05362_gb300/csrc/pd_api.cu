@@ -87,6 +87,8 @@ struct pd_ctx {
     uint8_t *stage_b = nullptr;  // B bytes
     dbl4 *snap_u = nullptr, *snap_v = nullptr, *snap_acc = nullptr;
     uint32_t *snap_brk = nullptr;
+    uint32_t *stage_bits = nullptr;  // a caller's bond memory in internal order (pd_set_state*)
+    int64_t n_state_applied = 0, n_state_unchanged = 0;  // pd_set_state* calls by outcome
 
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -543,7 +545,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     ALLOC(c->cand_ptr, int64_t, n + 1);
     ALLOC(c->cand_cnt, int64_t, n + 1);
     CK(cudaMemsetAsync(c->cand_ptr, 0, sizeof(int64_t) * (n + 1), c->st));
-    c->cand_cap = std::max<int64_t>(1024, 8 * n);
+    c->cand_cap = c->opt.cand_capacity > 0 ? c->opt.cand_capacity : std::max<int64_t>(1024, 8 * n);
     ALLOC(c->cand, int2, c->cand_cap);
     if (c->mat.beta_d > 0 || c->mat.mu > 0) ALLOC(c->cand_fd, dbl4, c->cand_cap);  // damping + friction per candidate
     // reductions
@@ -605,6 +607,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
     if (c->opt.tiles < -1 || c->opt.tiles > 1) { delete c; return PD_EINVAL; }
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
+    if (c->opt.cand_capacity < 0) { delete c; return PD_EINVAL; }
     c->mat = *mat;
     c->n = n;
     pd_status s = create_impl(c, x, vol, grain, v0);
@@ -674,7 +677,7 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     clear_graphs(c);
     c->bonds_ready = false;
     release(c, c->rowptr); release(c, c->col); release(c, c->brk); release(c, c->kc_of);
-    release(c, c->crow); release(c, c->snap_brk); release(c, c->stage_b);
+    release(c, c->crow); release(c, c->snap_brk); release(c, c->stage_b); release(c, c->stage_bits);
     c->delta = horizon;
     constants(c);
     const int64_t n = c->n;
@@ -790,6 +793,7 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     c->nwords = (B + 31) / 32 + 1;
     ALLOC(c->brk, uint32_t, c->nwords);
     ALLOC(c->snap_brk, uint32_t, c->nwords);
+    ALLOC(c->stage_bits, uint32_t, c->nwords);
     ALLOC(c->stage_b, uint8_t, B + 16);
     CK(cudaMemsetAsync(c->brk, 0, sizeof(uint32_t) * c->nwords, c->st));
     // mixed path: neighbour index with the broken flag in bit 31, one word per slot
@@ -967,7 +971,8 @@ static pd_status snapshot(pd_ctx *c, bool restore)
 static pd_status rebuild_period(pd_ctx *c, double dt, int *k)
 {
     if (!c->opt.contact) { *k = 1 << 30; return PD_OK; }
-    if (c->opt.contact_every > 0) { *k = c->opt.contact_every; return PD_OK; }
+    // a period the caller fixed is still lowered while a stale list forced it down
+    if (c->opt.contact_every > 0) { *k = std::min(c->opt.contact_every, c->k_cap); return PD_OK; }
     int nb = vmax_blocks(c->n);
     if (c->opt.precision == PD_MIXED) materialize_df(c->vh, c->vl, 1, c->n, c->v, c->st);
     vmax(c->v, c->n, c->dscratch, c->st);
@@ -1429,58 +1434,72 @@ static pd_status get_state_impl(pd_ctx *c, double *u, double *v, uint8_t *broken
     return sync(c);
 }
 
+// Applies a caller state.  Everything given is staged and compared on the device
+// with the current state first: non-finite u or v rejects the call; a state
+// equal to the current one in every given part (what pd_get_state returned, sent
+// back unchanged) is not applied again, and its force evaluation is skipped, since
+// the stored acceleration already belongs to it.
 static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, const uint8_t *broken,
                                 const uint32_t *bits, const double *t)
 {
     if (!c) return PD_EINVAL;
     CK(cudaSetDevice(c->opt.device));
+    if ((broken || bits) && !c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
     const size_t nb = sizeof(double) * 3 * c->n;
-    if (u || v) {
-        // stage both, check both on the device, apply only if both are finite
-        double *su = c->stage, *sv = c->stage + 3 * c->n;
+    const bool mixed = c->opt.precision == PD_MIXED;
+    const bool with_bits = (broken || bits) && c->B > 0;
+    double *su = c->stage, *sv = c->stage + 3 * c->n;
+    unsigned flags = 0;
+    if (u || v || with_bits) {
         CK(cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
         if (u) {
             CK(cudaMemcpyAsync(su, u, nb, cudaMemcpyHostToDevice, c->st));
             check_finite(su, 3 * c->n, 1u, c->dflag, c->st);
+            state_differs(su, c->perm, c->n, mixed ? c->uh[c->cur] : nullptr, mixed ? c->ul[c->cur] : nullptr, REC,
+                          c->u[c->cur], 4u, c->dflag, c->st);
         }
         if (v) {
             CK(cudaMemcpyAsync(sv, v, nb, cudaMemcpyHostToDevice, c->st));
             check_finite(sv, 3 * c->n, 2u, c->dflag, c->st);
+            state_differs(sv, c->perm, c->n, mixed ? c->vh : nullptr, mixed ? c->vl : nullptr, 1, c->v, 8u, c->dflag,
+                          c->st);
         }
-        unsigned bad = 0;
-        CK(cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
-        pd_status s = sync(c);
-        if (s) return s;
-        if (bad & 1u) return fail(c, PD_EINVAL, "u contains a non-finite value");
-        if (bad & 2u) return fail(c, PD_EINVAL, "v contains a non-finite value");
-        if (u) {
-            if (c->opt.precision == PD_MIXED) {
-                from_caller(su, c->perm, c->n, c->u[0], c->st);
-                split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], REC, c->st);
-            } else {
-                from_caller(su, c->perm, c->n, c->u[c->cur], c->st);
-            }
-        }
-        if (v) {
-            from_caller(sv, c->perm, c->n, c->v, c->st);
-            if (c->opt.precision == PD_MIXED) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
-        }
-    }
-    if (broken || bits) {
-        if (!c->bonds_ready) return fail(c, PD_ESTATE, "no bonds yet");
-        if (c->B) {
+        if (with_bits) {  // the caller's bond memory in internal slot order, then compared
             if (broken) {
                 CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
-                bytes_to_bits(c->stage_b, c->kc_of, c->B, c->brk, c->st);
+                bytes_to_bits(c->stage_b, c->kc_of, c->B, c->stage_bits, c->st);
             } else {
                 uint32_t *sw = (uint32_t *)c->stage_b;
                 CK(cudaMemcpyAsync(sw, bits, sizeof(uint32_t) * (size_t)((c->B + 31) / 32), cudaMemcpyHostToDevice,
                                    c->st));
-                packed_to_bits(sw, c->kc_of, c->B, c->brk, c->st);
+                packed_to_bits(sw, c->kc_of, c->B, c->stage_bits, c->st);
             }
-            if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
-            if (c->colf) sync_colf_flags(c->brk, c->col, c->B, c->colf, c->st);
+            words_differ(c->stage_bits, c->brk, (c->B + 31) / 32, 16u, c->dflag, c->st);
         }
+        CK(cudaMemcpyAsync(&flags, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+        pd_status s = sync(c);
+        if (s) return s;
+        if (flags & 1u) return fail(c, PD_EINVAL, "u contains a non-finite value");
+        if (flags & 2u) return fail(c, PD_EINVAL, "v contains a non-finite value");
+    }
+    const bool changed = (flags & (4u | 8u | 16u)) != 0;
+    if (u && (flags & 4u)) {
+        if (mixed) {
+            from_caller(su, c->perm, c->n, c->u[0], c->st);
+            split_df(c->u[0], c->xl4, c->n, c->uh[c->cur], c->ul[c->cur], REC, c->st);
+        } else {
+            from_caller(su, c->perm, c->n, c->u[c->cur], c->st);
+        }
+    }
+    if (v && (flags & 8u)) {
+        from_caller(sv, c->perm, c->n, c->v, c->st);
+        if (mixed) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
+    }
+    if (with_bits && (flags & 16u)) {
+        CK(cudaMemcpyAsync(c->brk, c->stage_bits, sizeof(uint32_t) * (size_t)((c->B + 31) / 32),
+                           cudaMemcpyDeviceToDevice, c->st));
+        if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);
+        if (c->colf) sync_colf_flags(c->brk, c->col, c->B, c->colf, c->st);
     }
     if (t) c->t = *t;
     c->latched = 0;
@@ -1488,7 +1507,8 @@ static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, con
     CK(reset_impulse(c));
     pd_status s = sync(c);
     if (s) return s;
-    if (c->bonds_ready) return eval_forces(c);
+    ++(changed ? c->n_state_applied : c->n_state_unchanged);
+    if (c->bonds_ready && changed) return eval_forces(c);
     return PD_OK;
 }
 
@@ -1536,6 +1556,14 @@ pd_status pd_step_counters(pd_ctx *c, int64_t *steps, int64_t *rebuilds, int64_t
     if (steps) *steps = c->n_steps;
     if (rebuilds) *rebuilds = c->n_rebuilds;
     if (rollbacks) *rollbacks = c->n_rollbacks;
+    return PD_OK;
+}
+
+pd_status pd_state_counters(pd_ctx *c, int64_t *applied, int64_t *unchanged)
+{
+    if (!c) return PD_EINVAL;
+    if (applied) *applied = c->n_state_applied;
+    if (unchanged) *unchanged = c->n_state_unchanged;
     return PD_OK;
 }
 

@@ -2,6 +2,7 @@
 // candidate lists, and the small per-node reductions (damage, critical step,
 // contact pairs for output).
 #include "pd_build.cuh"
+#include "pd_df.cuh"
 #include "pd_grid.cuh"
 
 namespace {
@@ -507,6 +508,40 @@ __global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
+// flag |= bit when the caller-order doubles `staged` differ from the current
+// state: the double-float pairs (hi, lo) at stride `stride` when hi is given
+// (each converted by the formula every query uses), else the FP64 array d64
+__global__ void k_state_differs(const double *__restrict__ staged, const int32_t *__restrict__ perm, int64_t n,
+                                const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride,
+                                const dbl4 *__restrict__ d64, unsigned bit, unsigned *flag)
+{
+    bool diff = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = perm[k];
+        double a, b, c;
+        if (hi) {
+            const float4 h = hi[stride * k], l = lo[stride * k];
+            a = df_to_double(df{h.x, l.x});
+            b = df_to_double(df{h.y, l.y});
+            c = df_to_double(df{h.z, l.z});
+        } else {
+            const dbl4 q = d64[k];
+            a = q.x; b = q.y; c = q.z;
+        }
+        diff |= (a != staged[3 * i]) | (b != staged[3 * i + 1]) | (c != staged[3 * i + 2]);
+    }
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
+}
+
+__global__ void k_words_differ(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, int64_t nw,
+                               unsigned bit, unsigned *flag)
+{
+    bool diff = false;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
+        diff |= a[w] != b[w];
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
+}
+
 __global__ void k_from_caller(const double *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, dbl4 *out)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
@@ -719,6 +754,17 @@ void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cuda
 void check_finite(const double *a, int64_t m, unsigned bit, unsigned *flag, cudaStream_t st)
 {
     k_nonfinite<<<grid_of(m), 256, 0, st>>>(a, m, bit, flag);
+}
+
+void state_differs(const double *staged, const int32_t *perm, int64_t n, const float4 *hi, const float4 *lo,
+                   int stride, const dbl4 *d64, unsigned bit, unsigned *flag, cudaStream_t st)
+{
+    k_state_differs<<<grid_of(n), 256, 0, st>>>(staged, perm, n, hi, lo, stride, d64, bit, flag);
+}
+
+void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, unsigned bit, unsigned *flag, cudaStream_t st)
+{
+    k_words_differ<<<grid_of(nw), 256, 0, st>>>(a, b, nw, bit, flag);
 }
 
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st)

@@ -50,6 +50,12 @@ void bits_to_packed(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint32
 void packed_to_bits(const uint32_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st);
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st);
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st);
+// *flag |= bit when the caller-order state `staged` (n*3) differs from the current
+// one: double-float pairs hi/lo (stride in float4) when hi != NULL, else d64
+void state_differs(const double *staged, const int32_t *perm, int64_t n, const float4 *hi, const float4 *lo,
+                   int stride, const dbl4 *d64, unsigned bit, unsigned *flag, cudaStream_t st);
+// *flag |= bit when the nw words of a and b differ
+void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, unsigned bit, unsigned *flag, cudaStream_t st);
 // *flag |= bit when any of the m doubles at a is not finite
 void check_finite(const double *a, int64_t m, unsigned bit, unsigned *flag, cudaStream_t st);
 void split_hilo(const dbl4 *u, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);

@@ -49,7 +49,8 @@ class Options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("contact", ctypes.c_int), ("contact_every", ctypes.c_int), ("skin", ctypes.c_double),
-                ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("tiles", ctypes.c_int)]
+                ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("tiles", ctypes.c_int),
+                ("cand_capacity", ctypes.c_int64)]
 
 
 class Wall(ctypes.Structure):
@@ -100,6 +101,7 @@ def lib():
                 "pd_tuning": (i32, [P, P, P, P]),
                 "pd_last_step_stats": (i32, [P, P, P, P]),
                 "pd_step_counters": (i32, [P, P, P, P]),
+                "pd_state_counters": (i32, [P, P, P]),
                 "pd_set_profiling": (i32, [P, i32]),
                 "pd_stable_dt_noalloc": (i32, [i64, P, P, P, P, f64, f64, P, P]),
                 "pd_last_error": (ctypes.c_char_p, [P]),
@@ -350,6 +352,12 @@ def pd_step_counters(h):
     return a.value, b.value, c.value
 
 
+def pd_state_counters(h):
+    a, u = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().pd_state_counters(h, ctypes.byref(a), ctypes.byref(u)), h)
+    return a.value, u.value
+
+
 def pd_last_step_stats(h):
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
     _check(lib().pd_last_step_stats(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), h)
@@ -377,7 +385,7 @@ class Context:
 
     def __init__(self, x, vol, grain, material, v0=None, precision="mixed", contact=True,
                  contact_every=0, skin=0.0, lanes=0, chunk=64, device=0, stream=None,
-                 torch_memory=True, tiles=0):
+                 torch_memory=True, tiles=0, cand_capacity=0, allocator=None):
         import torch
         m = material
         self.material = Material(m.E, m.rho, m.G0, m.contact_radius, m.contact_factor, m.constants,
@@ -390,7 +398,10 @@ class Context:
         self.stream = stream
         o.stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         self._alloc = None
-        if torch_memory:
+        if allocator is not None:  # an object with ALLOC_FN / FREE_FN callbacks .alloc and .free
+            self._alloc = allocator
+            o.alloc, o.free = allocator.alloc, allocator.free
+        elif torch_memory:
             self._alloc = _TorchAllocator(device, o.stream)
             o.alloc, o.free = self._alloc.alloc, self._alloc.free
         o.precision = PD_FP64 if precision == "fp64" else PD_MIXED
@@ -400,6 +411,7 @@ class Context:
         o.lanes_per_node = lanes
         o.graph_chunk = chunk
         o.tiles = tiles
+        o.cand_capacity = int(cand_capacity)
         self.options = o
         self.n = int(np.asarray(x).reshape(-1, 3).shape[0])
         self.h = pd_create(x, vol, grain, self.material, o, v0)
@@ -481,6 +493,10 @@ class Context:
 
     def last_step_stats(self):
         return pd_last_step_stats(self.h)
+
+    def state_counters(self):
+        """(applied, unchanged) pd_set_state* calls since creation."""
+        return pd_state_counters(self.h)
 
     def step_counters(self):
         """(steps, contact-list rebuilds, rolled-back segments) since creation."""

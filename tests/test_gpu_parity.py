@@ -414,6 +414,38 @@ def test_packed_state_equals_byte_state(pd):
     assert np.array_equal(d.get_state()[2], ba)
 
 
+def test_set_state_of_the_current_state_is_skipped(pd):
+    """A state sent back unchanged (the byte form, then the packed form) is
+    recognised on the device: nothing is applied, the force evaluation is
+    skipped, and the run continues bit for bit as one that made no round trip.
+    A state that differs in one bit of one component is applied."""
+    sc = S.sphere()
+    a = pd.Context.from_scenario(sc, lanes=16)
+    b = pd.Context.from_scenario(sc, lanes=16)
+    dt = 0.8 * a.stable_dt()
+    a.step(dt, 50)
+    b.step(dt, 50)
+    u, v, broken, t = a.get_state()
+    a.set_state(u=u, v=v, broken=broken, t=t)
+    up, vp, bits, tp = pd.pd_get_state_packed(a.h, a.n, a.B)
+    pd.pd_set_state_packed(a.h, up, vp, bits, tp)
+    assert a.state_counters() == (0, 2)
+    a.step(dt, 50)
+    b.step(dt, 50)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    sa, wa = a.bulk_stress([sc.wall_area] * 2)
+    sb, wb = b.bulk_stress([sc.wall_area] * 2)
+    assert np.array_equal(wa, wb)
+    u2 = a.get_state()[0].copy()
+    u2[sc.n // 2, 1] = np.nextafter(u2[sc.n // 2, 1], np.inf)
+    a.set_state(u=u2)
+    assert a.state_counters() == (1, 2)
+    # held as a double-float pair: equal to about 2^-48 relative
+    assert np.allclose(a.get_state()[0], u2, rtol=2.0 ** -46, atol=0)
+    a.close(); b.close()
+
+
 def test_damage_and_stable_dt_match(pd):
     sc = S.small_block(nx=9, ny=7, nz=5, jitter=0.05)
     ctx = pd.Context.from_scenario(sc, contact=False)
