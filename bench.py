@@ -48,6 +48,7 @@ def make_workload(name):
             "aggregate": lambda: S.aggregate(n_grains=1000, seed=0),
             "shape-sphere": lambda: S.shape_study("sphere"), "shape-shell": lambda: S.shape_study("shell"),
             "shape-jack": lambda: S.shape_study("jack"), "double-hollow": S.double_hollow}[name]()
+KERNEL_NAMES = {0: "global gathers", 1: "shared-memory tiles", 2: "each bond once (two passes)"}
 BYTES_PER_NODE = 170.0      # x, V, u (r/w), v (r/w), F, row pointers per node and step
 BYTES_PER_BOND = 4.0 + 1.0 / 8.0  # neighbour index + broken bit per directed bond
 
@@ -203,6 +204,8 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-network leg")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per node (0 = autotune)")
     ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"])
+    ap.add_argument("--pairs", default="auto", choices=["auto", "on", "off"],
+                    help="each bond evaluated once (two passes)")
     ap.add_argument("--workload", default="plate", choices=sorted(WORKLOADS),
                     help="workload of the timed steps (the headline figure is the plate)")
     ap.add_argument("--no-aggregate", action="store_true",
@@ -231,11 +234,13 @@ def main():
     sc = make_workload(args.workload)
     stream = torch.cuda.Stream(local)
     ctx = pd.Context.from_scenario(sc, precision=args.precision, device=local, stream=stream,
-                                   lanes=args.lanes, tiles={"auto": 0, "on": 1, "off": -1}[args.tiles])
-    lanes, tiled, tms = ctx.tuning()
-    tuning = {"lanes_per_node": lanes, "tiled": tiled,
+                                   lanes=args.lanes, tiles={"auto": 0, "on": 1, "off": -1}[args.tiles],
+                                   pairs={"auto": 0, "on": 1, "off": -1}[args.pairs])
+    lanes, kernel, tms = ctx.tuning()
+    tuning = {"lanes_per_node": lanes, "kernel": KERNEL_NAMES[kernel],
               "ms_global_4_8_16_32": [round(float(t), 4) for t in tms[:4]],
-              "ms_tiled_4_8_16_32": [round(float(t), 4) for t in tms[4:]]}
+              "ms_tiled_4_8_16_32": [round(float(t), 4) for t in tms[4:8]],
+              "ms_pairs_4_8_16_32": [round(float(t), 4) for t in tms[8:]]}
     dt = 0.8 * ctx.stable_dt()
     n, B = sc.n, ctx.B
     # warm-up (captures the graphs)
@@ -353,7 +358,7 @@ def bench_aggregate(local, stream, steps=200):
     from paper_2506_05362_gb300 import pd, scenarios as S
     sc = S.aggregate(n_grains=1000, seed=0)
     ctx = pd.Context.from_scenario(sc, device=local, stream=stream)
-    lanes, tiled, _ = ctx.tuning()
+    lanes, kernel, _ = ctx.tuning()
     dt = 0.8 * ctx.stable_dt()
     ctx.step(dt, 10)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -375,7 +380,7 @@ def bench_aggregate(local, stream, steps=200):
     return {"workload": "1000 star-shaped glass grains, R ~ U(0.4, 0.6) mm, h = R/12 (0.5 mm/12), delta = 3h, "
                         "six walls, top wall at 10 m/s", "nodes": n, "directed_bonds": B, "steps": steps,
             "ms_per_step": ms / steps, "node_steps_per_s": n * steps / (ms * 1e-3),
-            "bond_updates_per_s": B * steps / (ms * 1e-3), "lanes_per_node": lanes, "tiled": tiled,
+            "bond_updates_per_s": B * steps / (ms * 1e-3), "lanes_per_node": lanes, "kernel": KERNEL_NAMES[kernel],
             "k_step_ms": force_ms, "k_step_hbm_frac": alg / (force_ms * 1e-3) / 1e9 / hbm, "peak_kind": kind}
 
 

@@ -129,6 +129,10 @@ typedef struct {
     int64_t cand_capacity;               /* initial capacity of the contact-candidate list
                                             (entries); 0 = max(1024, 8 n).  A rebuild that
                                             overflows it rolls its segment back and grows it. */
+    int pairs;                           /* mixed path: each bond evaluated once, from its
+                                            lower-index end, in two passes (Eq. pmb is pairwise
+                                            antisymmetric): 1 = on, -1 = off, 0 = chosen by the
+                                            autotuner; pairs = 1 with tiles = 1 is PD_EINVAL */
 } pd_options;
 
 /* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */
@@ -297,11 +301,13 @@ pd_status pd_get_state_packed(pd_ctx *ctx, double *u, double *v, uint32_t *broke
 pd_status pd_set_state_packed(pd_ctx *ctx, const double *u, const double *v, const uint32_t *broken_bits,
                               const double *t);
 
-/* Autotuning record of the bond loop: lanes per node chosen, whether the
- * shared-memory tiles were chosen, and the measured time (ms) of one force
- * evaluation per candidate: ms[0..3] global gathers with 4, 8, 16, 32 lanes,
- * ms[4..7] tiles with 4, 8, 16, 32 lanes (0 = not run).  Any pointer may be NULL. */
-pd_status pd_tuning(pd_ctx *ctx, int *lanes, int *tiled, double ms[8]);
+/* Autotuning record of the bond loop: lanes per node chosen, the kernel chosen
+ * (0 = every directed slot gathers its neighbour from global memory, 1 =
+ * shared-memory tiles, 2 = each bond once in two passes) and the measured time
+ * (ms) of one force evaluation per candidate: ms[0..3] kernel 0 with 4, 8, 16, 32
+ * lanes, ms[4..7] kernel 1, ms[8..11] kernel 2 (0 = not run).  Any pointer may be
+ * NULL. */
+pd_status pd_tuning(pd_ctx *ctx, int *lanes, int *kernel, double ms[12]);
 
 /* Profiling switch.  When on, pd_step launches its kernels one by one (no CUDA
  * graph) with CUDA events around every fused force/update launch, so that

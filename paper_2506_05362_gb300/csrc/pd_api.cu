@@ -65,7 +65,7 @@ struct pd_ctx {
     unsigned *counter = nullptr, *derr = nullptr, *vmax_bits = nullptr, *dflag = nullptr;
     int *stale = nullptr;
     int blocks = 0, lanes = 0, blocks_cap = 0;
-    double tune_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double tune_ms[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // global, tiled, each bond once; 4/8/16/32 lanes
     // shared-memory tiles of the mixed path
     int64_t *tile_ptr = nullptr;
     int32_t *ulist = nullptr;
@@ -75,6 +75,11 @@ struct pd_ctx {
     int tile_rows = 64, tile_cap = 0, tile_slot_cap = 0;
     size_t tile_smem = 0;
     bool tiled = false;
+    // each bond once (mixed path): split, mirror slots, per-slot factors, pass 1's row forces
+    int32_t *split = nullptr, *mir = nullptr;
+    float *tb = nullptr;
+    float4 *fup = nullptr;
+    bool pairs_ok = false, pairs = false;
     double centre[3] = {0, 0, 0};
 
     WallSet walls;
@@ -298,7 +303,13 @@ StepParams params(pd_ctx *c, int mode, int in, double dt)
     p.skin = skin_of(c);
     p.stale = c->stale;
     for (int q = 0; q < 3; ++q) p.centre[q] = c->centre[q];
-    if (mixed && c->tiled) {
+    if (mixed && c->pairs) {
+        p.pairs = 1;
+        p.split = c->split;
+        p.mir = c->mir;
+        p.tb = c->tb;
+        p.fup = c->fup;
+    } else if (mixed && c->tiled) {
         p.tile_cap = c->tile_cap;
         p.tile_slot_cap = c->tile_slot_cap;
         p.tile_rows = c->tile_rows;
@@ -606,6 +617,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     int l = c->opt.lanes_per_node;
     if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
     if (c->opt.tiles < -1 || c->opt.tiles > 1) { delete c; return PD_EINVAL; }
+    if (c->opt.pairs < -1 || c->opt.pairs > 1 || (c->opt.pairs == 1 && c->opt.tiles == 1)) { delete c; return PD_EINVAL; }
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
     if (c->opt.cand_capacity < 0) { delete c; return PD_EINVAL; }
     c->mat = *mat;
@@ -622,22 +634,24 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
 
 static pd_status autotune(pd_ctx *c)
 {
-    // time a force evaluation (idempotent at a fixed state) for each lane count,
-    // with and without shared-memory tiles on the mixed path
+    // time a force evaluation (idempotent at a fixed state) for each lane count and
+    // each kernel the context can run: per-slot gathers from global memory (0),
+    // shared-memory tiles (1), each bond once in two passes (2)
     const int cand[4] = {4, 8, 16, 32};
     const bool mixed = c->opt.precision == PD_MIXED;
-    const bool can_tile = c->tiled;
-    const int tmin = (can_tile && c->opt.tiles == 1) ? 1 : 0;
+    bool use[3] = {c->opt.tiles != 1 && c->opt.pairs != 1, c->tiled && c->opt.tiles != -1 && c->opt.pairs != 1,
+                   c->pairs_ok && c->opt.pairs != -1 && c->opt.tiles != 1};
+    if (!use[0] && !use[1] && !use[2]) use[0] = true;
     double best = INFINITY;
-    int bestl = 16;
-    bool best_tiled = false;
+    int bestl = 16, bestk = 0;
     if (c->opt.contact) enqueue_rebuild(c, c->cur);
+    for (int q = 0; q < 12; ++q) c->tune_ms[q] = 0;
     for (int q = 0; q < 4; ++q) {
-        c->tune_ms[q] = 0;
-        c->tune_ms[4 + q] = 0;
-        for (int tl = tmin; tl < (can_tile ? 2 : 1); ++tl) {
+        for (int kind = 0; kind < 3; ++kind) {
+            if (!use[kind]) continue;
             const int l = cand[q];
-            c->tiled = tl == 1;
+            c->tiled = kind == 1;
+            c->pairs = kind == 2;
             const int blocks = std::min(c->blocks_cap, step_blocks(l, c->opt.device, mixed, c->tiled, c->tile_smem));
             StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
             launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
@@ -648,12 +662,13 @@ static pd_status autotune(pd_ctx *c)
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
             const double t = ms / 5.0;
-            c->tune_ms[4 * tl + q] = t;
-            if (t < best) { best = t; bestl = l; best_tiled = c->tiled; }
+            c->tune_ms[4 * kind + q] = t;
+            if (t < best) { best = t; bestl = l; bestk = kind; }
         }
     }
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
-    c->tiled = best_tiled;
+    c->tiled = bestk == 1;
+    c->pairs = bestk == 2;
     c->lanes = bestl;
     c->blocks = std::min(c->blocks_cap, step_blocks(bestl, c->opt.device, mixed, c->tiled, c->tile_smem));
     clear_graphs(c);
@@ -678,6 +693,8 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     c->bonds_ready = false;
     release(c, c->rowptr); release(c, c->col); release(c, c->brk); release(c, c->kc_of);
     release(c, c->crow); release(c, c->snap_brk); release(c, c->stage_b); release(c, c->stage_bits);
+    release(c, c->split); release(c, c->mir); release(c, c->tb); release(c, c->fup);
+    c->pairs_ok = c->pairs = false;
     c->delta = horizon;
     constants(c);
     const int64_t n = c->n;
@@ -801,6 +818,23 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     if (c->opt.precision == PD_MIXED) {
         ALLOC(c->colf, int32_t, B + 16);
         sync_colf_flags(c->brk, c->col, B, c->colf, c->st);
+    }
+    // each bond once (mixed path; materials whose walls need the extra terms run the
+    // per-slot kernels that carry them)
+    if (c->opt.precision == PD_MIXED && c->opt.pairs >= 0 && !(c->mat.mu > 0) && !c->mat.wall_overlap) {
+        ALLOC(c->split, int32_t, n + 1);
+        ALLOC(c->mir, int32_t, B + 16);
+        ALLOC(c->tb, float, B + 16);
+        ALLOC(c->fup, float4, n);
+        CK(cudaMemsetAsync(c->dflag, 0, sizeof(unsigned), c->st));
+        pair_index(c->rowptr, c->col, n, c->split, c->mir, c->dflag, c->st);
+        unsigned bad = 0;
+        CK(cudaMemcpyAsync(&bad, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+        s = sync(c);
+        if (s) return s;
+        if (bad) return fail(c, PD_ECUDA, "bond list is not symmetric");
+        c->pairs_ok = true;
+        c->pairs = c->opt.pairs == 1;
     }
     CK(cudaGetLastError());
     s = sync(c);
@@ -1533,13 +1567,13 @@ pd_status pd_set_state_packed(pd_ctx *c, const double *u, const double *v, const
     return set_state_impl(c, u, v, nullptr, broken_bits, t);
 }
 
-pd_status pd_tuning(pd_ctx *c, int *lanes, int *tiled, double ms[8])
+pd_status pd_tuning(pd_ctx *c, int *lanes, int *kernel, double ms[12])
 {
     if (!c) return PD_EINVAL;
     if (lanes) *lanes = c->lanes;
-    if (tiled) *tiled = c->tiled ? 1 : 0;
+    if (kernel) *kernel = c->pairs ? 2 : (c->tiled ? 1 : 0);
     if (ms)
-        for (int q = 0; q < 8; ++q) ms[q] = c->tune_ms[q];
+        for (int q = 0; q < 12; ++q) ms[q] = c->tune_ms[q];
     return PD_OK;
 }
 

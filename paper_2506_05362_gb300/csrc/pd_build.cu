@@ -251,7 +251,23 @@ __global__ void k_cand(const dbl4 *__restrict__ x4, const dbl4 *__restrict__ u4,
                         ++k;
                     }
                 }
-        if (!FILL) cnt[i] = k;
+        if (!FILL) {
+            cnt[i] = k;
+        } else {
+            // ascending partner index (insertion sort; rows hold few candidates), so
+            // that the step kernels add contact terms in an order that does not
+            // depend on the grid's bucket order
+            int2 *row = cand + base;
+            for (int64_t a = 1; a < k; ++a) {
+                const int2 c = row[a];
+                int64_t b = a - 1;
+                while (b >= 0 && row[b].x > c.x) {
+                    row[b + 1] = row[b];
+                    --b;
+                }
+                row[b + 1] = c;
+            }
+        }
     }
 }
 
@@ -487,6 +503,39 @@ __global__ void k_sync_colf_flags(const uint32_t *__restrict__ brk, const int32_
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < B; k += (int64_t)gridDim.x * blockDim.x)
         colf[k] = (int32_t)((uint32_t)col[k] | (((brk[k >> 5] >> (k & 31)) & 1u) << 31));
+}
+
+// Index arrays of the each-bond-once passes: split[i] = first slot of row i whose
+// neighbour index exceeds i (rows are sorted ascending); for each such slot k
+// (bond i -> j), mir[k] = the slot of i in row j, and mir of that slot = k.  A
+// bond without its reverse (the lists are symmetric by construction) sets *bad.
+__global__ void k_pair_index(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col, int64_t n,
+                             int32_t *split, int32_t *mir, unsigned *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k0 = rowptr[i], k1 = rowptr[i + 1];
+        int64_t a = k0, b = k1;  // first slot with col > i
+        while (a < b) {
+            const int64_t m = (a + b) >> 1;
+            if (col[m] > i) b = m; else a = m + 1;
+        }
+        split[i] = (int32_t)a;
+        for (int64_t k = a; k < k1; ++k) {
+            const int64_t j = col[k];
+            int64_t lo = rowptr[j], hi = rowptr[j + 1];
+            while (lo < hi) {
+                const int64_t m = (lo + hi) >> 1;
+                if (col[m] < i) lo = m + 1; else hi = m;
+            }
+            if (lo < rowptr[j + 1] && col[lo] == i) {
+                mir[k] = (int32_t)lo;
+                mir[lo] = (int32_t)k;
+            } else {
+                mir[k] = -1;
+                atomicOr(bad, 1u);
+            }
+        }
+    }
 }
 
 // ---- state conversion -----------------------------------------------------------
@@ -808,6 +857,12 @@ void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B
 void sync_lcol_flags(const uint32_t *brk, int64_t B, uint16_t *lcol, cudaStream_t st)
 {
     k_sync_lcol_flags<<<grid_of(B), 256, 0, st>>>(brk, B, lcol);
+}
+
+void pair_index(const int64_t *rowptr, const int32_t *col, int64_t n, int32_t *split, int32_t *mir, unsigned *bad,
+                cudaStream_t st)
+{
+    k_pair_index<<<grid_of(n), 256, 0, st>>>(rowptr, col, n, split, mir, bad);
 }
 
 void sync_colf_flags(const uint32_t *brk, const int32_t *col, int64_t B, int32_t *colf, cudaStream_t st)

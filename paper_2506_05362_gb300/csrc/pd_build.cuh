@@ -69,3 +69,6 @@ void build_tiles(const int64_t *rowptr, const int32_t *col, int64_t n, int64_t B
                  int64_t *tile_ptr, uint16_t *lcol, uint16_t *lrow, cudaStream_t st);
 void sync_lcol_flags(const uint32_t *brk, int64_t B, uint16_t *lcol, cudaStream_t st);
 void sync_colf_flags(const uint32_t *brk, const int32_t *col, int64_t B, int32_t *colf, cudaStream_t st);
+// split (n) and mirror slots (B) of the each-bond-once passes; *bad |= 1 if a bond lacks its reverse
+void pair_index(const int64_t *rowptr, const int32_t *col, int64_t n, int32_t *split, int32_t *mir, unsigned *bad,
+                cudaStream_t st);

@@ -108,6 +108,13 @@ struct StepParams {
     uint16_t *lcol;                // bit 15 = broken (kept in step with brk)
     int32_t *colf;                 // mixed path: col with bit 31 = broken (kept in step with brk)
     const uint16_t *lrow;
+    // each bond once (mixed path): pass 1 evaluates the slots of row i whose
+    // neighbour index exceeds i and leaves the partner's factor at the mirror slot
+    int pairs;
+    const int32_t *split;          // per row: first slot whose neighbour index exceeds the row's
+    const int32_t *mir;            // per slot: the slot of the same bond in the neighbour's row
+    float *tb;                     // per slot: factor of the force term, written by pass 1
+    float4 *fup;                   // per row: pass 1's force from the row's own slots
 };
 
 #define PART_STRIDE 20  // 18 reaction components + max|v| + spare

@@ -354,6 +354,114 @@ __device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, i
     fbz = fmaf(g, yz, fbz);
 }
 
+// ---- Each bond once (mixed path, two passes) ---------------------------------
+// Eq. pmb is pairwise antisymmetric: with y the current bond vector from i to j,
+// the force density on i is c s V_j y/|y| and the one on j is -c s V_i y/|y|.  Pass
+// 1 evaluates every bond from its lower-index end i (the slots of row i whose
+// neighbour index is larger): it adds its own term and leaves the factor
+// c V_i s/|y| for j at the mirror slot (the same bond seen from j).  Pass 2 walks
+// each row's other slots, forms y from j's side (formed from the two records by
+// the same operations with the roles swapped, so it is exactly -y) and applies
+// the stored factor.  Every sum runs in a fixed order: results are reproducible.
+
+// y = x_j + u_j - x_i - u_i from the records of the row's node (o*) and the
+// neighbour (a*), operation by operation as in bond_mixed_flagged
+__device__ __forceinline__ void pair_y(const float4 &o0, const float4 &o1, const float4 &o2, const float *ol,
+                                       const float4 &a0, const float4 &a1, const float4 &a2, float2 &yxy, float &yz,
+                                       float2 &xxy, float &xz, float2 &exy, float &ez)
+{
+    float al[3];
+    xl_unpack(a1.w, a2.w, al);
+    xxy = __fadd2_rn(__fadd2_rn(make_float2(a0.x, a0.y), make_float2(-o0.x, -o0.y)),
+                     __fadd2_rn(make_float2(al[0], al[1]), make_float2(-ol[0], -ol[1])));
+    xz = (a0.z - o0.z) + (al[2] - ol[2]);
+    exy = __fadd2_rn(__fadd2_rn(make_float2(a1.x, a1.y), make_float2(-o1.x, -o1.y)),
+                     __fadd2_rn(make_float2(a2.x, a2.y), make_float2(-o2.x, -o2.y)));
+    ez = (a1.z - o1.z) + (a2.z - o2.z);
+    yxy = __fadd2_rn(xxy, exy);
+    yz = xz + ez;
+}
+
+// Pass 1, slot k of row i (neighbour j > i), mirror slot m: stretch, breaking of
+// both slots, the row's own term, and the partner's factor at tb[m].
+__device__ __forceinline__ void bond_pair_upper(const StepParams &p, int k, int m, int32_t raw, const float4 &o0,
+                                                const float4 &o1, const float4 &o2, const float *ol, const float4 &a0,
+                                                const float4 &a1, const float4 &a2, float &fbx, float &fby, float &fbz)
+{
+    float2 yxy, xxy, exy;
+    float yz, xz, ez;
+    pair_y(o0, o1, o2, ol, a0, a1, a2, yxy, yz, xxy, xz, exy, ez);
+    const float L2 = fmaf(xxy.x, xxy.x, fmaf(xxy.y, xxy.y, xz * xz));
+    const float y2 = fmaf(yxy.x, yxy.x, fmaf(yxy.y, yxy.y, yz * yz));
+    const float2 txy = __fadd2_rn(xxy, yxy);
+    const float num = fmaf(exy.x, txy.x, fmaf(exy.y, txy.y, ez * (xz + yz)));
+    const float rL = rsqrtf(L2), ry = rsqrtf(y2);
+    const float s = __fdividef(num * rL, fmaf(y2, ry, L2 * rL));
+    const bool intact = raw >= 0;
+    const bool brk = intact && (p.break_mode ? (fabsf(s) > p.s0f) : (s > p.s0f));
+    if (brk) {  // the bond memory of both directed slots, in both copies
+        p.colf[k] = (int32_t)((uint32_t)raw | 0x80000000u);
+        atomicOr((unsigned int *)p.colf + m, 0x80000000u);
+        atomicOr(p.brk + (k >> 5), 1u << (k & 31));
+        atomicOr(p.brk + (m >> 5), 1u << (m & 31));
+    }
+    float t = (intact && !brk) ? s * ry : 0.f;
+    if (p.conic) t *= p.delta_f - L2 * rL;
+    const float gi = a0.w * t;  // a0.w = c V_j
+    const float2 f = __ffma2_rn(make_float2(gi, gi), yxy, make_float2(fbx, fby));
+    fbx = f.x;
+    fby = f.y;
+    fbz = fmaf(gi, yz, fbz);
+    p.tb[m] = o0.w * t;  // o0.w = c V_i: the factor of j's term
+}
+
+// Pass 1: upper slots of every row; the row's partial force goes to fup.
+template <int G>
+__global__ void __launch_bounds__(STEP_THREADS, PD_MINB_GLOBAL) k_pairs_upper(const StepParams p)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
+        const int64_t row = r0 + grp;
+        float fbx = 0.f, fby = 0.f, fbz = 0.f;
+        if (row < p.n) {
+            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row),
+                         o2 = __ldg(p.ul_in + REC * row);
+            float ol[3];
+            xl_unpack(o1.w, o2.w, ol);
+            const int i0 = __ldg(p.split + row), i1 = (int)__ldg(p.rowptr + row + 1);
+            for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
+                int32_t raw[PD_INFLIGHT], mk[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    // a slot past the row end reuses the first slot's node and writes nothing
+                    const int kq = k + q * G;
+                    const bool ok = q == 0 || kq < i1;
+                    raw[q] = ok ? __ldg(p.colf + kq) : raw[0];
+                    mk[q] = ok ? __ldg(p.mir + kq) : -1;
+                }
+                float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
+                    a0[q] = __ldg(rj);
+                    a1[q] = __ldg(rj + 1);
+                    a2[q] = __ldg(rj + 2);
+                }
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q)
+                    if (mk[q] >= 0)
+                        bond_pair_upper(p, k + q * G, mk[q], raw[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby,
+                                        fbz);
+            }
+        }
+        fbx = group_sum<G>(fbx);
+        fby = group_sum<G>(fby);
+        fbz = group_sum<G>(fbz);
+        if (row < p.n && gl == 0) p.fup[row] = make_float4(fbx, fby, fbz, 0.f);
+    }
+}
+
 // u of node i in FP64: the double-float state of the mixed path, or the FP64 array
 template <bool MIXED>
 __device__ __forceinline__ dbl4 load_u_t(const StepParams &p, int64_t i)
@@ -506,6 +614,50 @@ __device__ __forceinline__ bool contact_term(const StepParams &p, int64_t q, con
     return true;
 }
 
+// Contact force density on `row` (Sec. 3.2 and the self-contact law, with the
+// pair damping and friction of Sec. 3.3).  The group's lanes evaluate the
+// candidates G at a time, and every lane adds the terms in list order through an
+// ordered shuffle chain.  The lists are sorted by partner index and a candidate
+// that does not touch adds exactly zero, so the result is the sum over the
+// touching pairs alone in ascending partner order: an evaluation at a given state
+// gives the same bits whichever rebuild (and skin superset) made the list.  All
+// lanes of the warp call it (inactive rows with active = false).
+template <int G, bool MIXED>
+__device__ __forceinline__ void contact_sum(const StepParams &p, int64_t row, bool active, int gl, double &cx,
+                                            double &cy, double &cz)
+{
+    cx = cy = cz = 0.0;
+    int64_t c0 = 0, c1 = 0;
+    if (active && p.contact) {
+        c0 = p.cand_ptr[row];
+        c1 = p.cand_ptr[row + 1];
+    }
+    const int nch = (int)((c1 - c0 + G - 1) / G);
+    const int nmax = __reduce_max_sync(0xffffffffu, nch);  // warp-uniform trip count
+    if (nmax == 0) return;
+    dbl4 ox = dbl4{0.0, 0.0, 0.0, 0.0};
+    double pix = 0.0, piy = 0.0, piz = 0.0;
+    int gi = 0;
+    if (nch > 0) {
+        ox = p.x4[row];
+        const dbl4 ou = load_u_t<MIXED>(p, row);
+        pix = dadd(ox.x, ou.x); piy = dadd(ox.y, ou.y); piz = dadd(ox.z, ou.z);
+        gi = p.grain[row];
+    }
+    const double R2 = dmul(p.Rc, p.Rc);
+    for (int t = 0; t < nmax; ++t) {
+        const int64_t q = c0 + (int64_t)t * G + gl;
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        if (q < c1 && !contact_term<MIXED>(p, q, ox, pix, piy, piz, gi, R2, gx, gy, gz)) gx = gy = gz = 0.0;
+#pragma unroll
+        for (int l = 0; l < G; ++l) {
+            cx += __shfl_sync(0xffffffffu, gx, l, G);
+            cy += __shfl_sync(0xffffffffu, gy, l, G);
+            cz += __shfl_sync(0xffffffffu, gz, l, G);
+        }
+    }
+}
+
 // velocity of node i in FP64 (double-float pair on the mixed path)
 template <bool MIXED>
 __device__ __forceinline__ void load_v_t(const StepParams &p, int64_t i, double &vx, double &vy, double &vz)
@@ -603,7 +755,7 @@ struct TileView {
 
 // Steps 1-4 for one row owned by a group of G lanes (all lanes call; inactive
 // groups pass active = false and still join the shuffles).
-template <int G, bool MIXED, bool WX = false>
+template <int G, bool MIXED, bool WX = false, bool PAIRS = false>
 __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bool active, int gl, int lrow,
                                             const TileView &tv, double *react, unsigned &err, float &vmax2f,
                                             double &vmax2)
@@ -614,7 +766,44 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
     double fdx = 0.0, fdy = 0.0, fdz = 0.0;
     if (active) {
         const int64_t k0 = p.rowptr[row], k1 = p.rowptr[row + 1];
-        if (MIXED) {
+        if (PAIRS) {
+            // pass 2: the slots whose bond pass 1 evaluated from the other end
+            // (neighbour index below the row's); their factors are in tb
+            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row),
+                         o2 = __ldg(p.ul_in + REC * row);
+            float ol[3];
+            xl_unpack(o1.w, o2.w, ol);
+            const int i0 = (int)k0, i1 = __ldg(p.split + row);
+            for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
+                int32_t raw[PD_INFLIGHT];
+                float g[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    const int kq = k + q * G;
+                    const bool ok = q == 0 || kq < i1;
+                    raw[q] = ok ? __ldg(p.colf + kq) : raw[0];
+                    g[q] = ok ? __ldcs(p.tb + kq) : 0.f;
+                }
+                float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
+                    a0[q] = __ldg(rj);
+                    a1[q] = __ldg(rj + 1);
+                    a2[q] = __ldg(rj + 2);
+                }
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT; ++q) {
+                    float2 yxy, xxy, exy;
+                    float yz, xz, ez;
+                    pair_y(o0, o1, o2, ol, a0[q], a1[q], a2[q], yxy, yz, xxy, xz, exy, ez);
+                    const float2 f = __ffma2_rn(make_float2(g[q], g[q]), yxy, make_float2(fbx, fby));
+                    fbx = f.x;
+                    fby = f.y;
+                    fbz = fmaf(g[q], yz, fbz);
+                }
+            }
+        } else if (MIXED) {
             const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row), o2 = __ldg(p.ul_in + REC * row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
@@ -665,30 +854,27 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
         }
     }
     __syncwarp();
-    // ---- 2. contact candidates (FP64, exact predicate)
-    if (active && p.contact) {
-        const int64_t c0 = p.cand_ptr[row], c1 = p.cand_ptr[row + 1];
-        if (c1 > c0) {
-            const dbl4 ox = p.x4[row], ou = load_u(p, row);
-            const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
-            const int gi = p.grain[row];
-            const double R2 = dmul(p.Rc, p.Rc);
-            for (int64_t q = c0 + gl; q < c1; q += G) {
-                double gx, gy, gz;
-                if (!contact_term<MIXED>(p, q, ox, pix, piy, piz, gi, R2, gx, gy, gz)) continue;
-                if (MIXED) {  // FP32 accumulators of the mixed path
-                    fbx += (float)gx; fby += (float)gy; fbz += (float)gz;
-                } else {
-                    fdx += gx; fdy += gy; fdz += gz;
-                }
-            }
-        }
-    }
-    // ---- 3. combine the group
+    // ---- 2. contact candidates (FP64, exact predicate, ordered sum)
+    double cx, cy, cz;
+    contact_sum<G, MIXED>(p, row, active, gl, cx, cy, cz);
+    // ---- 3. combine the group, then add pass 1's part (each bond once) and the contact sum
     if (MIXED) {
-        fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
+        fbx = group_sum<G>(fbx);
+        fby = group_sum<G>(fby);
+        fbz = group_sum<G>(fbz);
+        if (PAIRS && active) {
+            const float4 up = p.fup[row];
+            fbx += up.x;
+            fby += up.y;
+            fbz += up.z;
+        }
+        fbx += (float)cx;
+        fby += (float)cy;
+        fbz += (float)cz;
     } else {
-        fdx = group_sum<G>(fdx); fdy = group_sum<G>(fdy); fdz = group_sum<G>(fdz);
+        fdx = group_sum<G>(fdx) + cx;
+        fdy = group_sum<G>(fdy) + cy;
+        fdz = group_sum<G>(fdz) + cz;
     }
     // ---- 4. walls and Verlet update (group leader)
     if (MIXED) {
@@ -804,7 +990,7 @@ __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_rea
 
 // Rows in a grid-stride loop, neighbour records gathered from global memory
 // (FP64 path, and the mixed path without tiles).
-template <int G, bool MIXED, bool WX>
+template <int G, bool MIXED, bool WX, bool PAIRS = false>
 __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_step(const StepParams p)
 {
     constexpr int GPB = STEP_THREADS / G;
@@ -827,7 +1013,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_st
     const TileView tv{nullptr, nullptr, nullptr, false};
     for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
         const int64_t row = r0 + grp;
-        process_row<G, MIXED, WX>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
+        process_row<G, MIXED, WX, PAIRS>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
     }
     if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
     block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
@@ -850,8 +1036,10 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
     __shared__ bool s_last;
     const int T = p.tile_rows, cap = p.tile_cap;
     float4 *r0s = s_rec, *r1s = r0s + cap, *r2s = r1s + cap, *vhs = r2s + cap, *vls = vhs + T;
-    int64_t *rps = (int64_t *)(vls + T), *cps = rps + T + 1;
-    uint16_t *lrs = (uint16_t *)(cps + T + 1);
+    // row pointers: T + 1 entries, padded to an even count so that the 16-bit
+    // arrays after them (filled with 16-byte stores) start 16-byte aligned
+    int64_t *rps = (int64_t *)(vls + T);
+    uint16_t *lrs = (uint16_t *)(rps + ((T + 2) & ~1));
     uint16_t *lcs = lrs + ((T + 7) & ~7);
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
     if (gl == 0) {
@@ -879,10 +1067,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             const int nch = (int)((kend - ka + 7) >> 3);
             const uint4 *src = (const uint4 *)(p.lcol + ka);
             for (int q = threadIdx.x; q < nch; q += STEP_THREADS) ((uint4 *)lcs)[q] = src[q];
-            for (int q = threadIdx.x; q <= rows; q += STEP_THREADS) {
-                rps[q] = __ldg(p.rowptr + r0 + q);
-                cps[q] = p.contact ? __ldg(p.cand_ptr + r0 + q) : 0;
-            }
+            for (int q = threadIdx.x; q <= rows; q += STEP_THREADS) rps[q] = __ldg(p.rowptr + r0 + q);
             for (int q = threadIdx.x; q < rows; q += STEP_THREADS) {
                 vhs[q] = p.vh[r0 + q];
                 vls[q] = p.vl[r0 + q];
@@ -931,22 +1116,12 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
                 }
             }
             __syncwarp();
-            // contact candidates (rare; FP64 from global memory)
-            if (active && p.contact) {
-                const int64_t c0 = cps[rr], c1 = cps[rr + 1];
-                if (c1 > c0) {
-                    const dbl4 ox = p.x4[row], ou = load_u_t<true>(p, row);
-                    const double pix = dadd(ox.x, ou.x), piy = dadd(ox.y, ou.y), piz = dadd(ox.z, ou.z);
-                    const int gi = p.grain[row];
-                    const double R2 = dmul(p.Rc, p.Rc);
-                    for (int64_t q = c0 + gl; q < c1; q += G) {
-                        double gx, gy, gz;
-                        if (!contact_term<true>(p, q, ox, pix, piy, piz, gi, R2, gx, gy, gz)) continue;
-                        fbx += (float)gx; fby += (float)gy; fbz += (float)gz;
-                    }
-                }
-            }
-            fbx = group_sum<G>(fbx); fby = group_sum<G>(fby); fbz = group_sum<G>(fbz);
+            // contact candidates (rare; FP64 from global memory, ordered sum)
+            double cx, cy, cz;
+            contact_sum<G, true>(p, row, active, gl, cx, cy, cz);
+            fbx = group_sum<G>(fbx) + (float)cx;
+            fby = group_sum<G>(fby) + (float)cy;
+            fbz = group_sum<G>(fbz) + (float)cz;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             err |= epilogue_lanes<G, false>(p, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
                                      active ? o2 : z4, active ? vhs[rr] : z4, active ? vls[rr] : z4, s_react[grp],
@@ -1056,6 +1231,9 @@ void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
             k_step<G, true, true><<<blocks, STEP_THREADS, 0, st>>>(p);
         else
             k_step<G, false, true><<<blocks, STEP_THREADS, 0, st>>>(p);
+    } else if (mixed && p.pairs) {  // each bond once: pass 1, then pass 2 with the update
+        k_pairs_upper<G><<<blocks, STEP_THREADS, 0, st>>>(p);
+        k_step<G, true, false, true><<<blocks, STEP_THREADS, 0, st>>>(p);
     } else if (mixed && p.tile_cap > 0) {
         const size_t smem = tiled_smem(p.tile_cap, p.tile_rows, p.tile_slot_cap);
         k_step_tiled<G><<<blocks, STEP_THREADS, smem, st>>>(p);
@@ -1087,7 +1265,7 @@ int blocks_g(int sms, bool mixed, bool tiled, size_t smem)
 // bytes of dynamic shared memory of k_step_tiled
 size_t tiled_smem(int tile_cap, int tile_rows, int slot_cap)
 {
-    return (size_t)(3 * tile_cap + 2 * tile_rows) * sizeof(float4) + (size_t)2 * (tile_rows + 1) * sizeof(int64_t) +
+    return (size_t)(3 * tile_cap + 2 * tile_rows) * sizeof(float4) + (size_t)((tile_rows + 2) & ~1) * sizeof(int64_t) +
            (size_t)((tile_rows + 7) & ~7) * 2 + (size_t)(slot_cap + 16) * 2;
 }
 

@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("contact", ctypes.c_int), ("contact_every", ctypes.c_int), ("skin", ctypes.c_double),
                 ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("cand_capacity", ctypes.c_int64)]
+                ("cand_capacity", ctypes.c_int64), ("pairs", ctypes.c_int)]
 
 
 class Wall(ctypes.Structure):
@@ -340,10 +340,12 @@ def pack_broken(broken):
 
 
 def pd_tuning(h):
-    lanes, tiled = ctypes.c_int(), ctypes.c_int()
-    ms = np.zeros(8)
-    _check(lib().pd_tuning(h, ctypes.byref(lanes), ctypes.byref(tiled), _ptr(ms)), h)
-    return lanes.value, bool(tiled.value), ms
+    """(lanes per node, kernel: 0 global gathers / 1 tiles / 2 each bond once,
+    ms per candidate: 4 lane counts for each kernel in that order)."""
+    lanes, kernel = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(12)
+    _check(lib().pd_tuning(h, ctypes.byref(lanes), ctypes.byref(kernel), _ptr(ms)), h)
+    return lanes.value, kernel.value, ms
 
 
 def pd_step_counters(h):
@@ -385,7 +387,7 @@ class Context:
 
     def __init__(self, x, vol, grain, material, v0=None, precision="mixed", contact=True,
                  contact_every=0, skin=0.0, lanes=0, chunk=64, device=0, stream=None,
-                 torch_memory=True, tiles=0, cand_capacity=0, allocator=None):
+                 torch_memory=True, tiles=0, cand_capacity=0, allocator=None, pairs=0):
         import torch
         m = material
         self.material = Material(m.E, m.rho, m.G0, m.contact_radius, m.contact_factor, m.constants,
@@ -412,6 +414,7 @@ class Context:
         o.graph_chunk = chunk
         o.tiles = tiles
         o.cand_capacity = int(cand_capacity)
+        o.pairs = int(pairs)
         self.options = o
         self.n = int(np.asarray(x).reshape(-1, 3).shape[0])
         self.h = pd_create(x, vol, grain, self.material, o, v0)
@@ -485,7 +488,7 @@ class Context:
         pd_set_state(self.h, u, v, broken, t)
 
     def tuning(self):
-        """(lanes per node, tiles chosen, ms per candidate: 4 global then 4 tiled)."""
+        """(lanes per node, kernel chosen, ms per candidate; see pd_tuning)."""
         return pd_tuning(self.h)
 
     def set_profiling(self, on):

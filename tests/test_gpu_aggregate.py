@@ -87,8 +87,10 @@ def test_aggregate_forces_sampled(agg):
 
 def test_aggregate_steps_finite_and_tuned(agg):
     sc, ctx = agg
-    lanes, tiled, ms = ctx.tuning()
-    assert lanes in (4, 8, 16, 32)
+    lanes, kernel, ms = ctx.tuning()
+    assert lanes in (4, 8, 16, 32) and kernel in (0, 1, 2)
+    # the chosen candidate is the fastest one measured
+    assert ms[4 * kernel + (4, 8, 16, 32).index(lanes)] == min(t for t in ms if t > 0)
     ctx.set_state(u=np.zeros_like(sc.x), v=sc.v0)
     dt = 0.8 * ctx.stable_dt()
     ctx.step(dt, 50)

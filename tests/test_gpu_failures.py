@@ -126,11 +126,13 @@ def test_candidate_list_regrows_and_trajectory_holds(pd):
 
 def test_stale_contact_list_rolls_back_and_trajectory_holds(pd):
     """A rebuild period far too long for a thin skin (40 steps; skin 2% of R_c, so
-    a node at 5 m/s uses up half the skin in ~14 steps): the device flags the
-    stale list, the segment is rolled back and rerun with a shorter period, and
-    the trajectory equals the oracle's, which rebuilds every step."""
+    a node at 5 m/s uses up half the skin in ~14 steps), in calls of 50 steps
+    (each call rebuilds at its start): the device flags the stale list, the
+    segment is rolled back and rerun with a shorter period, and the trajectory
+    equals the oracle's, which rebuilds every step."""
     sc = colliding_pair()
-    ctx, ref = run_collision(pd, sc, contact_every=40, skin=0.02 * sc.material.contact_radius)
+    ctx, ref = run_collision(pd, sc, steps_per_call=50, after_touch=100, contact_every=40,
+                             skin=0.02 * sc.material.contact_radius)
     steps, rebuilds, rollbacks = ctx.step_counters()
     assert rollbacks > 0
     assert rebuilds > steps / 40
