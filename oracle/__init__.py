@@ -19,21 +19,26 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pd_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liborc.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liborc_omp.so")  # the same source with OpenMP (timing only)
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 ERR_NONFINITE = 1
 ERR_WALL = 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math."""
+    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math; once
+    serial (liborc.so, the checker) and once with OpenMP over the node loops
+    (liborc_omp.so, same arithmetic per node, for the all-core CPU baseline)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    for out, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+            tmp = out + f".{os.getpid()}.tmp"
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", *extra,
+                                   "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, out)
     return _LIB
 
 
@@ -49,38 +54,55 @@ class Problem(ctypes.Structure):
                 ("mu", ctypes.c_double), ("dt_f", ctypes.c_double), ("wall_overlap", ctypes.c_int)]
 
 
-def lib():
-    global _lib
+def lib(parallel: bool = False):
+    """The serial oracle library, or (parallel=True) its OpenMP build."""
+    global _lib, _lib_omp
     with _lock:
+        if parallel:
+            if _lib_omp is None:
+                build()
+                _lib_omp = _bind(ctypes.CDLL(_LIB_OMP))
+            return _lib_omp
         if _lib is None:
-            L = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
-            L.orc_constants.argtypes = [f64, f64, f64, f64, i32, i32, P]
-            L.orc_ball_cut.argtypes = [f64, f64, f64, f64, P]
-            L.orc_ball_cut.restype = None
-            L.orc_bond_row.argtypes = [i64, P, P, f64, i32, P, P, i64, P]
-            L.orc_bond_row.restype = i64
-            L.orc_bonds_brute.argtypes = [i64, P, P, f64, i32, P, P, P, P]
-            L.orc_bonds_brute.restype = i64
-            L.orc_bonds_cells.argtypes = [i64, P, P, f64, i32, P, P, P, P]
-            L.orc_bonds_cells.restype = i64
-            L.orc_contact_pairs.argtypes = [P, P, P, i32, P]
-            L.orc_contact_pairs.restype = i64
-            L.orc_forces.argtypes = [P, P, P, P, P, P, P]
-            L.orc_forces.restype = i32
-            L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P, P]
-            L.orc_step.restype = i32
-            L.orc_stable_dt.argtypes = [P]
-            L.orc_stable_dt.restype = f64
-            L.orc_damage.argtypes = [i64, P, P, P]
-            L.orc_fragments.argtypes = [i64, P, P, P, P]
-            L.orc_fragments.restype = i64
-            L.orc_fragment_stats.argtypes = [i64, P, P, P, P, i64, P, P, P]
-            L.orc_energy.argtypes = [P, P, P, P]
-            L.orc_energy.restype = f64
-            _lib = L
+            _lib = _bind(ctypes.CDLL(build()))
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Threads of the OpenMP build; returns the number it will use."""
+    return int(lib(parallel=True).orc_set_threads(int(k)))
+
+
+def _bind(L):
+    """Argument and result types of every oracle entry point."""
+    P = ctypes.c_void_p
+    i64, f64, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    L.orc_constants.argtypes = [f64, f64, f64, f64, i32, i32, P]
+    L.orc_ball_cut.argtypes = [f64, f64, f64, f64, P]
+    L.orc_ball_cut.restype = None
+    L.orc_bond_row.argtypes = [i64, P, P, f64, i32, P, P, i64, P]
+    L.orc_bond_row.restype = i64
+    L.orc_bonds_brute.argtypes = [i64, P, P, f64, i32, P, P, P, P]
+    L.orc_bonds_brute.restype = i64
+    L.orc_bonds_cells.argtypes = [i64, P, P, f64, i32, P, P, P, P]
+    L.orc_bonds_cells.restype = i64
+    L.orc_contact_pairs.argtypes = [P, P, P, i32, P]
+    L.orc_contact_pairs.restype = i64
+    L.orc_forces.argtypes = [P, P, P, P, P, P, P]
+    L.orc_forces.restype = i32
+    L.orc_step.argtypes = [P, P, P, P, P, P, f64, i64, P, P, P]
+    L.orc_step.restype = i32
+    L.orc_stable_dt.argtypes = [P]
+    L.orc_stable_dt.restype = f64
+    L.orc_damage.argtypes = [i64, P, P, P]
+    L.orc_fragments.argtypes = [i64, P, P, P, P]
+    L.orc_fragments.restype = i64
+    L.orc_fragment_stats.argtypes = [i64, P, P, P, P, i64, P, P, P]
+    L.orc_energy.argtypes = [P, P, P, P]
+    L.orc_energy.restype = f64
+    L.orc_set_threads.argtypes = [i32]
+    L.orc_set_threads.restype = i32
+    return L
 
 
 def _p(a):
@@ -163,7 +185,8 @@ class Model:
     directed slot), wall positions and time."""
 
     def __init__(self, x, vol, grain, rowptr, col, material, horizon, walls=None,
-                 body_force=(0.0, 0.0, 0.0), v0=None, contact=True):
+                 body_force=(0.0, 0.0, 0.0), v0=None, contact=True, parallel=False):
+        self.L = lib(parallel)  # the OpenMP build only times the CPU baseline
         self.x = np.ascontiguousarray(x, np.float64)
         self.vol = np.ascontiguousarray(vol, np.float64)
         self.grain = np.ascontiguousarray(grain, np.int32)
@@ -205,7 +228,7 @@ class Model:
         self.acc = np.zeros((n, 3))
 
     @classmethod
-    def from_scenario(cls, sc, rowptr=None, col=None, contact=True):
+    def from_scenario(cls, sc, rowptr=None, col=None, contact=True, parallel=False):
         from_sc = sc
         if rowptr is None:
             kinds = [k for k, _ in from_sc.filters]
@@ -214,7 +237,7 @@ class Model:
         walls = np.array([list(w.normal) + list(w.point) + list(w.velocity) for w in sc.walls],
                          np.float64).reshape(-1, 9)
         return cls(sc.x, sc.vol, sc.grain, rowptr, col, sc.material, sc.horizon, walls,
-                   sc.body_force, sc.v0, contact)
+                   sc.body_force, sc.v0, contact, parallel)
 
     @property
     def n(self):
@@ -224,7 +247,7 @@ class Model:
         """F at the current state, sets react; returns F.  Applies breaking unless
         frozen, which evaluates with the current bond memory unchanged."""
         self.P.frozen = 1 if frozen else 0
-        self.err |= lib().orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.wall_pos),
+        self.err |= self.L.orc_forces(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.wall_pos),
                                      _p(self.broken), _p(self.F), _p(self.react))
         self.P.frozen = 0
         return self.F
@@ -240,7 +263,7 @@ class Model:
             # the friction's stick branch depends on dt: a(t) is evaluated again with it
             self.P.dt_f = dt
             self.init()
-        self.err |= lib().orc_step(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.acc),
+        self.err |= self.L.orc_step(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.acc),
                                    _p(self.broken), _p(self.wall_pos), dt, nsteps, _p(self.F),
                                    _p(self.react), _p(self.impulse))
         self.t += dt * nsteps
@@ -249,11 +272,11 @@ class Model:
         return self
 
     def stable_dt(self):
-        return float(lib().orc_stable_dt(ctypes.byref(self.P)))
+        return float(self.L.orc_stable_dt(ctypes.byref(self.P)))
 
     def damage(self):
         phi = np.zeros(self.n)
-        lib().orc_damage(self.n, _p(self.rowptr), _p(self.broken), _p(phi))
+        self.L.orc_damage(self.n, _p(self.rowptr), _p(self.broken), _p(phi))
         return phi
 
     def fragments(self):
@@ -266,13 +289,13 @@ class Model:
         return fragment_stats(self.rowptr, self.broken, self.vol, label, nf)
 
     def energy(self):
-        return float(lib().orc_energy(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.broken)))
+        return float(self.L.orc_energy(ctypes.byref(self.P), _p(self.u), _p(self.v), _p(self.broken)))
 
     def contact_pairs(self, brute=False):
         """(m,2) int32 ordered contact pairs at the current state, sorted."""
-        cnt = lib().orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), None)
+        cnt = self.L.orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), None)
         pr = np.zeros((max(cnt, 1), 2), np.int32)
-        lib().orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), _p(pr))
+        self.L.orc_contact_pairs(ctypes.byref(self.P), _p(self.u), _p(self.broken), int(brute), _p(pr))
         return pr[:cnt].copy()
 
     def bulk_stress(self, areas):

@@ -45,6 +45,23 @@
 #define ORC_FILTER_NOTCH 1
 #define ORC_FILTER_SPHERE 2
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the OpenMP build (the timed CPU baseline on all host cores); the
+ * serial build ignores it and reports 1. */
+int orc_set_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+    return omp_get_max_threads();
+#else
+    (void)k;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------- */
 /* Material constants.                                                       */
 /* ------------------------------------------------------------------------- */
@@ -711,7 +728,12 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
     for (int l = 0; l < 3 * P->nw; ++l) react[l] = 0.0;
 
     /* 1. bonds for all rows (each row decides its own slots; a bond's two
-     *    directions see negated xi, eta and therefore decide identically) */
+     *    directions see negated xi, eta and therefore decide identically).  Rows
+     *    write only their own F and slots, so the OpenMP build (for timing on all
+     *    host cores) gives the same bits as the serial one. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int64_t i = 0; i < n; ++i) {
         double f[3] = {0.0, 0.0, 0.0};
         for (int64_t k = P->rowptr[i]; k < P->rowptr[i + 1]; ++k) {
@@ -734,14 +756,24 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
         for (int a = 0; a < 3; ++a) F[3 * i + a] = f[a];
     }
 
-    /* 2. contact, after every row has updated its bond memory */
+    /* 2. contact, after every row has updated its bond memory (rows again write
+     *    only their own F; each thread has its own scratch lists) */
     if (P->contact) {
         orc_grid g;
         orc_grid_build(&g, n, p, P->Rc);
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+        {
+        int64_t *tbuf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        int64_t *tnb = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 256)
+#endif
         for (int64_t i = 0; i < n; ++i) {
-            int64_t m = orc_contacts_of(P, p, broken, &g, i, buf, nb);
+            int64_t m = orc_contacts_of(P, p, broken, &g, i, tbuf, tnb);
             for (int64_t t = 0; t < m; ++t) {
-                int64_t j = nb[t];
+                int64_t j = tnb[t];
                 double d[3], xi[3];
                 for (int a = 0; a < 3; ++a) {
                     d[a] = p[3 * j + a] - p[3 * i + a];
@@ -784,10 +816,12 @@ int orc_forces(const orc_problem *P, const double *u, const double *v, const dou
                 }
             }
         }
+        free(tbuf); free(tnb);
+        }
         orc_grid_free(&g);
     }
 
-    /* 3. walls */
+    /* 3. walls (serial: the wall reactions are summed in caller order) */
     for (int64_t i = 0; i < n; ++i) {
         for (int l = 0; l < P->nw; ++l) {
             const double *nl = P->walls + 9 * l;
@@ -857,6 +891,9 @@ int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *b
     int err = 0;
     double hdt = 0.5 * dt;
     for (int64_t s = 0; s < nsteps; ++s) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t i = 0; i < 3 * n; ++i) {
             v[i] = v[i] + hdt * acc[i];
             u[i] = u[i] + dt * v[i];
@@ -871,6 +908,9 @@ int orc_step(const orc_problem *P, double *u, double *v, double *acc, uint8_t *b
         err |= orc_forces(&Q, u, v, wall_pos, broken, F, react);
         if (impulse)
             for (int l = 0; l < 3 * P->nw; ++l) impulse[l] += dt * react[l];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
         for (int64_t i = 0; i < n; ++i)
             for (int a = 0; a < 3; ++a) {
                 acc[3 * i + a] = (F[3 * i + a] + P->b[a]) / P->rho;

@@ -683,3 +683,32 @@ def test_self_contact_spring_branch_beyond_contact_radius():
     F = m.forces(frozen=True)
     assert F[0, 0] == pytest.approx(-Kn * (mat.contact_radius - d) * 1e-12, rel=1e-12)
     assert F[1, 0] == pytest.approx(-F[0, 0], rel=1e-15)
+
+
+# --------------------------------------------------------------------------- OpenMP build
+def test_openmp_build_gives_the_same_bits():
+    """The OpenMP build of the oracle (timed as the all-core CPU baseline) runs
+    the same per-node arithmetic: forces with contacts and breaking, and a short
+    trajectory, are bit-identical to the serial build's."""
+    sc = S.aggregate(n_grains=3, h=0.5e-3 / 4, gap_cells=0.2, seed=3)
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-0.5, 0.5, (sc.n, 3)) * sc.h
+    out = []
+    threads = oracle.set_threads(4)
+    assert threads == 4
+    for par in (False, True):
+        m = oracle.Model.from_scenario(sc, parallel=par)
+        # a third of the undirected bonds broken (both slots), so that fragments touch
+        rows = np.repeat(np.arange(sc.n), np.diff(m.rowptr))
+        key = np.minimum(rows, m.col).astype(np.int64) * (sc.n + 1) + np.maximum(rows, m.col)
+        uniq, inv = np.unique(key, return_inverse=True)
+        m.broken[:] = (np.random.default_rng(2).random(len(uniq)) < 0.3)[inv]
+        m.u = u.copy()
+        F = m.forces().copy()
+        pairs = len(m.contact_pairs())
+        m.init()
+        m.step(0.5 * m.stable_dt(), 5)
+        out.append((F, m.broken.copy(), m.u.copy(), m.v.copy(), m.react.copy(), pairs))
+    assert out[0][5] > 0 and out[0][1].sum() > 0
+    for a, b in zip(out[0][:5], out[1][:5]):
+        assert np.array_equal(a, b)
