@@ -282,12 +282,15 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
  * error and re-evaluates the forces (which may break bonds).  u and v are
  * checked on the device before anything is applied: a non-finite value in
  * either returns PD_EINVAL and leaves the whole state unchanged.  Every given
- * part is also compared on the device with the current state; when all of them
- * equal it (a state that pd_get_state returned, sent back unchanged), nothing
- * is applied and the force evaluation is skipped: the acceleration stored with
- * the current state is kept, so the call leaves the trajectory bit for bit as
- * if it had not been made.  The wall impulses of pd_bulk_stress_mean are zeroed
- * in either case.  Errors: PD_EINVAL (non-finite u or v), PD_ESTATE (bond
+ * part is also compared on the device with the current state; when applying it
+ * would leave the state bit for bit as it is (a state that pd_get_state
+ * returned, sent back unchanged) and the material has no velocity-dependent
+ * forces (beta_d = 0, mu = 0), nothing is applied and the force evaluation is
+ * skipped: the stored acceleration is the one an evaluation at this state gives,
+ * so the call leaves the trajectory bit for bit as it would have been.  With
+ * damping or friction the forces are always evaluated again (the stored
+ * acceleration saw the last step's half-step velocity, the evaluation sees the
+ * current one).  The wall impulses of pd_bulk_stress_mean are zeroed in any case.  Errors: PD_EINVAL (non-finite u or v), PD_ESTATE (bond
  * memory before pd_build_bonds), PD_ECUDA, and those of the force evaluation. */
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
@@ -327,8 +330,8 @@ pd_status pd_last_step_stats(pd_ctx *ctx, double *ms_force, double *ms_total, in
 pd_status pd_step_counters(pd_ctx *ctx, int64_t *steps, int64_t *rebuilds, int64_t *rollbacks);
 
 /* pd_set_state / pd_set_state_packed calls since pd_create (each pointer
- * nullable): applied (the state differed and the forces were evaluated again)
- * and unchanged (the state equalled the current one; nothing was applied). */
+ * nullable): applied (the forces were evaluated again) and unchanged (the state
+ * equalled the current one and the evaluation was skipped). */
 pd_status pd_state_counters(pd_ctx *ctx, int64_t *applied, int64_t *unchanged);
 
 const char *pd_last_error(const pd_ctx *ctx);

@@ -1469,10 +1469,13 @@ static pd_status get_state_impl(pd_ctx *c, double *u, double *v, uint8_t *broken
 }
 
 // Applies a caller state.  Everything given is staged and compared on the device
-// with the current state first: non-finite u or v rejects the call; a state
-// equal to the current one in every given part (what pd_get_state returned, sent
-// back unchanged) is not applied again, and its force evaluation is skipped, since
-// the stored acceleration already belongs to it.
+// with the current state first: non-finite u or v rejects the call; a state that
+// applying would leave bit for bit as it is (what pd_get_state returned, sent back
+// unchanged) is not applied again, and, for a material without velocity-dependent
+// forces, its force evaluation is skipped, since the stored acceleration is the
+// one an evaluation at this state gives.  With damping or friction the stored
+// acceleration saw the half-step velocity of the last step, so it is evaluated
+// again.
 static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, const uint8_t *broken,
                                 const uint32_t *bits, const double *t)
 {
@@ -1541,8 +1544,10 @@ static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, con
     CK(reset_impulse(c));
     pd_status s = sync(c);
     if (s) return s;
-    ++(changed ? c->n_state_applied : c->n_state_unchanged);
-    if (c->bonds_ready && changed) return eval_forces(c);
+    const bool velocity_forces = c->mat.beta_d > 0 || c->mat.mu > 0;
+    const bool skip = !changed && !velocity_forces;
+    ++(skip ? c->n_state_unchanged : c->n_state_applied);
+    if (c->bonds_ready && !skip) return eval_forces(c);
     return PD_OK;
 }
 

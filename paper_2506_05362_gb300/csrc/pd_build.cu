@@ -557,9 +557,18 @@ __global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
-// flag |= bit when the caller-order doubles `staged` differ from the current
-// state: the double-float pairs (hi, lo) at stride `stride` when hi is given
-// (each converted by the formula every query uses), else the FP64 array d64
+// true unless the double-float pair (h, l) is bit for bit the split of x that
+// applying x would store
+__device__ __forceinline__ bool pair_differs(double x, float h, float l)
+{
+    const df s = df_from_double(x);
+    return (__float_as_uint(s.hi) != __float_as_uint(h)) | (__float_as_uint(s.lo) != __float_as_uint(l));
+}
+
+// flag |= bit when applying the caller-order doubles `staged` would change the
+// current state: on the mixed path the double-float pairs (hi, lo) at stride
+// `stride` are compared bit for bit with the split of the staged values, else the
+// FP64 array d64 with the values themselves (bit for bit)
 __global__ void k_state_differs(const double *__restrict__ staged, const int32_t *__restrict__ perm, int64_t n,
                                 const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride,
                                 const dbl4 *__restrict__ d64, unsigned bit, unsigned *flag)
@@ -567,17 +576,16 @@ __global__ void k_state_differs(const double *__restrict__ staged, const int32_t
     bool diff = false;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[k];
-        double a, b, c;
         if (hi) {
             const float4 h = hi[stride * k], l = lo[stride * k];
-            a = df_to_double(df{h.x, l.x});
-            b = df_to_double(df{h.y, l.y});
-            c = df_to_double(df{h.z, l.z});
+            diff |= pair_differs(staged[3 * i], h.x, l.x) | pair_differs(staged[3 * i + 1], h.y, l.y) |
+                    pair_differs(staged[3 * i + 2], h.z, l.z);
         } else {
             const dbl4 q = d64[k];
-            a = q.x; b = q.y; c = q.z;
+            diff |= (__double_as_longlong(q.x) != __double_as_longlong(staged[3 * i])) |
+                    (__double_as_longlong(q.y) != __double_as_longlong(staged[3 * i + 1])) |
+                    (__double_as_longlong(q.z) != __double_as_longlong(staged[3 * i + 2]));
         }
-        diff |= (a != staged[3 * i]) | (b != staged[3 * i + 1]) | (c != staged[3 * i + 2]);
     }
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
