@@ -42,6 +42,17 @@ WORKLOADS = {
 }
 
 
+def cpu_sample(name, sc):
+    """The workload the CPU baseline times: the full workload up to ~1 M nodes; for
+    the 1000-grain aggregate a 64-grain aggregate of the same recipe (same grain
+    shapes, h, material and box loading), so that the oracle's set-up and steps
+    stay within a minute."""
+    from paper_2506_05362_gb300 import scenarios as S
+    if name == "aggregate":
+        return S.aggregate(n_grains=64, seed=0), "64-grain aggregate of the same recipe"
+    return sc, f"the full {name} workload"
+
+
 def make_workload(name):
     from paper_2506_05362_gb300 import scenarios as S
     return {"plate": S.kalthoff, "sphere": S.sphere, "hollow": S.hollow,
@@ -188,11 +199,12 @@ def run_reference(args):
 
 
 def cpu_baseline(sc, name="plate"):
-    """The oracle on a bounded sample of the full workload (8 steps; 1 above ~1 M
-    nodes): its OpenMP build on all host cores (the reported value), and the
-    serial build on one core beside it.  Both builds give the same bits."""
+    """The oracle on a bounded sample of the workload (8 steps; see cpu_sample): its
+    OpenMP build on all host cores (the reported value), and the serial build on
+    one core beside it.  Both builds give the same bits."""
     import oracle
-    steps = 8 if sc.n < 1_000_000 else 1
+    sc, what = cpu_sample(name, sc)
+    steps = 8
     cores = oracle.set_threads(host_cores())
     rates = {}
     for par in (True, False):
@@ -204,7 +216,7 @@ def cpu_baseline(sc, name="plate"):
         el = time.perf_counter() - t0
         rates[par] = (sc.n * steps / el, len(m.col) * steps / el)
     return {"value": rates[True][0], "unit": "node-steps/s", "cores": cores, "kind": "oracle",
-            "sample": (f"{steps} steps of the full {name} workload; FP64 C oracle, OpenMP build over the node "
+            "sample": (f"{steps} steps of {what} ({sc.n} nodes); FP64 C oracle, OpenMP build over the node "
                        f"loops on {cores} host cores (sched_getaffinity)"),
             "bond_updates_per_s": rates[True][1],
             "single_core": {"value": rates[False][0], "unit": "node-steps/s", "cores": 1,
@@ -300,12 +312,15 @@ def main():
             "traffic": None, "kernel": "k_step (fused bond force + contact + walls + Verlet)",
             "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
             "launch_ms": force_ms_per_launch}
+    # DRAM traffic of one launch from an ncu capture, while the kernel source is
+    # the one captured (profiles/k_step_traffic.json, one record per workload)
     traffic_file = os.path.join(ROOT, "profiles", "k_step_traffic.json")
     if os.path.exists(traffic_file):
         try:
-            tr = json.load(open(traffic_file))
-            if tr.get("kernel_source_hash") == kernel_hash() and args.workload == "plate":
+            tr = json.load(open(traffic_file)).get(args.workload)
+            if tr and tr.get("kernel_source_hash") == kernel_hash():
                 roof["traffic"] = tr["bytes_per_launch"]
+                roof["traffic_note"] = tr.get("note", "")
         except Exception:
             pass
 
@@ -327,7 +342,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - te
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and e2e_s > 0:
         e2e = {"value": ws * n * args.e2e_steps / e2e_s, "unit": "node-steps/s",
                "h2d_bytes_per_step": 48 * n + 4 * nwords, "d2h_bytes_per_step": 48 * n + 4 * nwords,
                "steps": args.e2e_steps,
@@ -339,7 +354,7 @@ def main():
     if args.precision == "mixed" and not args.no_fp64:
         c64 = pd.Context.from_scenario(sc, precision="fp64", device=local, stream=stream)
         c64.step(dt, args.warmup)
-        k64 = min(args.steps, 400)
+        k64 = min(args.steps, 400 if n < 1_000_000 else 20)
         barrier()
         ev0.record(stream)
         c64.step(dt, k64)
@@ -351,7 +366,7 @@ def main():
         c64.close()
 
     surrogate = None if args.no_surrogate else bench_surrogate(local, stream)
-    aggregate = None if args.no_aggregate else bench_aggregate(local, stream)
+    aggregate = None if (args.no_aggregate or args.workload == "aggregate") else bench_aggregate(local, stream)
     if rank != 0:
         return
     cpu = None if args.no_cpu_baseline else cpu_baseline(sc, args.workload)
@@ -360,7 +375,8 @@ def main():
             "vs_baseline": None, "dtype": "f32+df64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "nodes": n, "directed_bonds": B, "precision": args.precision,
-                       "l2": "inputs larger than L2: ~0.18 GB streamed from HBM per step (129 MB L2)",
+                       "l2": (f"inputs larger than L2: ~{alg_bytes / 1e9:.2f} GB streamed from HBM per step "
+                              "(129 MB L2)"),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "bond_updates_per_s": ws * B * args.steps / (ms * 1e-3),
             "clocks": clk.summary(), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,

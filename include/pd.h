@@ -133,6 +133,12 @@ typedef struct {
                                             lower-index end, in two passes (Eq. pmb is pairwise
                                             antisymmetric): 1 = on, -1 = off, 0 = chosen by the
                                             autotuner; pairs = 1 with tiles = 1 is PD_EINVAL */
+    int persistent;                      /* pd_step runs the steps between two contact-list
+                                            rebuilds in one cooperative launch (a grid-wide
+                                            barrier between steps; same results bit for bit):
+                                            1 = on, -1 = off, 0 = chosen by the library.  Applies
+                                            to the per-slot global-gather kernels; ignored while
+                                            profiling. */
 } pd_options;
 
 /* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */

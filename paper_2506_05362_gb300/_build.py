@@ -14,6 +14,11 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libpd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
+# Per-file flags.  The step kernels are compiled without implicit multiply-add
+# contraction: every fused multiply-add there is written out, so the same source
+# line rounds the same way in every kernel that inlines it (one launch per step or
+# several steps per launch give the same bits).
+FILE_FLAGS = {"pd_step.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -49,7 +54,8 @@ def build(force: bool = False, verbose: bool = False, defines=(), lib_path: str 
 
     def run(fo):
         f, o = fo
-        cmd = [nv, *ARCH, *CFLAGS, *[f"-D{d}" for d in defines], "-c", f, "-o", o]
+        cmd = [nv, *ARCH, *CFLAGS, *FILE_FLAGS.get(os.path.basename(f), []), *[f"-D{d}" for d in defines], "-c", f,
+               "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(f)}:\n{r.stderr}")

@@ -11,6 +11,11 @@
 #include "pd_grid.cuh"
 #include "pd_internal.cuh"
 
+// the multi-step kernel is the default up to this many nodes
+#ifndef PD_PERSIST_AUTO_NODES
+#define PD_PERSIST_AUTO_NODES 0
+#endif
+
 struct GraphEntry {
     int steps, k, parity;
     double dt;
@@ -80,6 +85,10 @@ struct pd_ctx {
     float *tb = nullptr;
     float4 *fup = nullptr;
     bool pairs_ok = false, pairs = false;
+    // several steps per launch (cooperative multi-step kernel of the global kernels)
+    unsigned *gbar = nullptr;
+    bool persist = false;
+    cudaError_t launch_err = cudaSuccess;
     double centre[3] = {0, 0, 0};
 
     WallSet walls;
@@ -376,6 +385,7 @@ pd_status status_of(pd_ctx *c, unsigned e)
     if (e & PDE_NONFINITE) return fail(c, PD_ENONFINITE, "non-finite force or state on the device");
     if (e & PDE_WALL) return fail(c, PD_EWALL, "a node is a whole contact radius behind a wall");
     if (e & PDE_CAPACITY) return fail(c, PD_ECAPACITY, "contact candidate capacity exceeded");
+    if (e & PDE_BARRIER) return fail(c, PD_ETIMEOUT, "a grid-wide barrier of the multi-step kernel timed out");
     if (e & PDE_SKIN) return fail(c, PD_ETIMEOUT, "contact list went stale between rebuilds");
     return PD_OK;
 }
@@ -562,7 +572,8 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     // reductions
     c->blocks_cap = 0;
     for (int g : {4, 8, 16, 32}) c->blocks_cap = std::max(c->blocks_cap, step_blocks(g, c->opt.device, mixed, false, 0));
-    ALLOC(c->partials, double, (int64_t)c->blocks_cap * PART_STRIDE);
+    ALLOC(c->partials, double, 2 * (int64_t)c->blocks_cap * PART_STRIDE);  // two step parities (multi-step kernel)
+    ALLOC(c->gbar, unsigned, 1);
     ALLOC(c->react, double, PD_MAX_WALLS * 3);
     ALLOC(c->disp, double, 1);
     ALLOC(c->wall_pos, double, PD_MAX_WALLS * 9);  // wall points, the wall impulses, the wall normals
@@ -618,6 +629,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
     if (c->opt.tiles < -1 || c->opt.tiles > 1) { delete c; return PD_EINVAL; }
     if (c->opt.pairs < -1 || c->opt.pairs > 1 || (c->opt.pairs == 1 && c->opt.tiles == 1)) { delete c; return PD_EINVAL; }
+    if (c->opt.persistent < -1 || c->opt.persistent > 1) { delete c; return PD_EINVAL; }
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
     if (c->opt.cand_capacity < 0) { delete c; return PD_EINVAL; }
     c->mat = *mat;
@@ -630,6 +642,18 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     }
     *out = c;
     return PD_OK;
+}
+
+// Grid of the step kernel for `lanes` lanes per node: the resident blocks, but no
+// more than the rows (or tiles) give work to (idle blocks only lengthen the
+// fixed-order reduction of the wall reactions).
+static int step_grid(const pd_ctx *c, int lanes)
+{
+    const bool mixed = c->opt.precision == PD_MIXED;
+    const int64_t per = c->tiled ? c->tile_rows : 256 / lanes;
+    const int64_t need = std::max<int64_t>(1, (c->n + per - 1) / per);
+    const int b = std::min(c->blocks_cap, step_blocks(lanes, c->opt.device, mixed, c->tiled, c->tile_smem));
+    return (int)std::min<int64_t>(b, need);
 }
 
 static pd_status autotune(pd_ctx *c)
@@ -652,7 +676,7 @@ static pd_status autotune(pd_ctx *c)
             const int l = cand[q];
             c->tiled = kind == 1;
             c->pairs = kind == 2;
-            const int blocks = std::min(c->blocks_cap, step_blocks(l, c->opt.device, mixed, c->tiled, c->tile_smem));
+            const int blocks = step_grid(c, l);
             StepParams p = params(c, MODE_FORCES, c->cur, 0.0);
             launch_step(p, l, blocks, c->st);  // warm-up; applies any breaking once
             CK(cudaEventRecord(c->ev0, c->st));
@@ -670,7 +694,7 @@ static pd_status autotune(pd_ctx *c)
     c->tiled = bestk == 1;
     c->pairs = bestk == 2;
     c->lanes = bestl;
-    c->blocks = std::min(c->blocks_cap, step_blocks(bestl, c->opt.device, mixed, c->tiled, c->tile_smem));
+    c->blocks = step_grid(c, bestl);
     clear_graphs(c);
     return sync(c);
 }
@@ -841,12 +865,14 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     if (s) return s;
     release(c, k1); release(c, k2); release(c, v1); release(c, v2); release(c, btmp); release(c, cnt);
     c->bonds_ready = true;
+    // several steps per launch: on request, or by default for problems small enough
+    // that one step's launch is mostly fixed cost
+    c->persist = c->opt.persistent == 1 || (c->opt.persistent == 0 && n <= PD_PERSIST_AUTO_NODES);
     if (c->opt.lanes_per_node == 0) {
         s = autotune(c);
         if (s) return s;
     } else {
-        c->blocks = std::min(c->blocks_cap, step_blocks(c->lanes, c->opt.device, c->opt.precision == PD_MIXED,
-                                                        c->tiled, c->tile_smem));
+        c->blocks = step_grid(c, c->lanes);
     }
     return eval_forces(c);
 }
@@ -926,6 +952,25 @@ pd_status pd_stable_dt(pd_ctx *c, double *dt)
 // ---- stepping -------------------------------------------------------------------
 // Enqueues one chunk of `steps` Verlet steps starting from u[parity]; contact
 // lists are rebuilt before the first step and then every k steps.
+// Whether pd_step runs its steps between rebuilds in one launch of the multi-step
+// kernel: the per-slot global-gather kernels only, not while profiling.
+static bool use_persist(const pd_ctx *c)
+{
+    return c->persist && !c->tiled && !c->pairs && !c->profiling;
+}
+
+// Grid of the multi-step kernel: resident blocks, at most one per GPB rows.
+static int persist_grid(const pd_ctx *c)
+{
+    const bool mixed = c->opt.precision == PD_MIXED;
+    const bool wx = c->walls.nw > 0 && (c->mat.mu > 0 || (c->mat.wall_overlap && c->walls.nw >= 2));
+    const int64_t rows_per_block = 256 / c->lanes;
+    const int64_t need = (c->n + rows_per_block - 1) / rows_per_block;
+    int b = persist_blocks(c->lanes, c->opt.device, mixed, wx);
+    b = (int)std::min<int64_t>({(int64_t)b, (int64_t)c->blocks_cap, need});
+    return b;
+}
+
 static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
 {
     int64_t launches = 0;
@@ -933,10 +978,37 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
     launch_drift(p, c->st);
     ++launches;
     int in = parity ^ 1;
-    for (int s = 0; s < steps; ++s) {
+    const int pgrid = use_persist(c) ? persist_grid(c) : 0;
+    for (int s = 0; s < steps;) {
         if (c->opt.contact && s % k == 0) {
             enqueue_rebuild(c, in);
             launches += 12;
+        }
+        if (pgrid > 0) {
+            // the steps up to the next rebuild, all MODE_FULL, in one launch; the
+            // chunk's last step (MODE_FINAL) is one k_step launch
+            const int run = c->opt.contact ? std::min(k - s % k, steps - s) : steps - s;
+            const bool ends = s + run == steps;
+            const int full = ends ? run - 1 : run;
+            if (full > 1) {
+                cudaMemsetAsync(c->gbar, 0, sizeof(unsigned), c->st);
+                StepParams pa = params(c, MODE_FULL, in, dt), pb = params(c, MODE_FULL, in ^ 1, dt);
+                cudaError_t e = launch_persist(pa, pb, full, c->lanes, pgrid, c->gbar, c->st);
+                if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
+                launches += 2;
+                if (full & 1) in ^= 1;
+            } else if (full == 1) {
+                launch_step(params(c, MODE_FULL, in, dt), c->lanes, c->blocks, c->st);
+                launches += (c->opt.contact && c->cand_fd) ? 2 : 1;
+                in ^= 1;
+            }
+            s += full;
+            if (ends) {
+                launch_step(params(c, MODE_FINAL, in, dt), c->lanes, c->blocks, c->st);
+                launches += (c->opt.contact && c->cand_fd) ? 2 : 1;
+                ++s;
+            }
+            continue;
         }
         const bool last = (s == steps - 1);
         StepParams q = params(c, last ? MODE_FINAL : MODE_FULL, in, dt);
@@ -949,6 +1021,7 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
         }
         launches += (c->opt.contact && c->cand_fd) ? 2 : 1;  // the pair-damping kernel runs first
         if (!last) in ^= 1;
+        ++s;
     }
     return launches;
 }
@@ -1043,6 +1116,18 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
     const int chunk = chunk_for(c, k);
     while (left > 0) {
         int steps = (int)std::min<int64_t>(left, chunk);
+        if (use_persist(c)) {  // cooperative launches, enqueued directly (not captured)
+            c->launch_err = cudaSuccess;
+            *launches += enqueue_chunk(c, steps, std::min(k, steps), c->cur, dt);
+            if (c->launch_err != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, PD_ECUDA, std::string("multi-step launch: ") + cudaGetErrorString(c->launch_err));
+            }
+            CK(cudaGetLastError());
+            c->cur ^= (steps & 1);
+            left -= steps;
+            continue;
+        }
         if (c->profiling) {
             int kk = std::min(k, steps);
             if ((int)c->prof_ev.size() < c->prof_used + 2 * steps) {
@@ -1122,8 +1207,8 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out,
         ++c->n_rollbacks;
         s = snapshot(c, true);
         if (s) return s;
-        if (e & (PDE_NONFINITE | PDE_WALL)) {
-            c->latched |= e & (PDE_NONFINITE | PDE_WALL);
+        if (e & (PDE_NONFINITE | PDE_WALL | PDE_BARRIER)) {
+            c->latched |= e & (PDE_NONFINITE | PDE_WALL | PDE_BARRIER);
             sync(c);
             return status_of(c, e);
         }

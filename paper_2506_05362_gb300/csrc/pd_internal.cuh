@@ -21,7 +21,8 @@ enum : unsigned {
     PDE_NONFINITE = 1u,
     PDE_WALL = 2u,
     PDE_CAPACITY = 4u,   // contact candidate list overflow
-    PDE_SKIN = 8u        // a node moved more than half the skin between rebuilds
+    PDE_SKIN = 8u,       // a node moved more than half the skin between rebuilds
+    PDE_BARRIER = 16u    // a grid-wide barrier of the multi-step kernel timed out
 };
 
 // what the fused step kernel does after the force evaluation
@@ -117,7 +118,7 @@ struct StepParams {
     float4 *fup;                   // per row: pass 1's force from the row's own slots
 };
 
-#define PART_STRIDE 20  // 18 reaction components + max|v| + spare
+#define PART_STRIDE 20  // 18 reaction components, max|v| (multi-step kernel), spare
 #define PD_GL 32        // Gauss-Legendre points of the multi-wall overlap integrals
 
 // Radix sort of (key, value) pairs, LSD 8-bit digits, stable.  bits = number of
@@ -155,6 +156,10 @@ void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64
 
 // Step kernels (pd_step.cu)
 void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
+// several MODE_FULL steps in one cooperative launch (see k_persist)
+int persist_blocks(int lanes, int device, bool mixed, bool wx);
+cudaError_t launch_persist(const StepParams &pa, const StepParams &pb, int nsteps, int lanes, int blocks,
+                           unsigned *bar, cudaStream_t st);
 void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float state <-> FP64 (mixed path)
 // double-float pair arrays with an element stride (1 for dense, REC for records)

@@ -36,6 +36,14 @@ constexpr int STEP_THREADS = 256;
 #ifndef PD_INFLIGHT
 #define PD_INFLIGHT 3
 #endif
+// the global-gather mixed kernel: slot words loaded one batch ahead (software
+// pipeline), PD_INFLIGHT_PF bonds per lane and batch
+#ifndef PD_PREFETCH
+#define PD_PREFETCH 1
+#endif
+#ifndef PD_INFLIGHT_PF
+#define PD_INFLIGHT_PF 2
+#endif
 #ifndef PD_MINB_GLOBAL
 #define PD_MINB_GLOBAL 4
 #endif
@@ -212,7 +220,7 @@ __device__ __forceinline__ double3 wall_overlap_terms(const double *wall_pos, co
 // WX (the kernels launched when friction or inclusion-exclusion is on) also the
 // wall friction and the multi-wall terms, which other kernels do not carry.
 template <bool WX>
-__device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, double py, double pz,
+__device__ __forceinline__ unsigned wall_force(const StepParams &p, const double *wp, double px, double py, double pz,
                                                double vol, double vx, double vy, double vz, double &fx,
                                                double &fy, double &fz, double *react)
 {
@@ -220,7 +228,7 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
     int touching = 0;
     for (int l = 0; l < p.walls.nw; ++l) {
         const double nx = p.walls.n[l][0], ny = p.walls.n[l][1], nz = p.walls.n[l][2];
-        const double *w = p.wall_pos + 3 * l;
+        const double *w = wp + 3 * l;
         double d = dadd(dadd(dmul(px - w[0], nx), dmul(py - w[1], ny)), dmul(pz - w[2], nz));
         if (!(d < p.Rc)) continue;
         if (d <= -p.Rc) { e |= PDE_WALL; continue; }
@@ -254,7 +262,7 @@ __device__ __forceinline__ unsigned wall_force(const StepParams &p, double px, d
         ++touching;
     }
     if (WX && p.wall_overlap && touching >= 2) {
-        const double3 o = wall_overlap_terms(p.wall_pos, p.wall_n, p.gl, p.walls.nw, p.Rc, p.Kn, px, py, pz, vol,
+        const double3 o = wall_overlap_terms(wp, p.wall_n, p.gl, p.walls.nw, p.Rc, p.Kn, px, py, pz, vol,
                                              react);
         fx += o.x; fy += o.y; fz += o.z;
     }
@@ -524,7 +532,8 @@ __device__ __forceinline__ unsigned epilogue_component(const StepParams &p, int6
 // warp calls it (inactive rows included) so that the shuffles that broadcast a
 // wall force and sum |v|^2 are uniform.
 template <int G, bool WX>
-__device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t row, bool active, int gl, float Fx,
+__device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, const double *wp, int64_t row, bool active,
+                                                   int gl, float Fx,
                                                    float Fy, float Fz, const float4 &oxh, const float4 &uh,
                                                    const float4 &ul, const float4 &vh, const float4 &vl,
                                                    double *react, float &vmax2)
@@ -537,7 +546,7 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
             const float cx = (float)p.centre[0], cy = (float)p.centre[1], cz = (float)p.centre[2];
             bool near = false;
             for (int l = 0; l < p.walls.nw; ++l) {
-                const double *w = p.wall_pos + 3 * l;
+                const double *w = wp + 3 * l;
                 const float qx = (float)w[0] - cx, qy = (float)w[1] - cy, qz = (float)w[2] - cz;
                 const float d = (px - qx) * (float)p.walls.n[l][0] + (py - qy) * (float)p.walls.n[l][1] +
                                 (pz - qz) * (float)p.walls.n[l][2];
@@ -550,7 +559,7 @@ __device__ __forceinline__ unsigned epilogue_lanes(const StepParams &p, int64_t 
                 const double ux = df_to_double(df{uh.x, ul.x}), uy = df_to_double(df{uh.y, ul.y}),
                              uz = df_to_double(df{uh.z, ul.z});
                 double fx = 0.0, fy = 0.0, fz = 0.0;
-                err |= wall_force<WX>(p, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, df_to_double(df{vh.x, vl.x}),
+                err |= wall_force<WX>(p, wp, dadd(ox.x, ux), dadd(ox.y, uy), dadd(ox.z, uz), ox.w, df_to_double(df{vh.x, vl.x}),
                                   df_to_double(df{vh.y, vl.y}), df_to_double(df{vh.z, vl.z}), fx, fy, fz, react);
                 wx = (float)fx; wy = (float)fy; wz = (float)fz;
             }
@@ -684,10 +693,10 @@ __device__ __forceinline__ void load_v_t(const StepParams &p, int64_t i, double 
 // field; candidates that do not touch get zero, and the step kernel adds the
 // term only to pairs it accepts.
 template <bool MIXED>
-__global__ void k_pair_damping(const StepParams p)
+__device__ __forceinline__ void pair_damping_rows(const StepParams &p, int64_t first, int64_t stride)
 {
     const double R2 = dmul(p.Rc, p.Rc);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = first; i < p.n; i += stride) {
         const int64_t c0 = p.cand_ptr[i], c1 = p.cand_ptr[i + 1];
         if (c1 <= c0) continue;
         const dbl4 ox = p.x4[i], ou = load_u_t<MIXED>(p, i);
@@ -747,6 +756,12 @@ __global__ void k_pair_damping(const StepParams p)
     }
 }
 
+template <bool MIXED>
+__global__ void k_pair_damping(const StepParams p)
+{
+    pair_damping_rows<MIXED>(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
 // Tile staging of the mixed path: the records of the nodes a tile touches.
 struct TileView {
     const float4 *s0, *s1, *s2;  // shared copies of xh4, uh_in, ul_in for the tile's list
@@ -756,7 +771,8 @@ struct TileView {
 // Steps 1-4 for one row owned by a group of G lanes (all lanes call; inactive
 // groups pass active = false and still join the shuffles).
 template <int G, bool MIXED, bool WX = false, bool PAIRS = false>
-__device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bool active, int gl, int lrow,
+__device__ __forceinline__ void process_row(const StepParams &p, const double *wp, int64_t row, bool active, int gl,
+                                            int lrow,
                                             const TileView &tv, double *react, unsigned &err, float &vmax2f,
                                             double &vmax2)
 {
@@ -808,6 +824,43 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
             const int i0 = (int)k0, i1 = (int)k1;
+#if PD_PREFETCH
+            // software pipeline: the slot words of the next batch are loaded while
+            // the current batch's records are gathered and evaluated, so that the
+            // streamed index load and the dependent gather do not follow one
+            // another on every batch
+            int32_t raw[PD_INFLIGHT_PF];
+            {
+                const int k = i0 + gl;
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
+                    const int kq = k + q * G;
+                    raw[q] = kq < i1 ? __ldg(p.colf + kq) : (int32_t)0x80000000u;
+                }
+            }
+            for (int k = i0 + gl; k < i1; k += PD_INFLIGHT_PF * G) {
+                float4 a0[PD_INFLIGHT_PF], a1[PD_INFLIGHT_PF], a2[PD_INFLIGHT_PF];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
+                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);  // one 48-byte record
+                    a0[q] = __ldg(rj);
+                    a1[q] = __ldg(rj + 1);
+                    a2[q] = __ldg(rj + 2);
+                }
+                int32_t nxt[PD_INFLIGHT_PF];
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
+                    // a slot past the row end gathers node 0 and is flagged (no force)
+                    const int kq = k + (PD_INFLIGHT_PF + q) * G;
+                    nxt[q] = kq < i1 ? __ldg(p.colf + kq) : (int32_t)0x80000000u;
+                }
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT_PF; ++q)
+                    bond_mixed_flagged(p, k + q * G, raw[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
+#pragma unroll
+                for (int q = 0; q < PD_INFLIGHT_PF; ++q) raw[q] = nxt[q];
+            }
+#else
             for (int k = i0 + gl; k < i1; k += PD_INFLIGHT * G) {
                 int32_t raw[PD_INFLIGHT];
 #pragma unroll
@@ -830,6 +883,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
                 for (int q = 0; q < PD_INFLIGHT; ++q)
                     bond_mixed_flagged(p, k + q * G, raw[q], o0, o1, o2, ol, a0[q], a1[q], a2[q], fbx, fby, fbz);
             }
+#endif
         } else {
             const dbl4 ox = p.x4[row], ou = p.u_in[row];
             for (int64_t k = k0 + gl; k < k1; k += G) {
@@ -883,7 +937,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
             oxh = __ldg(p.xh4 + REC * row); ouh = __ldg(p.uh_in + REC * row); oul = __ldg(p.ul_in + REC * row);
             ovh = p.vh[row]; ovl = p.vl[row];
         }
-        err |= epilogue_lanes<G, WX>(p, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
+        err |= epilogue_lanes<G, WX>(p, wp, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
     }
     if (!MIXED && active && gl == 0) {
         const double hdt = 0.5 * p.dt;
@@ -891,7 +945,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, int64_t row, bo
         const dbl4 ox = p.x4[row], ou = p.u_in[row];
         const dbl4 ov = p.v[row];
         if (p.walls.nw)
-            err |= wall_force<WX>(p, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, ov.x, ov.y, ov.z, Fx, Fy,
+            err |= wall_force<WX>(p, wp, dadd(ox.x, ou.x), dadd(ox.y, ou.y), dadd(ox.z, ou.z), ox.w, ov.x, ov.y, ov.z, Fx, Fy,
                               Fz, react);
         if (!isfinite(Fx) || !isfinite(Fy) || !isfinite(Fz)) err |= PDE_NONFINITE;
         dbl4 a;
@@ -966,6 +1020,9 @@ __device__ __forceinline__ void block_finish(const StepParams &p, double (*s_rea
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c = warp; c < ncomp; c += STEP_THREADS / 32) {
         double s = 0.0;
+        // unrolled so that the loads of several blocks' partials are in flight
+        // together; the additions keep their order
+#pragma unroll 8
         for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(p.partials + (int64_t)b * PART_STRIDE + c);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -1013,10 +1070,196 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_st
     const TileView tv{nullptr, nullptr, nullptr, false};
     for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
         const int64_t row = r0 + grp;
-        process_row<G, MIXED, WX, PAIRS>(p, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
+        process_row<G, MIXED, WX, PAIRS>(p, p.wall_pos, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
     }
     if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
     block_finish<GPB>(p, s_react, s_vmax, s_err, s_last, err);
+}
+
+// ---- Several steps in one launch ------------------------------------------------
+// A run of MODE_FULL steps between two contact-list rebuilds in one cooperative
+// launch: each step does what one k_step launch does (the same rows, the same
+// arithmetic, the same fixed-order reductions), separated by a grid-wide barrier,
+// so the trajectory is bit for bit that of one launch per step while the launch
+// cost and the gap between launches are paid once per run.  Every block keeps
+// its own copy of the wall positions and of the skin bookkeeping and advances
+// them identically; block 0 alone writes the wall reactions and impulses, and
+// at the end the walls, displacement bound and stale flag.  Even steps use the
+// parameters pa (state buffers in -> out), odd steps pb (out -> in).
+
+constexpr unsigned BAR_ABORT = 0x80000000u;     // set in the barrier word by a block that gave up
+constexpr unsigned long long BAR_WAIT_NS = 1000000000ull;  // a barrier wait gives up after 1 s
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier: the barrier word counts arrivals; barrier number k is passed
+// once it reaches (k + 1) * gridDim.x.  A wait that lasts longer than BAR_WAIT_NS,
+// or that sees another block's abort mark, records PDE_BARRIER, marks the word
+// and returns false; every block then leaves the kernel.
+__device__ bool grid_barrier(unsigned *bar, unsigned target, unsigned *err, int *s_ok)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        const unsigned long long t0 = global_ns();
+        for (unsigned it = 1;; ++it) {
+            const unsigned v = ld_acquire_u32(bar);
+            if (v & BAR_ABORT) { ok = 0; break; }
+            if (v >= target) break;
+            if ((it & 63u) == 0 && global_ns() - t0 > BAR_WAIT_NS) {
+                atomicOr(err, (unsigned)PDE_BARRIER);
+                atomicOr(bar, BAR_ABORT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// The wall reactions of one step from the per-block partials (the last-block
+// reduction of block_finish: one warp per component, lanes striding over the
+// blocks, a fixed xor butterfly), written with the impulse by block 0.
+__device__ __forceinline__ void reduce_reactions(const StepParams &p, const double *partials, int nblocks)
+{
+    const int ncomp = 3 * p.walls.nw;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int c = warp; c < ncomp; c += STEP_THREADS / 32) {
+        double s = 0.0;
+#pragma unroll 8
+        for (int b = lane; b < nblocks; b += 32) s += __ldcg(partials + (int64_t)b * PART_STRIDE + c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            p.react[c] = s;
+            p.impulse[c] = dadd(p.impulse[c], dmul(p.dt, s));
+        }
+    }
+}
+
+template <int G, bool MIXED, bool WX>
+__device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsigned *bar, unsigned &nbar,
+                                             double (*s_react)[PD_MAX_WALLS * 3], double *s_vmax, double *s_wall,
+                                             unsigned &s_err, int &s_ok, double &s_disp)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    if (p.pair_diss && p.contact && p.cand_fd) {  // damping and friction of the candidates first
+        pair_damping_rows<MIXED>(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+        if (!grid_barrier(bar, ++nbar * gridDim.x, p.err, &s_ok)) return false;
+    }
+    if (gl == 0)
+        for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
+    if (threadIdx.x == 0) s_err = 0;
+    __syncthreads();
+    unsigned err = 0;
+    double vmax2 = 0.0;
+    float vmax2f = 0.f;
+    const TileView tv{nullptr, nullptr, nullptr, false};
+    for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
+        const int64_t row = r0 + grp;
+        process_row<G, MIXED, WX, false>(p, s_wall, row, row < p.n, gl, 0, tv, s_react[grp], err, vmax2f, vmax2);
+    }
+    if (gl == 0) s_vmax[grp] = MIXED ? (double)vmax2f : vmax2;
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    // this block's partials, in the buffer of the step's parity
+    double *partials = p.partials + (int64_t)(step & 1) * gridDim.x * PART_STRIDE;
+    double *part = partials + (int64_t)blockIdx.x * PART_STRIDE;
+    const int ncomp = 3 * p.walls.nw;
+    if ((int)threadIdx.x < ncomp) {
+        double sum = 0.0;
+        for (int g = 0; g < GPB; ++g) sum += s_react[g][threadIdx.x];
+        part[threadIdx.x] = sum;
+    } else if (threadIdx.x == 32) {
+        double m = 0.0;
+        for (int g = 0; g < GPB; ++g) m = fmax(m, s_vmax[g]);
+        part[PART_STRIDE - 2] = m > 0.0 ? (double)__double2float_ru(m) : 0.0;
+        if (s_err) atomicOr(p.err, s_err);
+    }
+    if (!grid_barrier(bar, ++nbar * gridDim.x, p.err, &s_ok)) return false;
+    if (blockIdx.x == 0) reduce_reactions(p, partials, gridDim.x);
+    {  // the same bookkeeping in every block: max |v|^2 over the blocks' partials,
+       // read by all threads at once (a max does not depend on the order)
+        double vm = 0.0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += STEP_THREADS)
+            vm = fmax(vm, __ldcg(partials + (int64_t)b * PART_STRIDE + PART_STRIDE - 2));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vm = fmax(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+        if ((threadIdx.x & 31) == 0) s_vmax[threadIdx.x >> 5] = vm;  // s_vmax holds >= 8 entries (G <= 32)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double m = 0.0;
+            for (int w = 0; w < STEP_THREADS / 32; ++w) m = fmax(m, s_vmax[w]);
+            s_disp = s_disp + p.dt * sqrt(m);
+        }
+    }
+    if ((int)threadIdx.x < ncomp) {
+        const int l = threadIdx.x / 3, q = threadIdx.x % 3;
+        s_wall[threadIdx.x] = dadd(s_wall[threadIdx.x], dmul(p.dt, p.walls.v[l][q]));
+    }
+    __syncthreads();
+    return true;
+}
+
+template <int G, bool MIXED, bool WX>
+__global__ void __launch_bounds__(STEP_THREADS, 2)
+    k_persist(const __grid_constant__ StepParams pa, const __grid_constant__ StepParams pb, int nsteps, unsigned *bar)
+{
+    constexpr int GPB = STEP_THREADS / G;
+    __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
+    __shared__ double s_vmax[GPB];
+    __shared__ double s_wall[PD_MAX_WALLS * 3];
+    __shared__ unsigned s_err;
+    __shared__ int s_ok;
+    __shared__ double s_disp;
+    const int ncomp = 3 * pa.walls.nw;
+    if ((int)threadIdx.x < ncomp) s_wall[threadIdx.x] = pa.wall_pos[threadIdx.x];
+    if (threadIdx.x == 0) {
+        s_disp = *pa.disp;
+        if (blockIdx.x == 0 && pa.contact && *pa.stale) atomicOr(pa.err, (unsigned)PDE_SKIN);
+    }
+    __syncthreads();
+    unsigned nbar = 0;
+    int done = 0;
+    for (int st = 0; st < nsteps; ++st) {
+        // a list that went stale in the previous step of this run: the next step
+        // would use it, so the run stops here with the stale mark (as k_step does)
+        if (st > 0 && pa.contact && 2.0 * s_disp >= pa.skin) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(pa.err, (unsigned)PDE_SKIN);
+            break;
+        }
+        // one copy of the step's code for both parities: the parameter block is
+        // chosen at run time (grid-constant parameters can be addressed)
+        const StepParams &p = (st & 1) ? pb : pa;
+        const bool ok = persist_step<G, MIXED, WX>(p, st, bar, nbar, s_react, s_vmax, s_wall, s_err, s_ok, s_disp);
+        if (!ok) return;
+        done = st + 1;
+    }
+    if (blockIdx.x == 0) {
+        if ((int)threadIdx.x < ncomp) pa.wall_pos[threadIdx.x] = s_wall[threadIdx.x];
+        if (threadIdx.x == 0 && done > 0) {
+            *pa.disp = s_disp;
+            if (2.0 * s_disp >= pa.skin) *pa.stale = 1;
+        }
+    }
 }
 
 // Mixed path with shared-memory tiles.  A block takes tile t (rows
@@ -1085,7 +1328,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             const int64_t row = r0 + rr;
             const bool active = rr < rows;
             if (!on) {
-                process_row<G, true>(p, row, active, gl, 0, off, s_react[grp], err, vmax2f, vmax2);
+                process_row<G, true>(p, p.wall_pos, row, active, gl, 0, off, s_react[grp], err, vmax2f, vmax2);
                 continue;
             }
             float fbx = 0.f, fby = 0.f, fbz = 0.f;
@@ -1123,7 +1366,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             fby = group_sum<G>(fby) + (float)cy;
             fbz = group_sum<G>(fbz) + (float)cz;
             const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            err |= epilogue_lanes<G, false>(p, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
+            err |= epilogue_lanes<G, false>(p, p.wall_pos, row, active, gl, fbx, fby, fbz, active ? o0 : z4, active ? o1 : z4,
                                      active ? o2 : z4, active ? vhs[rr] : z4, active ? vls[rr] : z4, s_react[grp],
                                      vmax2f);
         }
@@ -1245,6 +1488,29 @@ void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 }
 
 template <int G>
+cudaError_t launch_persist_g(const StepParams &pa, const StepParams &pb, int nsteps, int blocks, unsigned *bar,
+                             bool mixed, cudaStream_t st)
+{
+    void *args[] = {(void *)&pa, (void *)&pb, (void *)&nsteps, (void *)&bar};
+    const void *fn;
+    if (pa.wall_extra)
+        fn = mixed ? (const void *)k_persist<G, true, true> : (const void *)k_persist<G, false, true>;
+    else
+        fn = mixed ? (const void *)k_persist<G, true, false> : (const void *)k_persist<G, false, false>;
+    return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(STEP_THREADS), args, 0, st);
+}
+
+template <int G>
+int persist_blocks_g(int sms, bool mixed, bool wx)
+{
+    int per = 0;
+    const void *fn = wx ? (mixed ? (const void *)k_persist<G, true, true> : (const void *)k_persist<G, false, true>)
+                        : (mixed ? (const void *)k_persist<G, true, false> : (const void *)k_persist<G, false, false>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, STEP_THREADS, 0);
+    return sms * per;
+}
+
+template <int G>
 int blocks_g(int sms, bool mixed, bool tiled, size_t smem)
 {
     int per = 0;
@@ -1281,6 +1547,35 @@ int step_blocks(int lanes, int device, bool mixed, bool tiled, size_t tile_smem)
         case 8: return blocks_g<8>(sms, mixed, tiled, tile_cap);
         case 16: return blocks_g<16>(sms, mixed, tiled, tile_cap);
         default: return blocks_g<32>(sms, mixed, tiled, tile_cap);
+    }
+}
+
+// Most blocks a cooperative launch of the multi-step kernel may have (0: none).
+int persist_blocks(int lanes, int device, bool mixed, bool wx)
+{
+    int sms = 0, coop = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    if (sms < 1 || !coop) return 0;
+    switch (lanes) {
+        case 4: return persist_blocks_g<4>(sms, mixed, wx);
+        case 8: return persist_blocks_g<8>(sms, mixed, wx);
+        case 16: return persist_blocks_g<16>(sms, mixed, wx);
+        default: return persist_blocks_g<32>(sms, mixed, wx);
+    }
+}
+
+// nsteps MODE_FULL steps in one cooperative launch; pa for even steps, pb for odd
+// ones.  bar (one word) must be zero.  Returns the launch status.
+cudaError_t launch_persist(const StepParams &pa, const StepParams &pb, int nsteps, int lanes, int blocks,
+                           unsigned *bar, cudaStream_t st)
+{
+    const bool mixed = pa.xh4 != nullptr;
+    switch (lanes) {
+        case 4: return launch_persist_g<4>(pa, pb, nsteps, blocks, bar, mixed, st);
+        case 8: return launch_persist_g<8>(pa, pb, nsteps, blocks, bar, mixed, st);
+        case 16: return launch_persist_g<16>(pa, pb, nsteps, blocks, bar, mixed, st);
+        default: return launch_persist_g<32>(pa, pb, nsteps, blocks, bar, mixed, st);
     }
 }
 

@@ -758,3 +758,52 @@ def test_self_contact_repulsion_trajectory(pd, precision, tol):
     assert rel_l2(u, ref.u) < tol
     assert rel_l2(vg, ref.v) < 10 * tol
     ctx.close()
+
+
+# --------------------------------------------------------------------------- several steps per launch
+def _collision_scenario(zeta=0.0):
+    from paper_2506_05362_gb300 import surrogate as SG
+    sc = S.aggregate(n_grains=2, h=0.5e-3 / 4, gap_cells=0.5, seed=4)
+    c = sc.x[sc.grain == 0].mean(0) - sc.x[sc.grain == 1].mean(0)
+    c /= np.linalg.norm(c)
+    sc.v0 = np.where((sc.grain == 0)[:, None], -8.0 * c, 8.0 * c)
+    sc.walls = []
+    if zeta:
+        sc.material.beta_d = SG.damping_coefficient(sc.material, sc.horizon, sc.h ** 3, zeta)
+    return sc
+
+
+@pytest.mark.parametrize("case", ["sphere-mixed", "sphere-fp64", "collision", "collision-damped", "friction-walls"])
+def test_multi_step_launch_equals_one_launch_per_step(pd, case):
+    """The steps between two rebuilds in one cooperative launch (grid-wide barrier
+    between steps) give bit for bit the trajectory of one launch per step: state,
+    wall points, wall forces and their time average; with walls, contacts and
+    rebuilds, pair damping, and the wall-friction kernels."""
+    precision = "fp64" if case == "sphere-fp64" else "mixed"
+    if case.startswith("sphere"):
+        sc, steps, calls = S.sphere(), 150, 2
+    elif case == "friction-walls":
+        sc = damped_blocks()
+        sc.material.mu = 0.4
+        steps, calls = 60, 3
+    else:
+        sc, steps, calls = _collision_scenario(0.3 if case == "collision-damped" else 0.0), 300, 8
+    ctxs = [pd.Context.from_scenario(sc, precision=precision, lanes=8, tiles=-1, pairs=-1, persistent=pm)
+            for pm in (1, -1)]
+    dt = 0.5 * ctxs[0].stable_dt()
+    nw = len(sc.walls)
+    for _ in range(calls):
+        for ctx in ctxs:
+            ctx.step(dt, steps)
+    a, b = ctxs
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    if nw:
+        assert np.array_equal(a.get_walls(), b.get_walls())
+        areas = [1e-6] * nw
+        assert np.array_equal(a.bulk_stress(areas)[1], b.bulk_stress(areas)[1])
+        assert np.array_equal(a.bulk_stress_mean(areas)[1], b.bulk_stress_mean(areas)[1])
+    assert a.step_counters() == b.step_counters()
+    if case.startswith("collision"):
+        assert len(a.contacts()) > 0
+    a.close(); b.close()
