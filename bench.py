@@ -35,6 +35,8 @@ WORKLOADS = {
     "sphere": "glass sphere radius 1 mm, h=0.1 mm, 4,139 nodes, delta=3h, plates at 1 m/s, dt=0.8 dt_crit",
     "hollow": "glass hollow sphere R=1 mm, r=0.7 mm, h=0.02 mm, 343,846 nodes, delta=3h, plates at 5 m/s",
     "aggregate": "1000 star-shaped glass grains, h=R/12, ~7.6 M nodes, delta=3h, six walls, top wall at 10 m/s",
+    "aggregate-125": ("125 star-shaped glass grains of the aggregate recipe (920,726 nodes; the case the aggregate's "
+                      "DRAM traffic is captured on)"),
     "shape-sphere": "shape study: 125 solid glass spheres R=1 mm, h=R/8 (262,875 nodes), delta=3h, top wall 10 m/s",
     "shape-shell": "shape study: 125 glass shells R=1 mm, r=0.7R, h=R/8 (170,500 nodes), top wall 10 m/s",
     "shape-jack": "shape study: 125 glass jacks R=1 mm (arms R/3), h=R/8 (93,375 nodes), top wall 10 m/s",
@@ -57,6 +59,7 @@ def make_workload(name):
     from paper_2506_05362_gb300 import scenarios as S
     return {"plate": S.kalthoff, "sphere": S.sphere, "hollow": S.hollow,
             "aggregate": lambda: S.aggregate(n_grains=1000, seed=0),
+            "aggregate-125": lambda: S.aggregate(n_grains=125, seed=0),
             "shape-sphere": lambda: S.shape_study("sphere"), "shape-shell": lambda: S.shape_study("shell"),
             "shape-jack": lambda: S.shape_study("jack"), "double-hollow": S.double_hollow}[name]()
 KERNEL_NAMES = {0: "global gathers", 1: "shared-memory tiles", 2: "each bond once (two passes)"}
@@ -238,6 +241,8 @@ def main():
     ap.add_argument("--tiles", default="auto", choices=["auto", "on", "off"])
     ap.add_argument("--pairs", default="auto", choices=["auto", "on", "off"],
                     help="each bond evaluated once (two passes)")
+    ap.add_argument("--persistent", default="auto", choices=["auto", "on", "off"],
+                    help="the steps between rebuilds in one cooperative launch")
     ap.add_argument("--workload", default="plate", choices=sorted(WORKLOADS),
                     help="workload of the timed steps (the headline figure is the plate)")
     ap.add_argument("--no-aggregate", action="store_true",
@@ -267,7 +272,8 @@ def main():
     stream = torch.cuda.Stream(local)
     ctx = pd.Context.from_scenario(sc, precision=args.precision, device=local, stream=stream,
                                    lanes=args.lanes, tiles={"auto": 0, "on": 1, "off": -1}[args.tiles],
-                                   pairs={"auto": 0, "on": 1, "off": -1}[args.pairs])
+                                   pairs={"auto": 0, "on": 1, "off": -1}[args.pairs],
+                                   persistent={"auto": 0, "on": 1, "off": -1}[args.persistent])
     lanes, kernel, tms = ctx.tuning()
     tuning = {"lanes_per_node": lanes, "kernel": KERNEL_NAMES[kernel],
               "ms_global_4_8_16_32": [round(float(t), 4) for t in tms[:4]],

@@ -13,7 +13,7 @@
 
 // the multi-step kernel is the default up to this many nodes
 #ifndef PD_PERSIST_AUTO_NODES
-#define PD_PERSIST_AUTO_NODES 0
+#define PD_PERSIST_AUTO_NODES 20000
 #endif
 
 struct GraphEntry {
@@ -1207,7 +1207,9 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out,
         ++c->n_rollbacks;
         s = snapshot(c, true);
         if (s) return s;
-        if (e & (PDE_NONFINITE | PDE_WALL | PDE_BARRIER)) {
+        // a stale or overflowed contact list comes first: a node that went through a
+        // wall or a non-finite state later in the segment may be its consequence
+        if ((e & (PDE_NONFINITE | PDE_WALL | PDE_BARRIER)) && !(e & (PDE_SKIN | PDE_CAPACITY))) {
             c->latched |= e & (PDE_NONFINITE | PDE_WALL | PDE_BARRIER);
             sync(c);
             return status_of(c, e);

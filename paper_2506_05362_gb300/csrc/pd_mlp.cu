@@ -326,13 +326,26 @@ __global__ void k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld,
     float acc = 0.f;
     const bf16 *r = dZT + (int64_t)c * ld;  // ld is a multiple of 8: rows start 16-byte aligned
     const int64_t r8 = rows / 8;
-    for (int64_t q = threadIdx.x; q < r8; q += blockDim.x) {
-        const uint4 w = *(const uint4 *)(r + 8 * q);
-        const __nv_bfloat162 *h = (const __nv_bfloat162 *)&w;
+    // RS_BATCH 16-byte loads of a thread are issued before any is added (one block
+    // per column leaves few loads in flight otherwise); the additions keep the
+    // order of a plain strided loop
+    constexpr int RS_BATCH = 8;
+    for (int64_t q0 = threadIdx.x; q0 < r8; q0 += (int64_t)RS_BATCH * blockDim.x) {
+        uint4 w[RS_BATCH];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float2 f = __bfloat1622float2(h[e]);
-            acc += f.x + f.y;
+        for (int b = 0; b < RS_BATCH; ++b) {
+            const int64_t q = q0 + (int64_t)b * blockDim.x;
+            w[b] = q < r8 ? *(const uint4 *)(r + 8 * q) : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int b = 0; b < RS_BATCH; ++b) {
+            if (q0 + (int64_t)b * blockDim.x >= r8) break;
+            const __nv_bfloat162 *h = (const __nv_bfloat162 *)&w[b];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h[e]);
+                acc += f.x + f.y;
+            }
         }
     }
     for (int64_t q = 8 * r8 + threadIdx.x; q < rows; q += blockDim.x) acc += __bfloat162float(r[q]);
@@ -353,7 +366,8 @@ __global__ void k_reduce_dw(const float *__restrict__ part, int splits, int N, i
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(q / k_valid), c = (int)(q % k_valid);
         float s = 0.f;
-        for (int z = 0; z < splits; ++z) s += part[((size_t)z * N + r) * K + c];
+#pragma unroll 8
+        for (int z = 0; z < splits; ++z) s += part[((size_t)z * N + r) * K + c];  // loads in flight together
         gW[q] = s;
     }
 }

@@ -69,6 +69,18 @@ __device__ __forceinline__ double group_sum(double v)
     return v;
 }
 
+// A step whose segment will be rolled back anyway: the contact list went stale in
+// an earlier step (the mark is in *p.stale, or in the error word of an earlier
+// kernel), or a rebuild overflowed the candidate list.  Every block reads values
+// that only earlier kernels wrote (block 0 of k_step adds PDE_SKIN to the error
+// word only when *p.stale is set), so all blocks of a launch agree and return
+// together; the rest of the segment then costs little more than its launches.
+__device__ __forceinline__ bool segment_doomed(const StepParams &p)
+{
+    return (p.contact && *(volatile const int *)p.stale) ||
+           (*(volatile const unsigned *)p.err & (PDE_SKIN | PDE_CAPACITY));
+}
+
 // Wall cap force on a node at p (Sec. 4.1).  Returns error bits.
 // ---- Several walls (Sec. 4.1.1) ------------------------------------------------
 // In a frame whose axes point out through each wall, the part of the ball
@@ -429,6 +441,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_GLOBAL) k_pairs_upper(co
 {
     constexpr int GPB = STEP_THREADS / G;
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
+    if (segment_doomed(p)) return;
     for (int64_t r0 = (int64_t)blockIdx.x * GPB; r0 < p.n; r0 += (int64_t)gridDim.x * GPB) {
         const int64_t row = r0 + grp;
         float fbx = 0.f, fby = 0.f, fbz = 0.f;
@@ -1063,6 +1076,7 @@ __global__ void __launch_bounds__(STEP_THREADS, MIXED ? PD_MINB_GLOBAL : 2) k_st
         s_err = 0;
         if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
     }
+    if (segment_doomed(p)) return;  // uniform over the grid (see segment_doomed)
     __syncthreads();
     unsigned err = 0;
     double vmax2 = 0.0;
@@ -1292,6 +1306,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
         s_err = 0;
         if (blockIdx.x == 0 && p.contact && *p.stale) atomicOr(p.err, (unsigned)PDE_SKIN);
     }
+    if (segment_doomed(p)) return;  // uniform over the grid (see segment_doomed)
     __syncthreads();
     unsigned err = 0;
     double vmax2 = 0.0;

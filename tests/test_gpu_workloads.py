@@ -47,3 +47,28 @@ def test_workload_lists_and_trajectory(pd, name):
     assert np.abs(ref.react).max() > 0, "the top wall should push"
     assert np.linalg.norm(wf - ref.react) / np.linalg.norm(ref.react) < 1e-5
     ctx.close()
+
+
+def test_hollow_crush_small_against_oracle(pd):
+    """The hollow-sphere crushing run (crush.py) on a reduced shell (R = 14 h, r = 9 h):
+    200 steps, before any bond breaks, recorded every 20 steps.  The plate-force
+    curve (time-averaged wall forces of each record interval) follows the oracle's,
+    and the first 200 steps taken as one captured graph end in the recorded run's
+    state bit for bit."""
+    from paper_2506_05362_gb300 import crush as C
+    sc = S.hollow(outer_cells=14, inner_cells=9)
+    ref = oracle.Model.from_scenario(sc)
+    dt = 0.8 * ref.stable_dt()
+    res = C.crush(sc, dt=dt, graph_steps=200, strain_end=0.0, record_every=20)
+    assert res["graph_equal_to_recorded"]
+    ref.init()
+    F = []
+    for _ in range(len(res["t"])):
+        ref.step(dt, 20)
+        F.append(ref.bulk_stress_mean([sc.wall_area] * 2)[1][:, 2].copy())
+    F = np.array(F)
+    assert ref.broken.sum() == 0, "the window should end before damage"
+    got = np.stack([res["force_top"], res["force_bottom"]], 1)
+    assert np.abs(F).max() > 0
+    assert np.linalg.norm(got - F) / np.linalg.norm(F) < 1e-5
+    assert np.allclose(res["strain"][-1], (2 * 5.0 * 200 * dt) / res["diameter"], rtol=1e-9)
