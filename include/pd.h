@@ -289,8 +289,8 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
  * checked on the device before anything is applied: a non-finite value in
  * either returns PD_EINVAL and leaves the whole state unchanged.  Every given
  * part is also compared on the device with the current state; when applying it
- * would leave the state bit for bit as it is (a state that pd_get_state
- * returned, sent back unchanged) and the material has no velocity-dependent
+ * would leave the state as it is (a state that pd_get_state returned, sent back
+ * unchanged; zeros of either sign count as equal) and the material has no velocity-dependent
  * forces (beta_d = 0, mu = 0), nothing is applied and the force evaluation is
  * skipped: the stored acceleration is the one an evaluation at this state gives,
  * so the call leaves the trajectory bit for bit as it would have been.  With

@@ -557,18 +557,19 @@ __global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
-// true unless the double-float pair (h, l) is bit for bit the split of x that
-// applying x would store
+// true unless the double-float pair (h, l) equals the split of x that applying x
+// would store (compared as values: a zero part may carry either sign, which no
+// later operation on a nonzero value can tell apart)
 __device__ __forceinline__ bool pair_differs(double x, float h, float l)
 {
     const df s = df_from_double(x);
-    return (__float_as_uint(s.hi) != __float_as_uint(h)) | (__float_as_uint(s.lo) != __float_as_uint(l));
+    return (s.hi != h) | (s.lo != l);
 }
 
 // flag |= bit when applying the caller-order doubles `staged` would change the
 // current state: on the mixed path the double-float pairs (hi, lo) at stride
-// `stride` are compared bit for bit with the split of the staged values, else the
-// FP64 array d64 with the values themselves (bit for bit)
+// `stride` are compared with the split of the staged values, else the FP64 array
+// d64 with the values themselves
 __global__ void k_state_differs(const double *__restrict__ staged, const int32_t *__restrict__ perm, int64_t n,
                                 const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride,
                                 const dbl4 *__restrict__ d64, unsigned bit, unsigned *flag)
@@ -582,9 +583,7 @@ __global__ void k_state_differs(const double *__restrict__ staged, const int32_t
                     pair_differs(staged[3 * i + 2], h.z, l.z);
         } else {
             const dbl4 q = d64[k];
-            diff |= (__double_as_longlong(q.x) != __double_as_longlong(staged[3 * i])) |
-                    (__double_as_longlong(q.y) != __double_as_longlong(staged[3 * i + 1])) |
-                    (__double_as_longlong(q.z) != __double_as_longlong(staged[3 * i + 2]));
+            diff |= (q.x != staged[3 * i]) | (q.y != staged[3 * i + 1]) | (q.z != staged[3 * i + 2]);
         }
     }
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);

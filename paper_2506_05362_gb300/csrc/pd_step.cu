@@ -365,9 +365,12 @@ __device__ __forceinline__ void bond_mixed_flagged(const StepParams &p, int k, i
         atomicOr(p.brk + (k >> 5), 1u << (k & 31));
     }
     // a0.w holds c V_j (the record's volume slot is scaled at bond build); the
-    // conic micromodulus multiplies by delta - |xi| (uniform branch)
-    float g = (intact && !brk) ? a0.w * s * ry : 0.f;
+    // conic micromodulus multiplies by delta - |xi| (uniform branch).  The mask
+    // comes last, so that a masked slot adds exactly zero whatever its arithmetic
+    // gave (a padding slot may even gather the row's own record)
+    float g = a0.w * s * ry;
     if (p.conic) g *= p.delta_f - L2 * rL;
+    g = (intact && !brk) ? g : 0.f;
     const float2 f = __ffma2_rn(make_float2(g, g), yxy, make_float2(fbx, fby));
     fbx = f.x;
     fby = f.y;
@@ -847,8 +850,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 const int k = i0 + gl;
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
+                    // a slot past the row end gathers the first slot's node, flagged
                     const int kq = k + q * G;
-                    raw[q] = kq < i1 ? __ldg(p.colf + kq) : (int32_t)0x80000000u;
+                    raw[q] = kq < i1 ? __ldg(p.colf + kq)
+                                     : (q == 0 ? (int32_t)0x80000000u : (int32_t)((uint32_t)raw[0] | 0x80000000u));
                 }
             }
             for (int k = i0 + gl; k < i1; k += PD_INFLIGHT_PF * G) {
@@ -863,9 +868,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 int32_t nxt[PD_INFLIGHT_PF];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
-                    // a slot past the row end gathers node 0 and is flagged (no force)
+                    // a slot past the row end gathers this batch's first node (a
+                    // neighbour of the row), flagged: no force
                     const int kq = k + (PD_INFLIGHT_PF + q) * G;
-                    nxt[q] = kq < i1 ? __ldg(p.colf + kq) : (int32_t)0x80000000u;
+                    nxt[q] = kq < i1 ? __ldg(p.colf + kq) : (int32_t)((uint32_t)raw[0] | 0x80000000u);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT_PF; ++q)

@@ -428,6 +428,31 @@ def study_aggregates(n_aggregates: int = 25, grain_counts=(50, 100), epochs: int
     return _fit_and_judge(runs, fit, vr, hr, fit + vr, t_data, epochs, seed, device, None)
 
 
+def scaling_aggregates(runs, train_sizes, held: int = 3, val: int = 2, epochs: int = 400, seed: int = 0,
+                       device: int = 0):
+    """Held-out error against the number of training aggregates, on one fixed
+    held-out set: the last ``held`` aggregates of ``runs`` (all their paths) are
+    judged, the ``val`` before them stop the training early, and the network is
+    trained on the first n aggregates for every n in ``train_sizes``.  Returns the
+    reports and the least-squares slope of log(median error) on log(n)."""
+    P = len(LOADING_PATHS)
+    n_ag = len(runs) // P
+    n_fit_max = n_ag - held - val
+    vr = runs[n_fit_max * P:(n_fit_max + val) * P]
+    hr = runs[(n_fit_max + val) * P:]
+    reps = []
+    for n in train_sizes:
+        assert 0 < n <= n_fit_max
+        fit = runs[:n * P]
+        rep = _fit_and_judge(runs, fit, vr, hr, fit + vr, 0.0, epochs, seed, device, None)
+        rep["train_aggregates"] = n
+        reps.append(rep)
+    x = np.log([r["train_aggregates"] for r in reps])
+    y = np.log([r["err_median"] for r in reps])
+    slope = float(np.polyfit(x, y, 1)[0]) if len(reps) > 1 else float("nan")
+    return reps, slope
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -449,6 +474,10 @@ if __name__ == "__main__":
                     help="confining pressure that ends the isotropic pre-compression, Pa")
     ap.add_argument("--held", type=int, default=3)
     ap.add_argument("--val", type=int, default=2)
+    ap.add_argument("--train-sizes", type=int, nargs="+", default=None,
+                    help="with --aggregates: train on the first n aggregates for each n, one fixed held-out set")
+    ap.add_argument("--generate-only", action="store_true",
+                    help="with --aggregates and --runs-file: extend the runs file and stop")
     a = ap.parse_args()
     import os
     if a.aggregates > 0:
@@ -461,6 +490,21 @@ if __name__ == "__main__":
                                   zeta=a.zeta, p_confine=a.p_confine)
             if a.runs_file:
                 save_runs(a.runs_file, runs)
+        if a.generate_only:
+            print(json.dumps({"aggregates": len(runs) // P, "runs": len(runs)}))
+            raise SystemExit(0)
+        if a.train_sizes:
+            reps, slope = scaling_aggregates(runs[:a.aggregates * P], a.train_sizes, held=a.held, val=a.val,
+                                             epochs=a.epochs, seed=a.seed)
+            out = {"slope_log_err_vs_log_n": slope,
+                   "by_size": [{k: v for k, v in r.items() if k != "held"} for r in reps],
+                   "held_by_size": [r["held"] for r in reps]}
+            if a.out:
+                with open(a.out, "w") as f:
+                    json.dump(out, f, indent=1)
+            print(json.dumps({"slope": slope, "sizes": [(r["train_aggregates"], r["err_median"], r["err_max"],
+                                                          r["err_mean_history_median"]) for r in reps]}))
+            raise SystemExit(0)
         rep = study_aggregates(a.aggregates, grain_counts=tuple(a.grains), epochs=a.epochs, records=a.records, h=h,
                                seed=a.seed, zeta=a.zeta, held=a.held, val=a.val, runs=runs[:a.aggregates * P],
                                p_confine=a.p_confine)
