@@ -139,6 +139,12 @@ typedef struct {
                                             1 = on, -1 = off, 0 = chosen by the library.  Applies
                                             to the per-slot global-gather kernels; ignored while
                                             profiling. */
+    int barrier_absent;                  /* test aid, 0 in use: the grid-wide barrier of the
+                                            multi-step kernel waits for this many more blocks
+                                            than it launches, so that its bounded wait (1 s)
+                                            runs out: pd_step then returns PD_ETIMEOUT, the
+                                            state of the segment's start is restored, and the
+                                            error is latched until pd_set_state. */
 } pd_options;
 
 /* A rigid plane (Sec. 4.1).  normal points into the domain (unit length). */

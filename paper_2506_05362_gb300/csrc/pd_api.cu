@@ -629,7 +629,7 @@ pd_status pd_create(int64_t n, const double *x, const double *vol, const int32_t
     if (l != 0 && l != 4 && l != 8 && l != 16 && l != 32) { delete c; return PD_EINVAL; }
     if (c->opt.tiles < -1 || c->opt.tiles > 1) { delete c; return PD_EINVAL; }
     if (c->opt.pairs < -1 || c->opt.pairs > 1 || (c->opt.pairs == 1 && c->opt.tiles == 1)) { delete c; return PD_EINVAL; }
-    if (c->opt.persistent < -1 || c->opt.persistent > 1) { delete c; return PD_EINVAL; }
+    if (c->opt.persistent < -1 || c->opt.persistent > 1 || c->opt.barrier_absent < 0) { delete c; return PD_EINVAL; }
     if ((c->opt.alloc == nullptr) != (c->opt.free == nullptr)) { delete c; return PD_EINVAL; }
     if (c->opt.cand_capacity < 0) { delete c; return PD_EINVAL; }
     c->mat = *mat;
@@ -993,7 +993,8 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
             if (full > 1) {
                 cudaMemsetAsync(c->gbar, 0, sizeof(unsigned), c->st);
                 StepParams pa = params(c, MODE_FULL, in, dt), pb = params(c, MODE_FULL, in ^ 1, dt);
-                cudaError_t e = launch_persist(pa, pb, full, c->lanes, pgrid, c->gbar, c->st);
+                cudaError_t e =
+                    launch_persist(pa, pb, full, c->lanes, pgrid, c->gbar, (unsigned)c->opt.barrier_absent, c->st);
                 if (e != cudaSuccess && c->launch_err == cudaSuccess) c->launch_err = e;
                 launches += 2;
                 if (full & 1) in ^= 1;

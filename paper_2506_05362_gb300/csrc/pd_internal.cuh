@@ -159,7 +159,7 @@ void launch_step(const StepParams &p, int lanes, int blocks, cudaStream_t st);
 // several MODE_FULL steps in one cooperative launch (see k_persist)
 int persist_blocks(int lanes, int device, bool mixed, bool wx);
 cudaError_t launch_persist(const StepParams &pa, const StepParams &pb, int nsteps, int lanes, int blocks,
-                           unsigned *bar, cudaStream_t st);
+                           unsigned *bar, unsigned absent, cudaStream_t st);
 void launch_drift(const StepParams &p, cudaStream_t st);
 // double-float state <-> FP64 (mixed path)
 // double-float pair arrays with an element stride (1 for dense, REC for records)

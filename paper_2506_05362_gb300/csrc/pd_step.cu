@@ -1175,7 +1175,7 @@ __device__ __forceinline__ void reduce_reactions(const StepParams &p, const doub
 }
 
 template <int G, bool MIXED, bool WX>
-__device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsigned *bar, unsigned &nbar,
+__device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsigned *bar, unsigned &nbar, unsigned arrivals,
                                              double (*s_react)[PD_MAX_WALLS * 3], double *s_vmax, double *s_wall,
                                              unsigned &s_err, int &s_ok, double &s_disp)
 {
@@ -1183,7 +1183,7 @@ __device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsi
     const int gl = threadIdx.x % G, grp = threadIdx.x / G;
     if (p.pair_diss && p.contact && p.cand_fd) {  // damping and friction of the candidates first
         pair_damping_rows<MIXED>(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
-        if (!grid_barrier(bar, ++nbar * gridDim.x, p.err, &s_ok)) return false;
+        if (!grid_barrier(bar, ++nbar * arrivals, p.err, &s_ok)) return false;
     }
     if (gl == 0)
         for (int q = 0; q < PD_MAX_WALLS * 3; ++q) s_react[grp][q] = 0.0;
@@ -1214,7 +1214,7 @@ __device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsi
         part[PART_STRIDE - 2] = m > 0.0 ? (double)__double2float_ru(m) : 0.0;
         if (s_err) atomicOr(p.err, s_err);
     }
-    if (!grid_barrier(bar, ++nbar * gridDim.x, p.err, &s_ok)) return false;
+    if (!grid_barrier(bar, ++nbar * arrivals, p.err, &s_ok)) return false;
     if (blockIdx.x == 0) reduce_reactions(p, partials, gridDim.x);
     {  // the same bookkeeping in every block: max |v|^2 over the blocks' partials,
        // read by all threads at once (a max does not depend on the order)
@@ -1241,8 +1241,12 @@ __device__ __forceinline__ bool persist_step(const StepParams &p, int step, unsi
 
 template <int G, bool MIXED, bool WX>
 __global__ void __launch_bounds__(STEP_THREADS, 2)
-    k_persist(const __grid_constant__ StepParams pa, const __grid_constant__ StepParams pb, int nsteps, unsigned *bar)
+    k_persist(const __grid_constant__ StepParams pa, const __grid_constant__ StepParams pb, int nsteps, unsigned *bar,
+              unsigned absent)
 {
+    // a barrier is passed once every block has arrived; `absent` (0 in use) adds
+    // arrivals that never come, which tests the bounded wait and its error status
+    const unsigned arrivals = gridDim.x + absent;
     constexpr int GPB = STEP_THREADS / G;
     __shared__ double s_react[GPB][PD_MAX_WALLS * 3];
     __shared__ double s_vmax[GPB];
@@ -1269,7 +1273,8 @@ __global__ void __launch_bounds__(STEP_THREADS, 2)
         // one copy of the step's code for both parities: the parameter block is
         // chosen at run time (grid-constant parameters can be addressed)
         const StepParams &p = (st & 1) ? pb : pa;
-        const bool ok = persist_step<G, MIXED, WX>(p, st, bar, nbar, s_react, s_vmax, s_wall, s_err, s_ok, s_disp);
+        const bool ok =
+            persist_step<G, MIXED, WX>(p, st, bar, nbar, arrivals, s_react, s_vmax, s_wall, s_err, s_ok, s_disp);
         if (!ok) return;
         done = st + 1;
     }
@@ -1510,9 +1515,9 @@ void launch_g(const StepParams &p, int blocks, cudaStream_t st, bool mixed)
 
 template <int G>
 cudaError_t launch_persist_g(const StepParams &pa, const StepParams &pb, int nsteps, int blocks, unsigned *bar,
-                             bool mixed, cudaStream_t st)
+                             unsigned absent, bool mixed, cudaStream_t st)
 {
-    void *args[] = {(void *)&pa, (void *)&pb, (void *)&nsteps, (void *)&bar};
+    void *args[] = {(void *)&pa, (void *)&pb, (void *)&nsteps, (void *)&bar, (void *)&absent};
     const void *fn;
     if (pa.wall_extra)
         fn = mixed ? (const void *)k_persist<G, true, true> : (const void *)k_persist<G, false, true>;
@@ -1589,14 +1594,14 @@ int persist_blocks(int lanes, int device, bool mixed, bool wx)
 // nsteps MODE_FULL steps in one cooperative launch; pa for even steps, pb for odd
 // ones.  bar (one word) must be zero.  Returns the launch status.
 cudaError_t launch_persist(const StepParams &pa, const StepParams &pb, int nsteps, int lanes, int blocks,
-                           unsigned *bar, cudaStream_t st)
+                           unsigned *bar, unsigned absent, cudaStream_t st)
 {
     const bool mixed = pa.xh4 != nullptr;
     switch (lanes) {
-        case 4: return launch_persist_g<4>(pa, pb, nsteps, blocks, bar, mixed, st);
-        case 8: return launch_persist_g<8>(pa, pb, nsteps, blocks, bar, mixed, st);
-        case 16: return launch_persist_g<16>(pa, pb, nsteps, blocks, bar, mixed, st);
-        default: return launch_persist_g<32>(pa, pb, nsteps, blocks, bar, mixed, st);
+        case 4: return launch_persist_g<4>(pa, pb, nsteps, blocks, bar, absent, mixed, st);
+        case 8: return launch_persist_g<8>(pa, pb, nsteps, blocks, bar, absent, mixed, st);
+        case 16: return launch_persist_g<16>(pa, pb, nsteps, blocks, bar, absent, mixed, st);
+        default: return launch_persist_g<32>(pa, pb, nsteps, blocks, bar, absent, mixed, st);
     }
 }
 

@@ -50,7 +50,8 @@ class Options(ctypes.Structure):
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("contact", ctypes.c_int), ("contact_every", ctypes.c_int), ("skin", ctypes.c_double),
                 ("lanes_per_node", ctypes.c_int), ("graph_chunk", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("cand_capacity", ctypes.c_int64), ("pairs", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("cand_capacity", ctypes.c_int64), ("pairs", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("barrier_absent", ctypes.c_int)]
 
 
 class Wall(ctypes.Structure):
@@ -387,7 +388,8 @@ class Context:
 
     def __init__(self, x, vol, grain, material, v0=None, precision="mixed", contact=True,
                  contact_every=0, skin=0.0, lanes=0, chunk=64, device=0, stream=None,
-                 torch_memory=True, tiles=0, cand_capacity=0, allocator=None, pairs=0, persistent=0):
+                 torch_memory=True, tiles=0, cand_capacity=0, allocator=None, pairs=0, persistent=0,
+                 barrier_absent=0):
         import torch
         m = material
         self.material = Material(m.E, m.rho, m.G0, m.contact_radius, m.contact_factor, m.constants,
@@ -416,6 +418,7 @@ class Context:
         o.cand_capacity = int(cand_capacity)
         o.pairs = int(pairs)
         o.persistent = int(persistent)
+        o.barrier_absent = int(barrier_absent)
         self.options = o
         self.n = int(np.asarray(x).reshape(-1, 3).shape[0])
         self.h = pd_create(x, vol, grain, self.material, o, v0)

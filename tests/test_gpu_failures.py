@@ -147,3 +147,31 @@ def test_bad_candidate_capacity_is_rejected(pd):
     with pytest.raises(pd.PDError) as e:
         pd.Context(sc.x, sc.vol, sc.grain, sc.material, cand_capacity=-1)
     assert e.value.status == pd.PD_EINVAL
+
+
+def test_grid_barrier_wait_runs_out_and_is_reported(pd):
+    """The multi-step kernel's grid barrier told to wait for one block more than
+    it launches (pd_options.barrier_absent, a test aid): every wait gives up after
+    1 s of GPU time, the kernel returns with its error bit, pd_step reports
+    PD_ETIMEOUT, the state of the segment's start is restored, the context refuses
+    pd_step until pd_set_state, and the device stays usable."""
+    import time
+    sc = S.sphere()
+    ctx = pd.Context.from_scenario(sc, lanes=8, tiles=-1, pairs=-1, persistent=1, barrier_absent=1)
+    before = ctx.get_state()
+    dt = 0.8 * ctx.stable_dt()
+    t0 = time.perf_counter()
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(dt, 20)
+    assert e.value.status == pd.PD_ETIMEOUT and "barrier" in str(e.value)
+    assert time.perf_counter() - t0 < 60
+    for x, y in zip(ctx.get_state(), before):
+        assert np.array_equal(x, y)
+    with pytest.raises(pd.PDError) as e:
+        ctx.step(dt, 1)
+    assert e.value.status == pd.PD_ESTATE
+    ctx.close()
+    ok = pd.Context.from_scenario(sc, lanes=8, tiles=-1, pairs=-1, persistent=1)
+    ok.step(dt, 20)
+    assert np.all(np.isfinite(ok.get_state()[0]))
+    ok.close()
