@@ -97,3 +97,39 @@ def test_aggregate_steps_finite_and_tuned(agg):
     u, v, broken, t = ctx.get_state()
     assert np.all(np.isfinite(u)) and np.all(np.isfinite(v))
     assert t == pytest.approx(50 * dt, rel=1e-12)
+
+
+def test_aggregate_contacts_sampled(agg):
+    """Contact pairs at full size on sampled rows: the aggregate compressed towards
+    its centre until grains touch (2% strain; no bond breaks in compression), then
+    for each sampled row that has partners the oracle's contact partners, computed
+    on a sub-problem of the nodes near the row (same definition: |p_j - p_i| < R_c,
+    minus same-grain pairs with an intact bond), against the library's pairs.  The
+    library holds u as a double-float pair, so a pair within 1e-9 of the contact
+    radius may decide either way."""
+    sc, ctx = agg
+    u = -0.02 * (sc.x - sc.x.mean(0))
+    ctx.set_state(u=u)
+    pairs = ctx.contacts()
+    assert len(pairs) > 1000
+    p = sc.x + u
+    Rc = sc.material.contact_radius
+    rows_with = np.unique(pairs[:, 0])
+    rng = np.random.default_rng(7)
+    rows = rng.choice(rows_with, 30, replace=False)
+    checked = 0
+    for i in rows:
+        near = np.flatnonzero(((p - p[i]) ** 2).sum(1) < (2.0 * Rc) ** 2)
+        sub = np.unique(np.concatenate([[i], near]))
+        li = int(np.searchsorted(sub, i))
+        rp, col = oracle.bonds(sc.x[sub], sc.grain[sub], sc.horizon)
+        m = oracle.Model(sc.x[sub], sc.vol[sub], sc.grain[sub], rp, col, sc.material, sc.horizon)
+        m.u = u[sub].copy()
+        op = m.contact_pairs()
+        want = set(sub[op[op[:, 0] == li, 1]].tolist())
+        got = set(pairs[pairs[:, 0] == i, 1].tolist())
+        for j in want ^ got:
+            d2 = float(((p[j] - p[i]) ** 2).sum())
+            assert abs(d2 - Rc * Rc) < 1e-9 * Rc * Rc, f"row {i}: partner {j} differs"
+        checked += len(want)
+    assert checked > 30
