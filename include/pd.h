@@ -294,12 +294,14 @@ pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, doubl
  * error and re-evaluates the forces (which may break bonds).  u and v are
  * checked on the device before anything is applied: a non-finite value in
  * either returns PD_EINVAL and leaves the whole state unchanged.  Every given
- * part is also compared on the device with the current state; when applying it
- * would leave the state as it is (a state that pd_get_state returned, sent back
- * unchanged; zeros of either sign count as equal) and the material has no velocity-dependent
- * forces (beta_d = 0, mu = 0), nothing is applied and the force evaluation is
- * skipped: the stored acceleration is the one an evaluation at this state gives,
- * so the call leaves the trajectory bit for bit as it would have been.  With
+ * part is also compared on the device with the current state; when all equal
+ * it in value (a state that pd_get_state returned, sent back unchanged) and the
+ * material has no velocity-dependent forces (beta_d = 0, mu = 0), nothing is
+ * applied and the force evaluation is skipped: the run goes on bit for bit as if
+ * the call had not been made.  (An applied state is held as double-float pairs
+ * split from the given doubles, which may differ in the last bits from the pairs
+ * a run holds; a restored checkpoint therefore reproduces a run that was itself
+ * restored from the same state.)  With
  * damping or friction the forces are always evaluated again (the stored
  * acceleration saw the last step's half-step velocity, the evaluation sees the
  * current one).  The wall impulses of pd_bulk_stress_mean are zeroed in any case.  Errors: PD_EINVAL (non-finite u or v), PD_ESTATE (bond

@@ -557,19 +557,12 @@ __global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
-// true unless the double-float pair (h, l) equals the split of x that applying x
-// would store (compared as values: a zero part may carry either sign, which no
-// later operation on a nonzero value can tell apart)
-__device__ __forceinline__ bool pair_differs(double x, float h, float l)
-{
-    const df s = df_from_double(x);
-    return (s.hi != h) | (s.lo != l);
-}
-
-// flag |= bit when applying the caller-order doubles `staged` would change the
-// current state: on the mixed path the double-float pairs (hi, lo) at stride
-// `stride` are compared with the split of the staged values, else the FP64 array
-// d64 with the values themselves
+// flag |= bit when the caller-order doubles `staged` differ in value from the
+// current state: the double-float pairs (hi, lo) at stride `stride`, each
+// converted by the formula every query uses, when hi is given, else the FP64
+// array d64.  (A pair whose lo lies more than 29 bits below hi does not survive
+// the conversion and back, so the test is on values: a state sent back unchanged
+// keeps its live pairs.)
 __global__ void k_state_differs(const double *__restrict__ staged, const int32_t *__restrict__ perm, int64_t n,
                                 const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride,
                                 const dbl4 *__restrict__ d64, unsigned bit, unsigned *flag)
@@ -577,14 +570,17 @@ __global__ void k_state_differs(const double *__restrict__ staged, const int32_t
     bool diff = false;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[k];
+        double a, b, c;
         if (hi) {
             const float4 h = hi[stride * k], l = lo[stride * k];
-            diff |= pair_differs(staged[3 * i], h.x, l.x) | pair_differs(staged[3 * i + 1], h.y, l.y) |
-                    pair_differs(staged[3 * i + 2], h.z, l.z);
+            a = df_to_double(df{h.x, l.x});
+            b = df_to_double(df{h.y, l.y});
+            c = df_to_double(df{h.z, l.z});
         } else {
             const dbl4 q = d64[k];
-            diff |= (q.x != staged[3 * i]) | (q.y != staged[3 * i + 1]) | (q.z != staged[3 * i + 2]);
+            a = q.x; b = q.y; c = q.z;
         }
+        diff |= (a != staged[3 * i]) | (b != staged[3 * i + 1]) | (c != staged[3 * i + 2]);
     }
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
