@@ -339,6 +339,7 @@ def main():
     b_h = torch.empty(max(nwords, 1), dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
     u0, v0, b0, t0 = pd.pd_get_state_packed(ctx.h, n, B)
     u_h[:] = u0; v_h[:] = v0; b_h[:nwords] = b0
+    sc0 = ctx.state_counters()
     barrier()
     te = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -347,11 +348,13 @@ def main():
         pd.pd_get_state_packed(ctx.h, n, B, u_h, v_h, b_h)
     barrier()
     e2e_s = time.perf_counter() - te
+    sc1 = ctx.state_counters()
     e2e = None
     if args.e2e_steps > 0 and e2e_s > 0:
         e2e = {"value": ws * n * args.e2e_steps / e2e_s, "unit": "node-steps/s",
                "h2d_bytes_per_step": 48 * n + 4 * nwords, "d2h_bytes_per_step": 48 * n + 4 * nwords,
                "steps": args.e2e_steps,
+               "set_state_applied": sc1[0] - sc0[0], "set_state_unchanged": sc1[1] - sc0[1],
                "path": "pd_set_state_packed + pd_step(dt,1) + pd_get_state_packed (u, v, bond memory at one "
                        "bit per bond), pinned host buffers"}
 

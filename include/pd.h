@@ -287,25 +287,33 @@ pd_status pd_contacts(pd_ctx *ctx, int64_t *npairs, int32_t *ij);
 pd_status pd_forces(pd_ctx *ctx, double *F);
 
 /* State for checkpoints and parity: u, v (n*3), broken (B bytes, 1 = broken, in
- * pd_bonds order), t.  Any output may be NULL. */
+ * pd_bonds order), t.  Any output may be NULL.  On the mixed path u and v are
+ * held as double-float pairs kept on the FP64 grid (hi + lo is a double after
+ * every update and every pd_set_state), so the doubles returned are the state
+ * exactly, not a rounding of it. */
 pd_status pd_get_state(pd_ctx *ctx, double *u, double *v, uint8_t *broken, double *t);
 
 /* Sets the state (any input may be NULL to keep it), clears a latched device
  * error and re-evaluates the forces (which may break bonds).  u and v are
  * checked on the device before anything is applied: a non-finite value in
- * either returns PD_EINVAL and leaves the whole state unchanged.  Every given
- * part is also compared on the device with the current state; when all equal
- * it in value (a state that pd_get_state returned, sent back unchanged) and the
- * material has no velocity-dependent forces (beta_d = 0, mu = 0), nothing is
- * applied and the force evaluation is skipped: the run goes on bit for bit as if
- * the call had not been made.  (An applied state is held as double-float pairs
- * split from the given doubles, which may differ in the last bits from the pairs
- * a run holds; a restored checkpoint therefore reproduces a run that was itself
- * restored from the same state.)  With
- * damping or friction the forces are always evaluated again (the stored
- * acceleration saw the last step's half-step velocity, the evaluation sees the
- * current one).  The wall impulses of pd_bulk_stress_mean are zeroed in any case.  Errors: PD_EINVAL (non-finite u or v), PD_ESTATE (bond
- * memory before pd_build_bonds), PD_ECUDA, and those of the force evaluation. */
+ * either returns PD_EINVAL and leaves the whole state unchanged.  Each value is
+ * held as the pair hi = RN(x), lo = x - hi rounded towards zero (hi + lo is x,
+ * or x with its last bits cut, within 2^-47 |x| + 2^-149 of it; the FP64 path
+ * holds x).  Every given part is compared on
+ * the device with the current state first; when applying it would change
+ * nothing (a state that pd_get_state returned, sent back unchanged, on any
+ * path) it is not applied again, and, when the material has no
+ * velocity-dependent forces (beta_d = 0, mu = 0), the force evaluation is
+ * skipped too.  Since the live pairs lie on the FP64 grid, setting a state read
+ * out at step k gives the state the run held at step k, whether the context is
+ * that run's or a fresh one with the same options, walls and time: the run goes
+ * on bit for bit as the uninterrupted one (a checkpoint restart is exact; with damping or friction the stored
+ * acceleration saw the last step's half-step velocity, the re-evaluation sees
+ * the current one, so there the restarted run is the one an uninterrupted run
+ * with a pd_set_state at step k gives).  The wall impulses of
+ * pd_bulk_stress_mean are zeroed in any case.  Errors: PD_EINVAL (non-finite u
+ * or v), PD_ESTATE (bond memory before pd_build_bonds), PD_ECUDA, and those of
+ * the force evaluation. */
 pd_status pd_set_state(pd_ctx *ctx, const double *u, const double *v, const uint8_t *broken,
                        const double *t);
 

@@ -1557,14 +1557,15 @@ static pd_status get_state_impl(pd_ctx *c, double *u, double *v, uint8_t *broken
 }
 
 // Applies a caller state.  Everything given is staged and compared on the device
-// with the current state first: non-finite u or v rejects the call; a state equal
-// in value to the current one (what pd_get_state returned, sent back unchanged) is
-// not applied again, so the live double-float pairs are kept, and, for a material
-// without velocity-dependent forces, its force evaluation is skipped, since the
-// stored acceleration is the one an evaluation at this state gives: the run goes
-// on exactly as if the call had not been made.  With damping or friction the stored
-// acceleration saw the half-step velocity of the last step, so it is evaluated
-// again.
+// with the current state first: non-finite u or v rejects the call; a part that
+// applying would leave as it is (on the mixed path the live pairs lie on the FP64
+// grid, so what pd_get_state returned, sent back unchanged, splits into exactly
+// them) is not applied again, and, for a material without velocity-dependent
+// forces, the force evaluation is skipped as well, since the stored acceleration
+// is the one an evaluation at this state gives: the run goes on exactly as if the
+// call had not been made, which is also how it goes on from the applied state.
+// With damping or friction the stored acceleration saw the half-step velocity of
+// the last step, so it is evaluated again.
 static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, const uint8_t *broken,
                                 const uint32_t *bits, const double *t)
 {

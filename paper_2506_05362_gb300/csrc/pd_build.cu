@@ -557,12 +557,12 @@ __global__ void k_nonfinite(const double *__restrict__ a, int64_t m, unsigned bi
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
-// flag |= bit when the caller-order doubles `staged` differ in value from the
-// current state: the double-float pairs (hi, lo) at stride `stride`, each
-// converted by the formula every query uses, when hi is given, else the FP64
-// array d64.  (A pair whose lo lies more than 29 bits below hi does not survive
-// the conversion and back, so the test is on values: a state sent back unchanged
-// keeps its live pairs.)
+// flag |= bit when applying the caller-order doubles `staged` would change the
+// current state: on the mixed path, when the split of a staged value (the one
+// applying uses) differs from the live pair (hi, lo) at stride `stride`; else when
+// it differs from the FP64 array d64.  The halves are compared as numbers (a zero
+// of either sign counts as equal).  The live pairs lie on the FP64 grid, so a
+// state read out and sent back unchanged splits into exactly the live pairs.
 __global__ void k_state_differs(const double *__restrict__ staged, const int32_t *__restrict__ perm, int64_t n,
                                 const float4 *__restrict__ hi, const float4 *__restrict__ lo, int stride,
                                 const dbl4 *__restrict__ d64, unsigned bit, unsigned *flag)
@@ -570,17 +570,16 @@ __global__ void k_state_differs(const double *__restrict__ staged, const int32_t
     bool diff = false;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = perm[k];
-        double a, b, c;
+        const double a = staged[3 * i], b = staged[3 * i + 1], c = staged[3 * i + 2];
         if (hi) {
             const float4 h = hi[stride * k], l = lo[stride * k];
-            a = df_to_double(df{h.x, l.x});
-            b = df_to_double(df{h.y, l.y});
-            c = df_to_double(df{h.z, l.z});
+            const df sa = df_from_double(a), sb = df_from_double(b), sc = df_from_double(c);
+            diff |= (sa.hi != h.x) | (sa.lo != l.x) | (sb.hi != h.y) | (sb.lo != l.y) | (sc.hi != h.z) |
+                    (sc.lo != l.z);
         } else {
             const dbl4 q = d64[k];
-            a = q.x; b = q.y; c = q.z;
+            diff |= (a != q.x) | (b != q.y) | (c != q.z);
         }
-        diff |= (a != staged[3 * i]) | (b != staged[3 * i + 1]) | (c != staged[3 * i + 2]);
     }
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }

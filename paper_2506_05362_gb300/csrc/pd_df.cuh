@@ -68,14 +68,41 @@ __device__ __forceinline__ df df_mul(df a, df b)
     return r;
 }
 
+// The state pairs (u and v of every node) are kept on the FP64 grid: hi + lo is
+// exactly a double, and splitting that double again gives the same pair.  A pair
+// is then converted to FP64 and back without change, so a state read out and sent
+// back is recognised as the live one, and a run restarted from a saved state goes
+// on bit for bit as the uninterrupted run.
+//
+// df_from_double(x): hi = RN(x), lo = x - hi rounded towards zero.  hi + lo is a
+// double (lo is either x - hi itself, when that fits 24 bits, or its truncation,
+// whose last bit then lies at or above the double grid of x), and |lo| reaches
+// ulp(hi)/2 only when x - hi is exactly that tie, which RN resolved to an even
+// hi; so RN(hi + lo) = hi and the split of hi + lo is the pair again.
 __device__ __forceinline__ df df_from_double(double x)
 {
     df r;
     r.hi = __double2float_rn(x);
-    r.lo = __double2float_rn(x - (double)r.hi);
+    r.lo = __double2float_rz(__dsub_rn(x, (double)r.hi));
     return r;
 }
 
-// the double nearest hi + lo (exact whenever lo lies within 29 bits of hi); every
-// kernel converts with this one formula, so all see the same FP64 value
+// A normalised pair (RN(hi + lo) = hi, as a two-sum leaves it) moved onto the FP64
+// grid: lo replaced by RN64(hi + lo) - hi.  That difference is exact in FP64 and
+// fits FP32 (it is lo itself, or lo rounded to a multiple of 2^(e - 52) with e the
+// exponent of hi + lo and |lo| below 2^(e - 29)), so hi + lo becomes exactly the
+// double nearest the old pair, moving it by at most 2^-53 of its value.  Only a lo
+// more than 28 binades below hi can lie off the grid (a 24-bit lo at least 2^(e-29)
+// in size has its last bit on it); the others, and hi = 0, are left as they are.
+__device__ __forceinline__ df df_on_fp64_grid(df a)
+{
+    if (fabsf(a.lo) < __fmul_rn(fabsf(a.hi), 0x1p-28f)) {
+        const double h = (double)a.hi;
+        a.lo = __double2float_rn(__dsub_rn(__dadd_rn(h, (double)a.lo), h));
+    }
+    return a;
+}
+
+// the double nearest hi + lo (exact for the state pairs, which lie on the FP64
+// grid); every kernel converts with this one formula, so all see the same value
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }

@@ -521,12 +521,14 @@ __device__ __forceinline__ unsigned epilogue_component(const StepParams &p, int6
     const df hdt{p.hdt_hi, p.hdt_lo};
     const float vhc = c == 0 ? vh.x : (c == 1 ? vh.y : vh.z);
     const float vlc = c == 0 ? vl.x : (c == 1 ? vl.y : vl.z);
-    df v = df_add(df{vhc, vlc}, df_mul_f(hdt, a));
+    // every pair the step stores, or would store when split into single-step
+    // calls, is put on the FP64 grid
+    df v = df_on_fp64_grid(df_add(df{vhc, vlc}, df_mul_f(hdt, a)));
     if (p.mode == MODE_FULL) {
-        v = df_add(v, df_mul_f(hdt, a));
+        v = df_on_fp64_grid(df_add(v, df_mul_f(hdt, a)));
         const float uhc = c == 0 ? uh.x : (c == 1 ? uh.y : uh.z);
         const float ulc = c == 0 ? ul.x : (c == 1 ? ul.y : ul.z);
-        const df u = df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v));
+        const df u = df_on_fp64_grid(df_add(df{uhc, ulc}, df_mul(df{p.dt_hi, p.dt_lo}, v)));
         ((float *)(p.uh_out + REC * row))[c] = u.hi;
         ((float *)(p.ul_out + REC * row))[c] = u.lo;
         if (c == 0) {  // packed x_lo travels with the record
@@ -1412,12 +1414,12 @@ __global__ void k_drift(const StepParams p)
         if (MIXED) {
             const float4 a = p.af[i], vh = p.vh[i], vl = p.vl[i], uh = p.uh_in[REC * i], ul = p.ul_in[REC * i];
             const df h{p.hdt_hi, p.hdt_lo}, dt{p.dt_hi, p.dt_lo};
-            const df vx = df_add(df{vh.x, vl.x}, df_mul_f(h, a.x));
-            const df vy = df_add(df{vh.y, vl.y}, df_mul_f(h, a.y));
-            const df vz = df_add(df{vh.z, vl.z}, df_mul_f(h, a.z));
-            const df ux = df_add(df{uh.x, ul.x}, df_mul(dt, vx));
-            const df uy = df_add(df{uh.y, ul.y}, df_mul(dt, vy));
-            const df uz = df_add(df{uh.z, ul.z}, df_mul(dt, vz));
+            const df vx = df_on_fp64_grid(df_add(df{vh.x, vl.x}, df_mul_f(h, a.x)));
+            const df vy = df_on_fp64_grid(df_add(df{vh.y, vl.y}, df_mul_f(h, a.y)));
+            const df vz = df_on_fp64_grid(df_add(df{vh.z, vl.z}, df_mul_f(h, a.z)));
+            const df ux = df_on_fp64_grid(df_add(df{uh.x, ul.x}, df_mul(dt, vx)));
+            const df uy = df_on_fp64_grid(df_add(df{uh.y, ul.y}, df_mul(dt, vy)));
+            const df uz = df_on_fp64_grid(df_add(df{uh.z, ul.z}, df_mul(dt, vz)));
             p.vh[i] = make_float4(vx.hi, vy.hi, vz.hi, 0.f);
             p.vl[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
             p.uh_out[REC * i] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);

@@ -488,6 +488,38 @@ def test_set_state_of_the_current_state_is_skipped(pd):
     a.close(); b.close()
 
 
+@pytest.mark.parametrize("name", ["sphere", "kalthoff_small", "aggregate_small"])
+@pytest.mark.parametrize("kernel", ["global", "tiled", "pairs"])
+def test_checkpoint_restart_is_exact(pd, name, kernel):
+    """A fresh context given a state read out at step k (u, v, bond memory, time
+    and wall points) goes on bit for bit as the run it was read from: the live
+    double-float pairs lie on the FP64 grid, so the doubles read out are the
+    state itself, not a rounding of it.  Sent back to the running context, the
+    same state is recognised as unchanged."""
+    sc = SCENARIOS[name]()
+    kw = dict(lanes=8, **KERNEL[kernel])
+    a = pd.Context.from_scenario(sc, **kw)
+    dt = 0.8 * a.stable_dt()
+    a.step(dt, 37)
+    u, v, broken, t = a.get_state()
+    w = a.get_walls() if sc.walls else None
+    b = pd.Context.from_scenario(sc, **kw)
+    if sc.walls:
+        wb = S.walls_array(sc.walls)
+        wb[:, 3:6] = w
+        b.set_walls(wb)
+    b.set_state(u=u, v=v, broken=broken, t=t)
+    a.set_state(u=u, v=v, broken=broken, t=t)
+    assert a.state_counters() == (0, 1)
+    a.step(dt, 41)
+    b.step(dt, 41)
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    if sc.walls:
+        assert np.array_equal(a.get_walls(), b.get_walls())
+    a.close(); b.close()
+
+
 def test_damage_and_stable_dt_match(pd):
     sc = S.small_block(nx=9, ny=7, nz=5, jitter=0.05)
     ctx = pd.Context.from_scenario(sc, contact=False)
