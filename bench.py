@@ -479,7 +479,7 @@ def bench_surrogate(local, stream, reps=20):
 def kernel_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ["pd_step.cu", "pd_internal.cuh"]:
+    for f in ["pd_step.cu", "pd_internal.cuh", "pd_df.cuh"]:
         h.update(open(os.path.join(ROOT, "paper_2506_05362_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

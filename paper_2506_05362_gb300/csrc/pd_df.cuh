@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 struct df {
     float hi, lo;
@@ -88,17 +89,26 @@ __device__ __forceinline__ df df_from_double(double x)
 }
 
 // A normalised pair (RN(hi + lo) = hi, as a two-sum leaves it) moved onto the FP64
-// grid: lo replaced by RN64(hi + lo) - hi.  That difference is exact in FP64 and
-// fits FP32 (it is lo itself, or lo rounded to a multiple of 2^(e - 52) with e the
-// exponent of hi + lo and |lo| below 2^(e - 29)), so hi + lo becomes exactly the
-// double nearest the old pair, moving it by at most 2^-53 of its value.  Only a lo
-// more than 28 binades below hi can lie off the grid (a 24-bit lo at least 2^(e-29)
-// in size has its last bit on it); the others, and hi = 0, are left as they are.
+// grid: lo replaced by RN64(hi + lo) - hi, which is exact in FP64 and fits FP32, so
+// hi + lo becomes exactly the double nearest the old pair (a move of at most 2^-53
+// of the value).  It is computed in FP32, without FP64 instructions: the grid of
+// hi + lo has spacing q = 2^(e - 52), e the exponent of hi + lo (that of hi, one less
+// when hi is a power of two and lo points towards zero); only a lo below 2^23 q in
+// size can have bits under q, and for it adding and subtracting M = 2^23 q (with
+// lo's sign) rounds it to a multiple of q, nearest and ties to even, as RN64 does
+// (hi / q is even).  hi = 0, or a grid finer than FP32's smallest subnormal, leaves
+// the pair as it is.
 __device__ __forceinline__ df df_on_fp64_grid(df a)
 {
-    if (fabsf(a.lo) < __fmul_rn(fabsf(a.hi), 0x1p-28f)) {
-        const double h = (double)a.hi;
-        a.lo = __double2float_rn(__dsub_rn(__dadd_rn(h, (double)a.lo), h));
+    const uint32_t hb = __float_as_uint(a.hi), lb = __float_as_uint(a.lo);
+    int eq = (int)((hb >> 23) & 0xffu) - 127 - 52;  // log2 q
+    if ((hb & 0x7fffffu) == 0u && ((hb ^ lb) & 0x80000000u) && a.lo != 0.f) eq -= 1;
+    if (eq >= -149) {
+        const float t = __uint_as_float((uint32_t)(eq + 23 + 127) << 23);  // 2^23 q, a normal FP32
+        if (fabsf(a.lo) < t) {
+            const float m = __uint_as_float(__float_as_uint(t) | (lb & 0x80000000u));
+            a.lo = __fsub_rn(__fadd_rn(a.lo, m), m);
+        }
     }
     return a;
 }

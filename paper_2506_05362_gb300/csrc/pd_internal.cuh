@@ -39,7 +39,20 @@ struct WallSet {
 };
 
 // Everything the force/update kernels need, passed by value.
-constexpr int REC = 3;  // float4 per mixed-path node record
+// Mixed-path node records: three float4 slots per node, (x_hi, c V), (u_hi,
+// packed x_lo.xy) and (u_lo, packed x_lo.z).  PD_PLANES = 1 (the default) keeps
+// three planes of n float4 (slot s of node i at [s n + i]), so that the lanes of a
+// group gathering neighbours that are consecutive in the node order read one
+// contiguous run per slot; PD_PLANES = 0 interleaves them (one 48-byte record per
+// node, slot s of node i at [3 i + s]).  Both give the same bits; the planes were
+// 1-2% faster per force evaluation on the plate and the hollow sphere and equal on
+// the aggregate (GB300, CUDA events).
+#ifndef PD_PLANES
+#define PD_PLANES 1
+#endif
+constexpr int REC = PD_PLANES ? 1 : 3;  // element stride of a record slot
+constexpr int REC_SLOTS = 3;            // float4 per node record
+__host__ __device__ inline int64_t rec_plane(int64_t n) { return PD_PLANES ? n : 1; }  // slot-to-slot offset
 
 struct StepParams {
     int64_t n;
@@ -47,13 +60,12 @@ struct StepParams {
     const int32_t *col;
     uint32_t *brk;                 // broken bit per directed slot
     // mixed path: x, u, v as double-float pairs (hi, lo), a in FP32
-    // mixed-path node records, REC float4 per node, interleaved so that one
-    // neighbour gather is one 48-byte record: [REC*i] = (x_hi, c V) with x
-    // relative to the bounding-box centre (static; c V set at bond build), [REC*i+1] = (u_hi, packed x_lo.xy),
-    // [REC*i+2] = (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
-    const float4 *xh4;             // record base of the current buffer (index REC*i)
+    // mixed-path node records (layout above): (x_hi, c V) with x relative to the
+    // bounding-box centre (static; c V set at bond build), (u_hi, packed x_lo.xy),
+    // (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
+    const float4 *xh4;             // x slots of the current buffer (index REC*i)
     const float4 *xl4;             // (x_lo, 0), dense
-    const float4 *uh_in, *ul_in;   // = xh4 + 1, xh4 + 2 (index REC*i)
+    const float4 *uh_in, *ul_in;   // = xh4 + plane, xh4 + 2 plane (index REC*i)
     float4 *uh_out, *ul_out;       // next buffer's u slots (index REC*i)
     float4 *vh, *vl;               // v (in place)
     float4 *af;                    // a = (F + b)/rho, stored for the next drift

@@ -319,9 +319,11 @@ __global__ void k_loss_final(const float *__restrict__ partial, int nb, int64_t 
 
 // row sums of dZ^T (bf16 [n x ld], first `rows` columns) into gb: the bias
 // gradient from the transposed copy, with coalesced reads; fixed order
-__global__ void k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld, int n_valid, float *gb)
+constexpr int RS_THREADS = 1024;  // one block per column; two blocks fit an SM, so the columns take one wave
+__global__ void __launch_bounds__(RS_THREADS) k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld,
+                                                       int n_valid, float *gb)
 {
-    __shared__ float s[256];
+    __shared__ float s[RS_THREADS];
     const int c = blockIdx.x;
     float acc = 0.f;
     const bf16 *r = dZT + (int64_t)c * ld;  // ld is a multiple of 8: rows start 16-byte aligned
@@ -351,26 +353,49 @@ __global__ void k_rowsum(const bf16 *__restrict__ dZT, int64_t rows, int64_t ld,
     for (int64_t q = 8 * r8 + threadIdx.x; q < rows; q += blockDim.x) acc += __bfloat162float(r[q]);
     s[threadIdx.x] = acc;
     __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
+    for (int o = RS_THREADS / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
         __syncthreads();
     }
     if (threadIdx.x == 0 && c < n_valid) gb[c] = s[0];
 }
 
-// fixed-order sum of split-K partials into the gradient vector; rows < n_valid, cols < k_valid
-__global__ void k_reduce_dw(const float *__restrict__ part, int splits, int N, int K, int n_valid, int k_valid,
-                            float *gW)
+// fixed-order sum of split-K partials into the gradient vector; rows < n_valid,
+// cols < k_valid.  A block takes 32 consecutive outputs at a time with RD_PARTS
+// warps: warp p adds splits p, p + RD_PARTS, p + 2 RD_PARTS, ... in that order
+// (each a 128-byte load of the 32 outputs, several in flight), then warp 0 adds
+// the RD_PARTS sums in order.  Many loads in flight per output instead of one
+// thread walking all splits.
+constexpr int RD_PARTS = 8;
+__global__ void __launch_bounds__(32 * RD_PARTS) k_reduce_dw(const float *__restrict__ part, int splits, int N, int K,
+                                                             int n_valid, int k_valid, float *gW)
 {
+    __shared__ float s[RD_PARTS][33];
+    const int lane = threadIdx.x & 31, pp = threadIdx.x >> 5;
     const int64_t total = (int64_t)n_valid * k_valid;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(q / k_valid), c = (int)(q % k_valid);
-        float s = 0.f;
-#pragma unroll 8
-        for (int z = 0; z < splits; ++z) s += part[((size_t)z * N + r) * K + c];  // loads in flight together
-        gW[q] = s;
+    const size_t zs = (size_t)N * K;
+    for (int64_t q0 = (int64_t)blockIdx.x * 32; q0 < total; q0 += (int64_t)gridDim.x * 32) {
+        const int64_t q = q0 + lane;
+        float acc = 0.f;
+        if (q < total) {
+            const int r = (int)(q / k_valid), c = (int)(q % k_valid);
+            const float *src = part + (size_t)r * K + c;
+#pragma unroll 4
+            for (int z = pp; z < splits; z += RD_PARTS) acc += src[(size_t)z * zs];
+        }
+        s[pp][lane] = acc;
+        __syncthreads();
+        if (pp == 0 && q < total) {
+            float t = s[0][lane];
+#pragma unroll
+            for (int w = 1; w < RD_PARTS; ++w) t += s[w][lane];
+            gW[q] = t;
+        }
+        __syncthreads();
     }
 }
+
+inline int rd_blocks(int64_t total) { return (int)std::min<int64_t>((total + 31) / 32, 8192); }
 
 // column sums of dZ (bf16, [rows x ld]) into gb (first n_valid), fixed order
 __global__ void k_colsum(const bf16 *__restrict__ dZ, int64_t rows, int ld, int n_valid, float *gb)
@@ -625,9 +650,9 @@ int backward_tc(pd_mlp *m, const float *X, const float *T, int64_t rows, float *
         const int splits = mlp_dw_tc(m->dZT[l], m->HT[l], rows, m->ldT, N, K, m->part, max_splits, m->tc_err,
                                      m->device, m->st);
         if (splits <= 0) return -2;
-        k_reduce_dw<<<grid1((int64_t)m->dims[l + 1] * m->dims[l]), 256, 0, m->st>>>(
+        k_reduce_dw<<<rd_blocks((int64_t)m->dims[l + 1] * m->dims[l]), 32 * RD_PARTS, 0, m->st>>>(
             m->part, splits, N, K, m->dims[l + 1], m->dims[l], m->grad + m->woff[l]);
-        k_rowsum<<<m->dims[l + 1], 256, 0, m->st>>>(m->dZT[l], rows, m->ldT, m->dims[l + 1], m->grad + m->boff[l]);
+        k_rowsum<<<m->dims[l + 1], RS_THREADS, 0, m->st>>>(m->dZT[l], rows, m->ldT, m->dims[l + 1], m->grad + m->boff[l]);
         if (l > 0 && mlp_dgelu_tc(m->dZ[l], m->WT[l], m->Z[l - 1], rows, K, N, m->dZ[l - 1], m->dZT[l - 1], m->ldT,
                                   m->tc_err, m->device, m->st))
             return -2;
@@ -671,7 +696,7 @@ pd_status backward_dev(pd_mlp *m, const float *X, const float *T, int64_t rows, 
         g.ksplit = (int)ks;
         g.out = m->part; g.ldo = K;
         gemm<true, true, EPI_PARTIAL>(g, splits, m->st);
-        k_reduce_dw<<<grid1((int64_t)m->dims[l + 1] * m->dims[l]), 256, 0, m->st>>>(
+        k_reduce_dw<<<rd_blocks((int64_t)m->dims[l + 1] * m->dims[l]), 32 * RD_PARTS, 0, m->st>>>(
             m->part, splits, N, K, m->dims[l + 1], m->dims[l], m->grad + m->woff[l]);
         k_colsum<<<m->dims[l + 1], 256, 0, m->st>>>(m->dZ[l], rows, N, m->dims[l + 1], m->grad + m->boff[l]);
         if (l > 0) {

@@ -469,8 +469,8 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_GLOBAL) k_pairs_upper(co
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
                     const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
                     a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + 1);
-                    a2[q] = __ldg(rj + 2);
+                    a1[q] = __ldg(rj + rec_plane(p.n));
+                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)
@@ -823,8 +823,8 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
                     const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
                     a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + 1);
-                    a2[q] = __ldg(rj + 2);
+                    a1[q] = __ldg(rj + rec_plane(p.n));
+                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
@@ -862,10 +862,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 float4 a0[PD_INFLIGHT_PF], a1[PD_INFLIGHT_PF], a2[PD_INFLIGHT_PF];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
-                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);  // one 48-byte record
+                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);  // one node record
                     a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + 1);
-                    a2[q] = __ldg(rj + 2);
+                    a1[q] = __ldg(rj + rec_plane(p.n));
+                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
                 }
                 int32_t nxt[PD_INFLIGHT_PF];
 #pragma unroll
@@ -895,10 +895,10 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
                     const int j = raw[q] & 0x7fffffff;
-                    const float4 *rj = p.xh4 + REC * j;  // one 48-byte record
+                    const float4 *rj = p.xh4 + REC * j;  // one node record
                     a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + 1);
-                    a2[q] = __ldg(rj + 2);
+                    a1[q] = __ldg(rj + rec_plane(p.n));
+                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)

@@ -6,7 +6,9 @@ Claims: (1) the split of a double, hi = RN32(x) and lo = RZ32(x - hi), is a pair
 whose sum is a double and whose split is the pair again; (2) a normalised pair
 (the output of a two-sum) moved onto the grid by lo <- RN32(RN64(hi + lo) - hi)
 is such a fixed point, the move changes the value by at most 2^-53 of it, and
-pairs with lo within 28 binades of hi are not moved at all."""
+pairs with lo within 28 binades of hi are not moved at all; (3) the kernels'
+FP32-only form of that move (round lo to a multiple of the grid spacing q by
+adding and subtracting 2^23 q) gives the same bits."""
 import numpy as np
 
 f32, f64 = np.float32, np.float64
@@ -32,6 +34,21 @@ def on_grid(hi, lo):
     h = hi[m].astype(f64)
     lo[m] = ((h + lo[m].astype(f64)) - h).astype(f32)
     return hi, lo
+
+
+def on_grid_fp32(hi, lo):
+    """The kernels' form: q = 2^(e - 52) from hi's exponent field (one binade less
+    when hi is a power of two and lo points towards zero), lo + M - M with
+    M = +-2^23 q when |lo| < 2^23 q, all in FP32."""
+    hb = hi.view(np.uint32).astype(np.int64)
+    eq = ((hb >> 23) & 0xFF) - 127 - 52
+    eq = eq - (((hb & 0x7FFFFF) == 0) & (np.signbit(lo) != np.signbit(hi)) & (lo != 0))
+    ok = eq >= -149
+    t = np.where(ok, np.clip(eq + 23 + 127, 1, 254) << 23, 0).astype(np.uint32).view(f32)
+    m = np.where(np.signbit(lo), -t, t).astype(f32)
+    with np.errstate(over="ignore", invalid="ignore"):
+        moved = ((lo + m) - m).astype(f32)
+    return hi, np.where(ok & (np.abs(lo) < t), moved, lo).astype(f32)
 
 
 def two_sum(a, b):
@@ -100,6 +117,22 @@ def test_two_sum_outputs_moved_onto_the_grid():
     # the rule is idempotent
     h3, l3 = on_grid(h2, l2)
     assert np.array_equal(h3, h2) and np.array_equal(l3, l2)
+
+
+def test_fp32_form_gives_the_same_bits():
+    rng = np.random.default_rng(2)
+    m = 1_000_000
+    a = (rng.uniform(-1, 1, m) * np.exp2(rng.integers(-100, 60, m))).astype(f32)
+    k = m // 5   # powers of two of either sign, where the grid halves below hi
+    a[:k] = (np.exp2(rng.integers(-100, 60, k)) * rng.choice([-1.0, 1.0], k)).astype(f32)
+    b = (a.astype(f64) * rng.uniform(-1, 1, m) * np.exp2(-rng.integers(0, 70, m).astype(f64))).astype(f32)
+    b[k:k + 1000] = 0.0
+    hi, lo = two_sum(a, b)
+    h1, l1 = on_grid(hi, lo)
+    h2, l2 = on_grid_fp32(hi, lo)
+    assert np.array_equal(h1.view(np.uint32), h2.view(np.uint32))
+    assert np.array_equal(l1.view(np.uint32), l2.view(np.uint32))   # zeros' signs included
+    assert (l1 != lo).sum() > 1000                                   # the move did happen
 
 
 def test_off_grid_pairs_would_not_survive_the_round_trip():
