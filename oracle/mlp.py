@@ -9,7 +9,8 @@ layers, trained with an MSE loss and Adam.  Readings:
   * loss = mean over batch and outputs of (y - t)^2.
   * Adam with beta1 = 0.9, beta2 = 0.999, eps = 1e-8 and bias correction.
   * The BF16 variant rounds to nearest-even exactly where the CUDA path stores
-    BF16: the network input, the weights, and each hidden activation after GELU.
+    BF16: the network input, the weights, each hidden activation after GELU,
+    and, for the backward pass, each hidden pre-activation that GELU' reads.
     Biases, the output and all accumulation stay in high precision.
 
 Parameter layout (flat float32 vector, shared with the library's get/set):
@@ -85,6 +86,7 @@ def loss_and_grad(theta, X, T, dims=DIMS, bf16=True):
     """MSE loss and its gradient with respect to the (unrounded) parameters;
     rounding is treated as the identity in the backward pass."""
     Y, cache = forward(theta, X, dims, bf16, keep=True)
+    q = bf16_round if bf16 else (lambda a: a)
     B = X.shape[0]
     diff = Y - T
     loss = float((diff * diff).sum() / (B * dims[-1]))
@@ -93,7 +95,7 @@ def loss_and_grad(theta, X, T, dims=DIMS, bf16=True):
     for i in range(len(cache) - 1, -1, -1):
         h, Wq, z = cache[i]
         if i < len(cache) - 1:
-            g = g * gelu_grad(z)
+            g = g * gelu_grad(q(z))
         gW = g.T @ h
         gb = g.sum(0)
         grads.append((gW, gb))

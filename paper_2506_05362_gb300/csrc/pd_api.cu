@@ -40,7 +40,7 @@ struct pd_ctx {
     int32_t *perm = nullptr, *inv = nullptr, *grain = nullptr;
     dbl4 *x4 = nullptr, *u[2] = {nullptr, nullptr}, *v = nullptr, *acc = nullptr, *F = nullptr;
     float4 *xh4 = nullptr, *xl4 = nullptr;
-    float4 *rec[2] = {nullptr, nullptr};                 // mixed path: node records (REC_SLOTS float4 per node), current / next
+    float4 *rec[2] = {nullptr, nullptr};                 // mixed path: node record buffers (rec_float4s(n) float4), current / next
     float4 *uh[2] = {nullptr, nullptr}, *ul[2] = {nullptr, nullptr};  // views of the u slots (stride REC)
     float4 *vh = nullptr, *vl = nullptr, *af = nullptr;  // mixed path: v pairs, a
     float4 *snap_vh = nullptr, *snap_vl = nullptr, *snap_af = nullptr, *snap_rec = nullptr;
@@ -521,14 +521,14 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
         ALLOC(c->xh4, float4, n);
         ALLOC(c->xl4, float4, n);
         for (int q = 0; q < 2; ++q) {
-            ALLOC(c->rec[q], float4, (int64_t)REC_SLOTS * n);
-            c->uh[q] = c->rec[q] + rec_plane(n);
-            c->ul[q] = c->rec[q] + 2 * rec_plane(n);
+            ALLOC(c->rec[q], float4, rec_float4s(n));
+            c->uh[q] = c->rec[q] + rec_uh0(n);
+            c->ul[q] = c->rec[q] + rec_ul0(n);
         }
         ALLOC(c->vh, float4, n);
         ALLOC(c->vl, float4, n);
         ALLOC(c->af, float4, n);
-        ALLOC(c->snap_rec, float4, (int64_t)REC_SLOTS * n);
+        ALLOC(c->snap_rec, float4, rec_float4s(n));
         ALLOC(c->snap_vh, float4, n);
         ALLOC(c->snap_vl, float4, n);
         ALLOC(c->snap_af, float4, n);
@@ -539,7 +539,7 @@ static pd_status create_impl(pd_ctx *c, const double *x, const double *vol, cons
     CK(cudaGetLastError());
     for (int q = 0; q < 2; ++q) {
         CK(cudaMemsetAsync(c->u[q], 0, sizeof(dbl4) * n, c->st));
-        if (mixed) CK(cudaMemsetAsync(c->rec[q], 0, sizeof(float4) * REC_SLOTS * n, c->st));
+        if (mixed) CK(cudaMemsetAsync(c->rec[q], 0, sizeof(float4) * rec_float4s(n), c->st));
     }
     CK(cudaMemsetAsync(c->acc, 0, sizeof(dbl4) * n, c->st));
     CK(cudaMemsetAsync(c->F, 0, sizeof(dbl4) * n, c->st));
@@ -1057,7 +1057,7 @@ static pd_status snapshot(pd_ctx *c, bool restore)
         return cudaMemcpyAsync(restore ? (void *)src : dst, restore ? dst : src, bytes, cudaMemcpyDeviceToDevice, c->st);
     };
     if (mixed) {
-        CK(cp(c->snap_rec, c->rec[c->cur], (size_t)REC_SLOTS * nf));
+        CK(cp(c->snap_rec, c->rec[c->cur], sizeof(float4) * (size_t)rec_float4s(c->n)));
         CK(cp(c->snap_vh, c->vh, nf));
         CK(cp(c->snap_vl, c->vl, nf));
         CK(cp(c->snap_af, c->af, nf));

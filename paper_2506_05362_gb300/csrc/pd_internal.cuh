@@ -40,19 +40,29 @@ struct WallSet {
 
 // Everything the force/update kernels need, passed by value.
 // Mixed-path node records: three float4 slots per node, (x_hi, c V), (u_hi,
-// packed x_lo.xy) and (u_lo, packed x_lo.z).  PD_PLANES = 1 (the default) keeps
-// three planes of n float4 (slot s of node i at [s n + i]), so that the lanes of a
-// group gathering neighbours that are consecutive in the node order read one
-// contiguous run per slot; PD_PLANES = 0 interleaves them (one 48-byte record per
-// node, slot s of node i at [3 i + s]).  Both give the same bits; the planes were
-// 1-2% faster per force evaluation on the plate and the hollow sphere and equal on
-// the aggregate (GB300, CUDA events).
+// packed x_lo.xy) and (u_lo, packed x_lo.z), in one of three layouts (all give the
+// same bits):
+//   PD_PLANES = 0: interleaved, one 48-byte record per node (slot s of node i at
+//     [3 i + s]);
+//   PD_PLANES = 1 (default): three planes of n float4 (slot s of node i at
+//     [s n + i]), so that the lanes of a group gathering neighbours that are
+//     consecutive in the node order read one contiguous run per slot;
+//   PD_PLANES = 2: an x plane and a u plane holding each node's (u_hi, u_lo) as
+//     one 32-byte aligned pair, so that a neighbour's u is one 256-bit load (x at
+//     [i], u_hi at [u0 + 2 i], u_lo at [u0 + 2 i + 1], u0 = n rounded up to even).
 #ifndef PD_PLANES
 #define PD_PLANES 1
 #endif
-constexpr int REC = PD_PLANES ? 1 : 3;  // element stride of a record slot
-constexpr int REC_SLOTS = 3;            // float4 per node record
-__host__ __device__ inline int64_t rec_plane(int64_t n) { return PD_PLANES ? n : 1; }  // slot-to-slot offset
+constexpr int RECX = PD_PLANES ? 1 : 3;                              // element stride of the x slots
+constexpr int REC = PD_PLANES == 0 ? 3 : (PD_PLANES == 1 ? 1 : 2);  // element stride of the u slots
+// float4 offsets of node 0's u_hi and u_lo slots from the record base, and the
+// float4 count of one record buffer
+__host__ __device__ inline int64_t rec_uh0(int64_t n)
+{
+    return PD_PLANES == 0 ? 1 : (PD_PLANES == 1 ? n : (n + 1) & ~(int64_t)1);
+}
+__host__ __device__ inline int64_t rec_ul0(int64_t n) { return PD_PLANES == 1 ? 2 * n : rec_uh0(n) + 1; }
+__host__ __device__ inline int64_t rec_float4s(int64_t n) { return PD_PLANES == 2 ? rec_uh0(n) + 2 * n : 3 * n; }
 
 struct StepParams {
     int64_t n;
@@ -63,9 +73,9 @@ struct StepParams {
     // mixed-path node records (layout above): (x_hi, c V) with x relative to the
     // bounding-box centre (static; c V set at bond build), (u_hi, packed x_lo.xy),
     // (u_lo, packed x_lo.z).  Two buffers (current / next) for u.
-    const float4 *xh4;             // x slots of the current buffer (index REC*i)
+    const float4 *xh4;             // x slots of the current buffer (index RECX*i)
     const float4 *xl4;             // (x_lo, 0), dense
-    const float4 *uh_in, *ul_in;   // = xh4 + plane, xh4 + 2 plane (index REC*i)
+    const float4 *uh_in, *ul_in;   // = xh4 + rec_uh0(n), xh4 + rec_ul0(n) (index REC*i)
     float4 *uh_out, *ul_out;       // next buffer's u slots (index REC*i)
     float4 *vh, *vl;               // v (in place)
     float4 *af;                    // a = (F + b)/rho, stored for the next drift

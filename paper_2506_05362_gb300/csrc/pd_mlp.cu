@@ -41,9 +41,9 @@ struct GemmArgs {
     int ldb;
     int ksplit;           // rows of K per split (EPI_PARTIAL), else K
     const float *bias;
-    float *Zout;          // EPI_HIDDEN (nullable)
+    bf16 *Zout;           // EPI_HIDDEN (nullable): pre-activations, stored as BF16
     bf16 *Hout;           // EPI_HIDDEN / EPI_DGELU
-    const float *Zin;     // EPI_DGELU
+    const bf16 *Zin;      // EPI_DGELU
     float *out;           // EPI_OUT / EPI_PARTIAL
     int ldo;
     int n_valid;
@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const GemmArgs g)
                     if (col + 1 < g.N + 1 && col < g.N) {
                         const float z0 = v0 + g.bias[col], z1 = (col + 1 < g.N) ? v1 + g.bias[col + 1] : 0.f;
                         if (g.Zout) {
-                            g.Zout[(size_t)row * g.ldo + col] = z0;
-                            if (col + 1 < g.N) g.Zout[(size_t)row * g.ldo + col + 1] = z1;
+                            g.Zout[(size_t)row * g.ldo + col] = __float2bfloat16_rn(z0);
+                            if (col + 1 < g.N) g.Zout[(size_t)row * g.ldo + col + 1] = __float2bfloat16_rn(z1);
                         }
                         __nv_bfloat162 hv = __floats2bfloat162_rn(gelu(z0), gelu(z1));
                         if (col + 1 < g.N)
@@ -234,8 +234,9 @@ __global__ void __launch_bounds__(THREADS) k_gemm(const GemmArgs g)
                     if (col + 1 < g.n_valid) g.out[(size_t)row * g.ldo + col + 1] = v1 + g.bias[col + 1];
                 } else if (EPI == EPI_DGELU) {
                     if (col < g.N) {
-                        const float d0 = v0 * gelu_grad(g.Zin[(size_t)row * g.ldo + col]);
-                        const float d1 = (col + 1 < g.N) ? v1 * gelu_grad(g.Zin[(size_t)row * g.ldo + col + 1]) : 0.f;
+                        const float d0 = v0 * gelu_grad(__bfloat162float(g.Zin[(size_t)row * g.ldo + col]));
+                        const float d1 =
+                            (col + 1 < g.N) ? v1 * gelu_grad(__bfloat162float(g.Zin[(size_t)row * g.ldo + col + 1])) : 0.f;
                         __nv_bfloat162 hv = __floats2bfloat162_rn(d0, d1);
                         if (col + 1 < g.N)
                             *(__nv_bfloat162 *)(g.Hout + (size_t)row * g.ldo + col) = hv;
@@ -459,7 +460,7 @@ struct pd_mlp {
     // activations (capacity in rows)
     int64_t cap = 0;
     bf16 *H[9] = {nullptr};   // H[0] input (padded), H[l+1] after layer l (hidden)
-    float *Z[8] = {nullptr};  // pre-activations of hidden layers
+    bf16 *Z[8] = {nullptr};   // pre-activations of hidden layers (BF16: only GELU' reads them)
     bf16 *dZ[9] = {nullptr};  // gradient w.r.t. pre-activation of layer l (dZ[L-1] = dY)
     // tcgen05 training: HT[l] = layer l's input transposed [pad[l] x ldT], dZT[l] =
     // dZ[l] transposed [pad[l+1] x ldT]
@@ -478,9 +479,9 @@ struct pd_mlp {
 int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
                    int64_t rows, float *Y, unsigned *err, int device, cudaStream_t st);
 int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
-                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         const float *X, int64_t rows, float *Y, void *const *Z, void *const *HT, int64_t ldT,
                          unsigned *err, int device, cudaStream_t st);
-int mlp_dgelu_tc(const void *dZ, const void *WT, const float *z, int64_t rows, int N, int K, void *out, void *outT,
+int mlp_dgelu_tc(const void *dZ, const void *WT, const void *z, int64_t rows, int N, int K, void *out, void *outT,
                  int64_t ldT, unsigned *err, int device, cudaStream_t st);
 int mlp_dw_tc(const void *dZT, const void *HT, int64_t rows, int64_t ldT, int M, int N, float *part, int max_splits,
               unsigned *err, int device, cudaStream_t st);
@@ -636,7 +637,7 @@ int backward_tc(pd_mlp *m, const float *X, const float *T, int64_t rows, float *
         if (m->pad[l + 1] % 32 != 0) return -1;
     void *W[8], *HT[8];
     const float *b[8];
-    float *Z[8];
+    void *Z[8];
     for (int l = 0; l < L; ++l) { W[l] = m->Wb[l]; b[l] = m->bias[l]; HT[l] = m->HT[l]; Z[l] = m->Z[l]; }
     if (mlp_forward_train_tc(L, m->dims, m->pad, W, b, X, rows, m->Y, Z, HT, m->ldT, m->tc_err, m->device, m->st))
         return -1;

@@ -57,8 +57,9 @@ struct Params {
     int64_t rows;
     unsigned *err;    // error word (1 = a wait timed out)
     // training forward (nullable otherwise): Z[l] pre-activations of hidden layer l
-    // [rows x N_l] FP32; HT[l] layer l's input transposed [K_l x ldT] BF16
-    float *Z[MAX_LAYERS];
+    // [rows x N_l] BF16 (only GELU' reads them); HT[l] layer l's input transposed
+    // [K_l x ldT] BF16
+    __nv_bfloat16 *Z[MAX_LAYERS];
     __nv_bfloat16 *HT[MAX_LAYERS];
     int64_t ldT;
 };
@@ -504,9 +505,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                                 }
                                 *(uint4 *)(sA + sw128_offset(m, c0 + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                                 if (P.Z[l] && row < P.rows) {  // training: Z for GELU', H^T for dW
-                                    float *zr = P.Z[l] + row * Ly.N + c0 + c8;
-                                    *(float4 *)zr = make_float4(zs[0], zs[1], zs[2], zs[3]);
-                                    *(float4 *)(zr + 4) = make_float4(zs[4], zs[5], zs[6], zs[7]);
+                                    *(uint4 *)(P.Z[l] + row * Ly.N + c0 + c8) =
+                                        make_uint4(pack_bf16x2(zs[0], zs[1]), pack_bf16x2(zs[2], zs[3]),
+                                                   pack_bf16x2(zs[4], zs[5]), pack_bf16x2(zs[6], zs[7]));
                                     const __nv_bfloat16 *hb = (const __nv_bfloat16 *)pk;
 #pragma unroll
                                     for (int e = 0; e < 8; ++e)
@@ -590,7 +591,7 @@ struct GemmP {
     int M, N, kchunks, kcs;   // kcs: K chunks per split
     int mode;
     int64_t m_valid;          // rows of C that exist
-    const float *z;           // DGELU: pre-activation [M x N]
+    const __nv_bfloat16 *z;   // DGELU: pre-activation [M x N], BF16
     __nv_bfloat16 *out, *outT;
     int64_t ldT;
     float *part;              // PARTIAL
@@ -707,15 +708,19 @@ __global__ void __launch_bounds__(G_THREADS, 1) k_gemm_tc(const __grid_constant_
                     for (int e = 0; e < 32; e += 4)
                         if (c0 + e < P.N) *(float4 *)(dst + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
                 } else {
-                    const float *zr = P.z + row * P.N + c0;
+                    const __nv_bfloat16 *zr = P.z + row * P.N + c0;
 #pragma unroll
                     for (int e = 0; e < 32; e += 8) {
                         if (c0 + e >= P.N) break;
-                        const float4 z0 = *(const float4 *)(zr + e), z1 = *(const float4 *)(zr + e + 4);
-                        const float d0 = v[e] * gelu_grad(z0.x), d1 = v[e + 1] * gelu_grad(z0.y);
-                        const float d2 = v[e + 2] * gelu_grad(z0.z), d3 = v[e + 3] * gelu_grad(z0.w);
-                        const float d4 = v[e + 4] * gelu_grad(z1.x), d5 = v[e + 5] * gelu_grad(z1.y);
-                        const float d6 = v[e + 6] * gelu_grad(z1.z), d7 = v[e + 7] * gelu_grad(z1.w);
+                        const uint4 zw = *(const uint4 *)(zr + e);  // 8 BF16 pre-activations
+                        const float2 z01 = __bfloat1622float2(*(const __nv_bfloat162 *)&zw.x);
+                        const float2 z23 = __bfloat1622float2(*(const __nv_bfloat162 *)&zw.y);
+                        const float2 z45 = __bfloat1622float2(*(const __nv_bfloat162 *)&zw.z);
+                        const float2 z67 = __bfloat1622float2(*(const __nv_bfloat162 *)&zw.w);
+                        const float d0 = v[e] * gelu_grad(z01.x), d1 = v[e + 1] * gelu_grad(z01.y);
+                        const float d2 = v[e + 2] * gelu_grad(z23.x), d3 = v[e + 3] * gelu_grad(z23.y);
+                        const float d4 = v[e + 4] * gelu_grad(z45.x), d5 = v[e + 5] * gelu_grad(z45.y);
+                        const float d6 = v[e + 6] * gelu_grad(z67.x), d7 = v[e + 7] * gelu_grad(z67.y);
                         const uint4 pk = make_uint4(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3), pack_bf16x2(d4, d5),
                                                     pack_bf16x2(d6, d7));
                         *(uint4 *)(P.out + row * P.N + c0 + e) = pk;
@@ -770,7 +775,7 @@ int gemm_tc(const GemmP &P0, const void *A, int64_t a_rows, int64_t a_cols, int6
 
 // dZ_prev = (dZ * W) . GELU'(Z): A = dZ [rows x K] (ld K), B = W^T [N x K] (ld K),
 // z = Z [rows x N]; writes out [rows x N] and outT [N x ldT].  N <= 256.
-int mlp_dgelu_tc(const void *dZ, const void *WT, const float *z, int64_t rows, int N, int K, void *out, void *outT,
+int mlp_dgelu_tc(const void *dZ, const void *WT, const void *z, int64_t rows, int N, int K, void *out, void *outT,
                  int64_t ldT, unsigned *err, int device, cudaStream_t st)
 {
     GemmP P;
@@ -781,7 +786,7 @@ int mlp_dgelu_tc(const void *dZ, const void *WT, const float *z, int64_t rows, i
     P.kcs = P.kchunks;
     P.mode = GEMM_DGELU;
     P.m_valid = rows;
-    P.z = z;
+    P.z = (const __nv_bfloat16 *)z;
     P.out = (__nv_bfloat16 *)out;
     P.outT = (__nv_bfloat16 *)outT;
     P.ldT = ldT;
@@ -819,11 +824,11 @@ size_t mlp_tc_smem() { return 1024 + 2 * A_BYTES + STAGES * W_STAGE_BYTES + 256;
 // W[l]: padded BF16 weights [pad_out x pad_in] row-major; bias[l]: pad_out
 // floats.  Returns 0 on success, -1 if the shape is unsupported or the tensor
 // maps cannot be made (the caller then uses the mma.sync kernels).
-// Training forward: the same kernel also stores Z[l] (FP32 [rows x pad[l+1]],
+// Training forward: the same kernel also stores Z[l] (BF16 [rows x pad[l+1]],
 // hidden layers) and HT[l] (BF16 [pad[l] x ldT], every layer's input
 // transposed).  Hidden widths must be multiples of 32.
 int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
-                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         const float *X, int64_t rows, float *Y, void *const *Z, void *const *HT, int64_t ldT,
                          unsigned *err, int device, cudaStream_t st);
 
 int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias, const float *X,
@@ -833,7 +838,7 @@ int mlp_forward_tc(int L, const int *dims, const int *pad, void *const *W, const
 }
 
 int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W, const float *const *bias,
-                         const float *X, int64_t rows, float *Y, float *const *Z, void *const *HT, int64_t ldT,
+                         const float *X, int64_t rows, float *Y, void *const *Z, void *const *HT, int64_t ldT,
                          unsigned *err, int device, cudaStream_t st)
 {
     if (L < 1 || L > MAX_LAYERS || rows < 1) return -1;
@@ -874,7 +879,7 @@ int mlp_forward_train_tc(int L, const int *dims, const int *pad, void *const *W,
     P.err = err;
     if (Z) {
         for (int l = 0; l < L; ++l) {
-            P.Z[l] = (l + 1 < L) ? Z[l] : nullptr;
+            P.Z[l] = (l + 1 < L) ? (__nv_bfloat16 *)Z[l] : nullptr;
             P.HT[l] = (__nv_bfloat16 *)HT[l];
         }
         P.ldT = ldT;

@@ -292,6 +292,29 @@ __device__ __forceinline__ void xl_unpack(float w1, float w2, float *xl)
     xl[2] = __uint_as_float(b << 16);
 }
 
+// The three record slots of neighbour j (mixed path), in the layout PD_PLANES
+// selects: (x_hi, c V), (u_hi, x_lo.xy packed), (u_lo, x_lo.z packed).
+__device__ __forceinline__ void gather_record(const StepParams &p, int32_t j, float4 &a0, float4 &a1, float4 &a2)
+{
+#if PD_PLANES == 2
+    a0 = __ldg(p.xh4 + j);
+    // the node's u pair is 32-byte aligned (u0 even): one 256-bit read-only load
+    const float4 *q = p.uh_in + 2 * (int64_t)j;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a1.x), "=f"(a1.y), "=f"(a1.z), "=f"(a1.w), "=f"(a2.x), "=f"(a2.y), "=f"(a2.z), "=f"(a2.w)
+        : "l"(q));
+#elif PD_PLANES == 1
+    a0 = __ldg(p.xh4 + j);
+    a1 = __ldg(p.uh_in + j);
+    a2 = __ldg(p.ul_in + j);
+#else
+    const float4 *r = p.xh4 + 3 * (int64_t)j;  // one 48-byte record
+    a0 = __ldg(r);
+    a1 = __ldg(r + 1);
+    a2 = __ldg(r + 2);
+#endif
+}
+
 // One bond of the mixed path (Eq. pmb with the bond memory of Eq. peri-damage):
 // records o* of the row's node and a* of the neighbour.
 template <bool FLAG = false>
@@ -449,7 +472,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_GLOBAL) k_pairs_upper(co
         const int64_t row = r0 + grp;
         float fbx = 0.f, fby = 0.f, fbz = 0.f;
         if (row < p.n) {
-            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row),
+            const float4 o0 = __ldg(p.xh4 + RECX * row), o1 = __ldg(p.uh_in + REC * row),
                          o2 = __ldg(p.ul_in + REC * row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
@@ -467,10 +490,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_GLOBAL) k_pairs_upper(co
                 float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
-                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
-                    a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + rec_plane(p.n));
-                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
+                    gather_record(p, raw[q] & 0x7fffffff, a0[q], a1[q], a2[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)
@@ -803,7 +823,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
         if (PAIRS) {
             // pass 2: the slots whose bond pass 1 evaluated from the other end
             // (neighbour index below the row's); their factors are in tb
-            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row),
+            const float4 o0 = __ldg(p.xh4 + RECX * row), o1 = __ldg(p.uh_in + REC * row),
                          o2 = __ldg(p.ul_in + REC * row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
@@ -821,10 +841,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
-                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);
-                    a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + rec_plane(p.n));
-                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
+                    gather_record(p, raw[q] & 0x7fffffff, a0[q], a1[q], a2[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
@@ -838,7 +855,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 }
             }
         } else if (MIXED) {
-            const float4 o0 = __ldg(p.xh4 + REC * row), o1 = __ldg(p.uh_in + REC * row), o2 = __ldg(p.ul_in + REC * row);
+            const float4 o0 = __ldg(p.xh4 + RECX * row), o1 = __ldg(p.uh_in + REC * row), o2 = __ldg(p.ul_in + REC * row);
             float ol[3];
             xl_unpack(o1.w, o2.w, ol);
             const int i0 = (int)k0, i1 = (int)k1;
@@ -862,10 +879,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 float4 a0[PD_INFLIGHT_PF], a1[PD_INFLIGHT_PF], a2[PD_INFLIGHT_PF];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT_PF; ++q) {
-                    const float4 *rj = p.xh4 + REC * (raw[q] & 0x7fffffff);  // one node record
-                    a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + rec_plane(p.n));
-                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
+                    gather_record(p, raw[q] & 0x7fffffff, a0[q], a1[q], a2[q]);
                 }
                 int32_t nxt[PD_INFLIGHT_PF];
 #pragma unroll
@@ -894,11 +908,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
                 float4 a0[PD_INFLIGHT], a1[PD_INFLIGHT], a2[PD_INFLIGHT];
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q) {
-                    const int j = raw[q] & 0x7fffffff;
-                    const float4 *rj = p.xh4 + REC * j;  // one node record
-                    a0[q] = __ldg(rj);
-                    a1[q] = __ldg(rj + rec_plane(p.n));
-                    a2[q] = __ldg(rj + 2 * rec_plane(p.n));
+                    gather_record(p, raw[q] & 0x7fffffff, a0[q], a1[q], a2[q]);
                 }
 #pragma unroll
                 for (int q = 0; q < PD_INFLIGHT; ++q)
@@ -955,7 +965,7 @@ __device__ __forceinline__ void process_row(const StepParams &p, const double *w
     if (MIXED) {
         float4 oxh = make_float4(0.f, 0.f, 0.f, 0.f), ouh = oxh, oul = oxh, ovh = oxh, ovl = oxh;
         if (active && gl < 3) {
-            oxh = __ldg(p.xh4 + REC * row); ouh = __ldg(p.uh_in + REC * row); oul = __ldg(p.ul_in + REC * row);
+            oxh = __ldg(p.xh4 + RECX * row); ouh = __ldg(p.uh_in + REC * row); oul = __ldg(p.ul_in + REC * row);
             ovh = p.vh[row]; ovl = p.vl[row];
         }
         err |= epilogue_lanes<G, WX>(p, wp, row, active, gl, fbx, fby, fbz, oxh, ouh, oul, ovh, ovl, react, vmax2f);
@@ -1346,7 +1356,7 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
             }
             for (int q = threadIdx.x; q < len; q += STEP_THREADS) {
                 const int j = __ldg(p.ulist + base + q);
-                r0s[q] = __ldg(p.xh4 + REC * j);
+                r0s[q] = __ldg(p.xh4 + RECX * j);
                 r1s[q] = __ldg(p.uh_in + REC * j);
                 r2s[q] = __ldg(p.ul_in + REC * j);
             }
@@ -1490,7 +1500,7 @@ __global__ void k_fill_record_x(const float4 *__restrict__ xh4, int64_t n, float
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         float4 r = xh4[i];
         r.w = cf * r.w;
-        rec[REC * i] = r;
+        rec[RECX * i] = r;
     }
 }
 

@@ -23,8 +23,10 @@ GRAD_TOL = 3e-2   # gradients also round dZ to BF16 at each layer
 # per row of 1024 hidden activations, each moving an output by ~1e-3 of its
 # column's RMS; the GELU's erf approximation (absolute error <= 1.5e-7) adds as
 # many.  A CPU emulation (FP32 accumulation, BF16 storage) gives at most 1.0e-2
-# of the column RMS; the bound takes 5x that.  Gradients round dZ to BF16 as
-# well: the emulation gives at most 2.8e-2 of the layer's RMS gradient.
+# of the column RMS; the bound takes 5x that.  Gradients round dZ and the
+# pre-activations that GELU' reads to BF16 as well (the oracle rounds the latter
+# where the kernels store them): the emulation gives at most 2.8e-2 of the
+# layer's RMS gradient.
 FWD_ATOL, FWD_RTOL = 5e-2, 1e-2      # scale: RMS of the output column
 GRAD_ATOL, GRAD_RTOL = 1e-1, 2e-2    # scale: RMS of the layer's W (or b) gradient
 
