@@ -262,11 +262,8 @@ __device__ __forceinline__ uint32_t sw128_offset(int m, int k)
 
 // bias + GELU + BF16 of the 16 accumulator columns [c, c + 16) of row m, written
 // to the next layer's swizzled A tile: the arithmetic of the whole-chunk path,
-// element for element (c is a multiple of 16, so the bias loads are aligned).  In
-// training (zrow set) the BF16 pre-activations go to row m of Z and the BF16
-// activations to column `row` of the transposed input of the next layer.
-__device__ __forceinline__ void epi16(const float *bias, const uint32_t (&r)[16], int c, unsigned char *sA, int m,
-                                      __nv_bfloat16 *zrow, __nv_bfloat16 *ht, int64_t ldT, int64_t row)
+// element for element (c is a multiple of 16, so the bias loads are aligned)
+__device__ __forceinline__ void epi16(const float *bias, const uint32_t (&r)[16], int c, unsigned char *sA, int m)
 {
     float bb[16];
 #pragma unroll
@@ -276,22 +273,15 @@ __device__ __forceinline__ void epi16(const float *bias, const uint32_t (&r)[16]
     }
 #pragma unroll
     for (int c8 = 0; c8 < 16; c8 += 8) {
-        uint32_t pk[4], zp[4];
+        uint32_t pk[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             const float2 zz = __fadd2_rn(make_float2(__uint_as_float(r[c8 + e]), __uint_as_float(r[c8 + e + 1])),
                                          make_float2(bb[c8 + e], bb[c8 + e + 1]));
             const float2 g2 = gelu2(zz);
             pk[e / 2] = pack_bf16x2(g2.x, g2.y);
-            zp[e / 2] = zrow ? pack_bf16x2(zz.x, zz.y) : 0u;
         }
         *(uint4 *)(sA + sw128_offset(m, c + c8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        if (zrow) {  // training: the BF16 pre-activations for GELU', the activations transposed for dW
-            *(uint4 *)(zrow + c + c8) = make_uint4(zp[0], zp[1], zp[2], zp[3]);
-            const __nv_bfloat16 *hb = (const __nv_bfloat16 *)pk;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) ht[(int64_t)(c + c8 + e) * ldT + row] = hb[e];
-        }
     }
 }
 
@@ -465,11 +455,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                     const int hw = ((Ly.N / 4 + 31) / 32) * 32;  // columns per part, whole 32-column loads
                     const int cend = min(Ly.N, (part + 1) * hw);
                     const uint32_t tacc = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * MAX_N);
-                    // hidden layers on whole 32-column chunks: the TMEM load of the next
+                    // inference on whole 32-column chunks: the TMEM load of the next
                     // 16 columns is in flight while the current 16 go through GELU
-                    const bool piped = !last && (Ly.N % 32) == 0;
-                    __nv_bfloat16 *zrow = (P.Z[l] && row < P.rows) ? P.Z[l] + row * Ly.N : nullptr;
-                    __nv_bfloat16 *ht = P.Z[l] ? P.HT[l + 1] : nullptr;
+                    const bool piped = !last && (Ly.N % 32) == 0 && !P.Z[l];
                     if (piped && part * hw < cend) {
                         uint32_t ra[16], rb[16];
                         __syncwarp();  // tcgen05.ld is warp-collective
@@ -478,14 +466,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_mlp_fwd_tc(const __grid_constant
                         for (int c0 = part * hw; c0 < cend; c0 += 32) {  // bounds uniform in the warp
                             __syncwarp();
                             tmem_ld16_issue(tacc + (uint32_t)(c0 + 16), rb);
-                            epi16(Ly.bias, ra, c0, sA, m, zrow, ht, P.ldT, row);
+                            epi16(Ly.bias, ra, c0, sA, m);
                             tmem_wait16(rb);
                             const bool more = c0 + 32 < cend;
                             if (more) {
                                 __syncwarp();
                                 tmem_ld16_issue(tacc + (uint32_t)(c0 + 32), ra);
                             }
-                            epi16(Ly.bias, rb, c0 + 16, sA, m, zrow, ht, P.ldT, row);
+                            epi16(Ly.bias, rb, c0 + 16, sA, m);
                             if (more) tmem_wait16(ra);
                         }
                     }
