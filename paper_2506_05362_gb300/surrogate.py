@@ -259,6 +259,53 @@ def rve_aggregate(n_grains: int = 50, seed: int = 0, paths=None, rate: float = 2
     return runs
 
 
+def history_spread(a, b):
+    """The surrogate's error measure between two stress histories [records x 6]:
+    RMS over the windows' last records of |sigma_b - sigma_a|, over the largest
+    |sigma_a| of the run."""
+    err = np.linalg.norm(b[WINDOW - 1:] - a[WINDOW - 1:], axis=1)
+    return float(np.sqrt((err ** 2).mean()) / (np.linalg.norm(a, axis=1).max() + 1e-30))
+
+
+def twin_spread(n_grains: int = 50, seed: int = 0, paths=None, eps=(0.0, 1e-9, 1e-6), rate: float = 2.0e3,
+                strain_end: float = 0.04, records: int = 64, h: float = 0.5e-3 / 12, zeta: float = 0.5,
+                p_confine: float = 2.0e6, sf_max: float = 0.62, max_precompress: int = 80000, device: int = 0,
+                stream=None, lanes: int = 8):
+    """How far the stress history of one packing moves under a change no input can
+    see: the aggregate is pre-compressed once as in ``rve_aggregate``, and every
+    path is loaded from the saved state as it is and from the same state with
+    every node displaced by eps * h in a random direction (eps = 0 repeats the run
+    and must give the same bits).  Returns one record per (path, eps) with the
+    spread of the two histories in the surrogate's error measure."""
+    paths = list(LOADING_PATHS) if paths is None else list(paths)
+    sc, walls, ctx = _rve_setup(n_grains, seed, h, None, zeta, rate, device, stream, lanes)
+    dt = 0.8 * ctx.stable_dt()
+    _precompress(ctx, sc, dt, p_confine, sf_max, max_precompress)
+    u, v, broken, t = ctx.get_state()
+    wall_pts = ctx.get_walls()
+    rng = np.random.default_rng(seed + 99991)
+    d = rng.normal(size=u.shape)
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+
+    def run_from(u0):
+        w = walls.copy()
+        w[:, 3:6] = wall_pts
+        w[:, 6:9] = 0.0
+        ctx.set_walls(w)
+        ctx.set_state(u=u0, v=v, broken=broken, t=t)
+        return _load(ctx, sc, walls, path, dt, rate, strain_end, records, n_grains)[1]
+
+    out = []
+    for path in paths:
+        ref = run_from(u)
+        for e in eps:
+            twin = run_from(u + e * h * d)
+            out.append({"path": path, "eps": e, "spread": history_spread(ref, twin),
+                        "identical": bool(np.array_equal(ref, twin))})
+    ctx.close()
+    return out
+
+
 def windows(run: Run):
     """(X (m, 109), Y (m, 6)) samples of one run."""
     T = run.strain.shape[0]
@@ -476,10 +523,31 @@ if __name__ == "__main__":
     ap.add_argument("--val", type=int, default=2)
     ap.add_argument("--train-sizes", type=int, nargs="+", default=None,
                     help="with --aggregates: train on the first n aggregates for each n, one fixed held-out set")
+    ap.add_argument("--twins", type=int, default=0,
+                    help="measure the history spread under an invisible perturbation on this many aggregates")
+    ap.add_argument("--twin-eps", type=float, nargs="+", default=[0.0, 1e-9, 1e-6],
+                    help="node displacements of the twin runs, in units of h")
     ap.add_argument("--generate-only", action="store_true",
                     help="with --aggregates and --runs-file: extend the runs file and stop")
     a = ap.parse_args()
     import os
+    if a.twins > 0:
+        h = a.h if a.h is not None else 0.5e-3 / 12
+        recs = []
+        for ag in range(a.twins):
+            for r in twin_spread(a.grains[ag % len(a.grains)], seed=a.seed + ag, eps=tuple(a.twin_eps),
+                                 records=a.records, h=h, zeta=a.zeta, p_confine=a.p_confine):
+                recs.append(dict(r, aggregate=ag, grains=a.grains[ag % len(a.grains)]))
+                print(json.dumps(recs[-1]), flush=True)
+        summary = {str(e): {"median": float(np.median([r["spread"] for r in recs if r["eps"] == e])),
+                            "max": float(np.max([r["spread"] for r in recs if r["eps"] == e])),
+                            "identical": int(sum(r["identical"] for r in recs if r["eps"] == e))}
+                   for e in a.twin_eps}
+        if a.out:
+            with open(a.out, "w") as f:
+                json.dump({"runs": recs, "summary": summary}, f, indent=1)
+        print(json.dumps(summary))
+        raise SystemExit(0)
     if a.aggregates > 0:
         h = a.h if a.h is not None else 0.5e-3 / 12
         P = len(LOADING_PATHS)

@@ -44,6 +44,17 @@ def test_paths_branch_from_one_shared_precompression():
     assert np.all(np.isfinite(b.stress)) and b.stress[:, :3].mean() < 0
 
 
+def test_twin_runs_repeat_exactly_and_diverge_when_perturbed():
+    """The spread measurement behind the surrogate's error floor: a path loaded
+    twice from one saved packing gives the same bits; displaced by 1e-6 h it
+    gives a different history."""
+    from paper_2506_05362_gb300 import surrogate as SG
+    recs = SG.twin_spread(8, seed=5, paths=["uniaxial_z"], eps=(0.0, 1e-6), records=24, h=0.5e-3 / 6,
+                          max_precompress=40000)
+    assert recs[0]["identical"] and recs[0]["spread"] == 0.0
+    assert not recs[1]["identical"] and recs[1]["spread"] > 0.0
+
+
 def test_surrogate_trains_and_is_judged_by_pd():
     from paper_2506_05362_gb300 import surrogate as SG
     runs = []
