@@ -69,9 +69,19 @@ def test_surrogate_trains_and_is_judged_by_pd():
     for r in train[:2]:
         err, _ = SG.judge(net, xs, ys, r)
         assert err < 0.1
+    errs, bases = [], []
     for r in held:
         err, t_net = SG.judge(net, xs, ys, r)
+        base = SG.baseline_error(train, r)
+        print(f"held-out {r.path}: error {err:.4f}, mean-history baseline {base:.4f}")
         assert np.isfinite(err) and err > 0
+        errs.append(err)
+        bases.append(base)
         # the gain: the whole run's stress history in a small fraction of its PD time
         assert r.pd_seconds / t_net > 100
+    # what the network knows beyond the method without it: on average over the
+    # held-out runs, stress histories closer than the mean history of the training
+    # runs (with 3 training runs per path one held-out run may not be; at the study's
+    # scale 23 of 24 are)
+    assert np.mean(errs) < np.mean(bases)
     net.close()
