@@ -218,7 +218,12 @@ pd_status pd_stable_dt(pd_ctx *ctx, double *dt_crit);
  * whose contact list went stale or overflowed is rolled back to its own start
  * and rerun with a shorter rebuild period or larger lists.  The contact list is
  * rebuilt often enough for the fastest node (or wall) to gain 50% in speed
- * (150% while speeds are growing).  With friction (mu > 0) the call first
+ * (150% while speeds are growing).  A call of one step rebuilds it only when the
+ * list on the device no longer holds for the current state (not built since the
+ * bonds were, or the displacement bound since the last rebuild past half the
+ * skin; a state applied by pd_set_state* is evaluated on a list rebuilt from it);
+ * the forces do not depend on which rebuild made the list, so the trajectory is
+ * the same either way.  With friction (mu > 0) the call first
  * records dt as the friction's time step and, if it changed, evaluates the
  * acceleration at the current state again with it; nsteps = 0 does only that.
  * Errors: PD_ESTATE (no bonds yet, or a latched device error), PD_EINVAL

@@ -18,6 +18,7 @@
 
 struct GraphEntry {
     int steps, k, parity;
+    bool skip0;  // no contact-list rebuild before the first step
     double dt;
     cudaGraphExec_t exec;
     int64_t launches;
@@ -108,6 +109,11 @@ struct pd_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double impulse_span = 0;       // time covered by the wall impulses since their reset
     int64_t n_rollbacks = 0, n_rebuilds = 0, n_steps = 0;  // since creation (successful segments' rebuilds)
+    // the contact list on the device holds for the current state: built from it or
+    // carried through steps whose displacement bound stayed inside the skin (the
+    // device's stale flag clear); a one-step pd_step then needs no rebuild
+    bool list_ok = false;
+    int h_stale = 0;
     int k_cap = 1 << 30;  // rebuild period a stale list forced down; relaxed by 2x per clean segment
     double last_vm = 0;   // fastest speed at the previous segment's start
     double last_ms = 0, last_force_ms = 0;
@@ -368,6 +374,7 @@ pd_status grow_candidates(pd_ctx *c)
         ALLOC(c->cand_fd, dbl4, cap);
     }
     c->cand_cap = cap;
+    c->list_ok = false;
     clear_graphs(c);
     return PD_OK;
 }
@@ -416,6 +423,7 @@ pd_status eval_forces(pd_ctx *c)
         }
         e &= ~(unsigned)PDE_SKIN;
         c->latched |= e & (PDE_NONFINITE | PDE_WALL);
+        c->list_ok = c->opt.contact != 0;  // rebuilt from this state just now
         return status_of(c, e);
     }
     return fail(c, PD_ECAPACITY, "contact candidate list could not be grown");
@@ -865,6 +873,7 @@ pd_status pd_build_bonds(pd_ctx *c, double horizon, int nfilt, const pd_bond_fil
     if (s) return s;
     release(c, k1); release(c, k2); release(c, v1); release(c, v2); release(c, btmp); release(c, cnt);
     c->bonds_ready = true;
+    c->list_ok = false;
     // several steps per launch: on request, or by default for problems small enough
     // that one step's launch is mostly fixed cost
     c->persist = c->opt.persistent == 1 || (c->opt.persistent == 0 && n <= PD_PERSIST_AUTO_NODES);
@@ -971,7 +980,7 @@ static int persist_grid(const pd_ctx *c)
     return b;
 }
 
-static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
+static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt, bool skip0 = false)
 {
     int64_t launches = 0;
     StepParams p = params(c, MODE_FULL, parity, dt);
@@ -980,7 +989,7 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
     int in = parity ^ 1;
     const int pgrid = use_persist(c) ? persist_grid(c) : 0;
     for (int s = 0; s < steps;) {
-        if (c->opt.contact && s % k == 0) {
+        if (c->opt.contact && s % k == 0 && !(skip0 && s == 0)) {
             enqueue_rebuild(c, in);
             launches += 12;
         }
@@ -1027,18 +1036,21 @@ static int64_t enqueue_chunk(pd_ctx *c, int steps, int k, int parity, double dt)
     return launches;
 }
 
-static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, GraphEntry **out)
+static pd_status get_graph(pd_ctx *c, int steps, int k, int parity, double dt, bool skip0, GraphEntry **out)
 {
     for (auto &g : c->graphs)
-        if (g.steps == steps && g.k == k && g.parity == parity && g.dt == dt) { *out = &g; return PD_OK; }
+        if (g.steps == steps && g.k == k && g.parity == parity && g.skip0 == skip0 && g.dt == dt) {
+            *out = &g;
+            return PD_OK;
+        }
     if (c->graphs.size() >= 6) clear_graphs(c);
     cudaGraph_t graph;
     CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-    int64_t launches = enqueue_chunk(c, steps, k, parity, dt);
+    int64_t launches = enqueue_chunk(c, steps, k, parity, dt, skip0);
     cudaError_t e = cudaStreamEndCapture(c->st, &graph);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(c, PD_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e)); }
     GraphEntry ge;
-    ge.steps = steps; ge.k = k; ge.parity = parity; ge.dt = dt; ge.launches = launches;
+    ge.steps = steps; ge.k = k; ge.parity = parity; ge.skip0 = skip0; ge.dt = dt; ge.launches = launches;
     e = cudaGraphInstantiate(&ge.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(c, PD_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e)); }
@@ -1110,16 +1122,17 @@ static int chunk_for(const pd_ctx *c, int k)
     return k < gc ? (gc / k) * k : gc;
 }
 
-static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t *launches)
+static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t *launches, bool skip0)
 {
     int64_t left = nsteps;
     *launches = 0;
     const int chunk = chunk_for(c, k);
     while (left > 0) {
         int steps = (int)std::min<int64_t>(left, chunk);
+        const bool sk = skip0 && left == nsteps;  // the first chunk only
         if (use_persist(c)) {  // cooperative launches, enqueued directly (not captured)
             c->launch_err = cudaSuccess;
-            *launches += enqueue_chunk(c, steps, std::min(k, steps), c->cur, dt);
+            *launches += enqueue_chunk(c, steps, std::min(k, steps), c->cur, dt, sk);
             if (c->launch_err != cudaSuccess) {
                 cudaGetLastError();
                 return fail(c, PD_ECUDA, std::string("multi-step launch: ") + cudaGetErrorString(c->launch_err));
@@ -1139,14 +1152,14 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
                     c->prof_ev.push_back(e);
                 }
             }
-            *launches += enqueue_chunk(c, steps, kk, c->cur, dt);
+            *launches += enqueue_chunk(c, steps, kk, c->cur, dt, sk);
             CK(cudaGetLastError());
             c->cur ^= (steps & 1);
             left -= steps;
             continue;
         }
         GraphEntry *g;
-        pd_status s = get_graph(c, steps, std::min(k, steps), c->cur, dt, &g);
+        pd_status s = get_graph(c, steps, std::min(k, steps), c->cur, dt, sk, &g);
         if (s) return s;
         CK(cudaGraphLaunch(g->exec, c->st));
         *launches += g->launches;
@@ -1163,10 +1176,14 @@ static pd_status run_steps(pd_ctx *c, double dt, int64_t nsteps, int k, int64_t 
 static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out, int64_t *launches, double *ms_out,
                              double *force_ms_out)
 {
-    // a one-step segment rebuilds at its start whatever the period: no speed readback
+    // a one-step segment rebuilds at its start whatever the period (no speed
+    // readback), unless the list on the device still holds for the current state:
+    // then it steps without a rebuild, and the device's stale check decides (a
+    // carried list that goes stale sends the step back to be rerun with a rebuild)
     int k = 1;
     pd_status s = left == 1 ? PD_OK : rebuild_period(c, dt, &k);
     if (s) return s;
+    bool carry = left == 1 && c->list_ok && c->opt.contact;
     // a rollback costs at most one segment of work
     int64_t m = std::min<int64_t>(left, (int64_t)PD_SEGMENT_CHUNKS * chunk_for(c, k));
     *m_out = m;
@@ -1176,9 +1193,10 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out,
     for (int attempt = 0; attempt < 8; ++attempt) {
         c->prof_used = 0;
         CK(cudaEventRecord(c->ev0, c->st));
-        s = run_steps(c, dt, m, k, launches);
+        s = run_steps(c, dt, m, k, launches, carry);
         if (s) return s;
         CK(cudaEventRecord(c->ev1, c->st));
+        if (c->opt.contact) CK(cudaMemcpyAsync(&c->h_stale, c->stale, sizeof(int), cudaMemcpyDeviceToHost, c->st));
         unsigned e = 0;
         s = read_err(c, &e);
         if (s) return s;
@@ -1195,16 +1213,20 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out,
             *force_ms_out = fm;
             if (attempt == 0 && c->k_cap < (1 << 29)) c->k_cap *= 2;  // a clean segment relaxes the cap
             c->n_steps += m;
-            if (c->opt.contact)  // each chunk rebuilds at its steps 0, k, 2k, ...
+            if (c->opt.contact) {  // each chunk rebuilds at its steps 0, k, 2k, ...
                 for (int64_t rest = m; rest > 0; rest -= chunk_for(c, k)) {
                     const int64_t len = std::min<int64_t>(rest, chunk_for(c, k)), kk = std::min<int64_t>(k, len);
                     c->n_rebuilds += (len + kk - 1) / kk;
                 }
+                if (carry) --c->n_rebuilds;  // ... but the first, with the list carried
+            }
+            c->list_ok = c->opt.contact && c->h_stale == 0;
             c->t += dt * (double)m;
             c->impulse_span += dt * (double)m;
             return PD_OK;
         }
         c->cur = cur0;
+        c->list_ok = false;
         ++c->n_rollbacks;
         s = snapshot(c, true);
         if (s) return s;
@@ -1220,10 +1242,15 @@ static pd_status run_segment(pd_ctx *c, double dt, int64_t left, int64_t *m_out,
             if (s) return s;
         }
         if (e & PDE_SKIN) {
+            if (carry) {  // the carried list went stale: the same step again, from a fresh list
+                carry = false;
+                continue;
+            }
             if (k == 1) return fail(c, PD_ETIMEOUT, "contact list stale even when rebuilt every step");
             k = std::max(1, k / 2);
             c->k_cap = k;  // later segments start from the period that is being tried now
         }
+        carry = false;
     }
     return fail(c, PD_ECAPACITY, "pd_step retried too often");
 }
@@ -1474,6 +1501,7 @@ pd_status pd_contacts(pd_ctx *c, int64_t *npairs, int32_t *ij)
             if (s) return s;
             continue;
         }
+        c->list_ok = c->opt.contact != 0;  // rebuilt from the current state
         break;
     }
     int64_t *cnt = (int64_t *)pd_dev_alloc(c, sizeof(int64_t) * (n + 1));
@@ -1631,9 +1659,7 @@ static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, con
     if (t) c->t = *t;
     c->latched = 0;
     CK(cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st));
-    CK(reset_impulse(c));
-    pd_status s = sync(c);
-    if (s) return s;
+    CK(reset_impulse(c));  // stream-ordered before any later work; the evaluation below synchronises
     const bool velocity_forces = c->mat.beta_d > 0 || c->mat.mu > 0;
     const bool skip = !changed && !velocity_forces;
     ++(skip ? c->n_state_unchanged : c->n_state_applied);

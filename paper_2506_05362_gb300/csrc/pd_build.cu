@@ -380,17 +380,20 @@ __global__ void k_bits_to_bytes(const uint32_t *__restrict__ brk, const int32_t 
         out[kc_of[k]] = (uint8_t)((brk[k >> 5] >> (k & 31)) & 1u);
 }
 
+// The internal bitset from one byte per canonical slot.  A warp builds one word
+// at a time: lane l takes internal slot 32 w + l (coalesced reads of the slot
+// map), and the word is the ballot of the lanes' bits.
 __global__ void k_bytes_to_bits(const uint8_t *__restrict__ in, const int32_t *__restrict__ kc_of, int64_t B,
                                 uint32_t *brk)
 {
     const int64_t nw = (B + 31) >> 5;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t word = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t k = (w << 5) + b;
-            if (k < B && in[kc_of[k]]) word |= 1u << b;
-        }
-        brk[w] = word;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+        const int64_t k = (w << 5) + lane;
+        const bool bit = k < B && in[kc_of[k]] != 0;
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) brk[w] = word;
     }
 }
 
@@ -415,21 +418,22 @@ __global__ void k_bits_to_packed(const uint32_t *__restrict__ brk, const int32_t
     }
 }
 
-// the internal bitset from canonical packed bits
+// the internal bitset from canonical packed bits, a word per warp as above
 __global__ void k_packed_to_bits(const uint32_t *__restrict__ in, const int32_t *__restrict__ kc_of, int64_t B,
                                  uint32_t *brk)
 {
     const int64_t nw = (B + 31) >> 5;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t word = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t k = (w << 5) + b;
-            if (k < B) {
-                const int32_t c = kc_of[k];
-                if ((in[c >> 5] >> (c & 31)) & 1u) word |= 1u << b;
-            }
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw; w += nwarps) {
+        const int64_t k = (w << 5) + lane;
+        bool bit = false;
+        if (k < B) {
+            const int32_t c = kc_of[k];
+            bit = (in[c >> 5] >> (c & 31)) & 1u;
         }
-        brk[w] = word;
+        const uint32_t word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) brk[w] = word;
     }
 }
 
@@ -782,7 +786,7 @@ void bits_to_bytes(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint8_t
 
 void bytes_to_bits(const uint8_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st)
 {
-    k_bytes_to_bits<<<grid_of((B + 31) / 32), 256, 0, st>>>(in, kc_of, B, brk);
+    k_bytes_to_bits<<<grid_of(B), 256, 0, st>>>(in, kc_of, B, brk);  // a warp per word
 }
 
 void bits_to_packed(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint32_t *out, cudaStream_t st)
@@ -794,7 +798,7 @@ void bits_to_packed(const uint32_t *brk, const int32_t *kc_of, int64_t B, uint32
 
 void packed_to_bits(const uint32_t *in, const int32_t *kc_of, int64_t B, uint32_t *brk, cudaStream_t st)
 {
-    k_packed_to_bits<<<grid_of((B + 31) / 32), 256, 0, st>>>(in, kc_of, B, brk);
+    k_packed_to_bits<<<grid_of(B), 256, 0, st>>>(in, kc_of, B, brk);  // a warp per word
 }
 
 void to_caller(const dbl4 *in, const int32_t *perm, int64_t n, double *out, cudaStream_t st)

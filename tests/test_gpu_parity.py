@@ -369,6 +369,42 @@ def test_contact_forces_do_not_depend_on_the_list_history(pd, precision, kernel)
 
 
 # --------------------------------------------------------------------------- invariants
+@pytest.mark.parametrize("kernel", ["global", "pairs"])
+def test_one_step_calls_carry_the_contact_list(pd, kernel):
+    """Calls of one step reuse the contact list while the device's displacement
+    bound says it holds: two grains colliding in 1-step calls rebuild far less
+    often than once per step, and follow bit for bit a run that rebuilds every
+    step; a state sent back unchanged between the calls changes nothing."""
+    sc = S.aggregate(n_grains=2, h=0.5e-3 / 4, gap_cells=0.5, seed=4)
+    c = sc.x[sc.grain == 0].mean(0) - sc.x[sc.grain == 1].mean(0)
+    c /= np.linalg.norm(c)
+    sc.v0 = np.where((sc.grain == 0)[:, None], -5.0 * c, 5.0 * c)
+    sc.walls = []
+    a = pd.Context.from_scenario(sc, lanes=8, persistent=-1, **KERNEL[kernel])
+    b = pd.Context.from_scenario(sc, lanes=8, contact_every=1, persistent=-1, **KERNEL[kernel])
+    dt = 0.5 * a.stable_dt()
+    touched = 0
+    for it in range(4000):
+        a.step(dt, 1)
+        if it % 7 == 3:  # a round trip of the state in between
+            up, vp, bits, tp = pd.pd_get_state_packed(a.h, a.n, a.B)
+            pd.pd_set_state_packed(a.h, up, vp, bits, tp)
+        if it % 25 == 24:
+            b.step(dt, 25)
+            if len(b.contacts()):
+                touched += 1
+            if touched > 4:
+                break
+    assert touched > 0, "grains never met"
+    steps_a, rebuilds_a, _ = a.step_counters()
+    steps_b, rebuilds_b, _ = b.step_counters()
+    assert steps_a == steps_b
+    assert rebuilds_a < steps_a / 2 and rebuilds_b >= steps_b
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert np.array_equal(x, y)
+    a.close(); b.close()
+
+
 def test_rigid_motion_zero_force_gpu(pd):
     sc = S.small_block(nx=8, ny=6, nz=5, jitter=0.03)
     ctx = pd.Context.from_scenario(sc, contact=False)
