@@ -1619,17 +1619,19 @@ static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, con
             state_differs(sv, c->perm, c->n, mixed ? c->vh : nullptr, mixed ? c->vl : nullptr, 1, c->v, 8u, c->dflag,
                           c->st);
         }
-        if (with_bits) {  // the caller's bond memory in internal slot order, then compared
-            if (broken) {
+        if (with_bits) {
+            const int64_t nw = (c->B + 31) / 32;
+            if (broken) {  // the caller's bytes in internal slot order, compared with the live bits
                 CK(cudaMemcpyAsync(c->stage_b, broken, c->B, cudaMemcpyHostToDevice, c->st));
                 bytes_to_bits(c->stage_b, c->kc_of, c->B, c->stage_bits, c->st);
-            } else {
+                words_differ(c->stage_bits, c->brk, nw, 0xffffffffu, 16u, c->dflag, c->st);
+            } else {  // the live bits in caller order (cheap: breaks are sparse), compared with the caller's
                 uint32_t *sw = (uint32_t *)c->stage_b;
-                CK(cudaMemcpyAsync(sw, bits, sizeof(uint32_t) * (size_t)((c->B + 31) / 32), cudaMemcpyHostToDevice,
-                                   c->st));
-                packed_to_bits(sw, c->kc_of, c->B, c->stage_bits, c->st);
+                CK(cudaMemcpyAsync(sw, bits, sizeof(uint32_t) * (size_t)nw, cudaMemcpyHostToDevice, c->st));
+                bits_to_packed(c->brk, c->kc_of, c->B, c->stage_bits, c->st);
+                const uint32_t last = (c->B & 31) ? (1u << (c->B & 31)) - 1u : 0xffffffffu;  // bits past B ignored
+                words_differ(sw, c->stage_bits, nw, last, 16u, c->dflag, c->st);
             }
-            words_differ(c->stage_bits, c->brk, (c->B + 31) / 32, 16u, c->dflag, c->st);
         }
         CK(cudaMemcpyAsync(&flags, c->dflag, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
         pd_status s = sync(c);
@@ -1651,6 +1653,7 @@ static pd_status set_state_impl(pd_ctx *c, const double *u, const double *v, con
         if (mixed) split_df(c->v, nullptr, c->n, c->vh, c->vl, 1, c->st);
     }
     if (with_bits && (flags & 16u)) {
+        if (bits) packed_to_bits((const uint32_t *)c->stage_b, c->kc_of, c->B, c->stage_bits, c->st);
         CK(cudaMemcpyAsync(c->brk, c->stage_bits, sizeof(uint32_t) * (size_t)((c->B + 31) / 32),
                            cudaMemcpyDeviceToDevice, c->st));
         if (c->lcol) sync_lcol_flags(c->brk, c->B, c->lcol, c->st);

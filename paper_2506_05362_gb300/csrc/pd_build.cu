@@ -589,11 +589,11 @@ __global__ void k_state_differs(const double *__restrict__ staged, const int32_t
 }
 
 __global__ void k_words_differ(const uint32_t *__restrict__ a, const uint32_t *__restrict__ b, int64_t nw,
-                               unsigned bit, unsigned *flag)
+                               uint32_t last_mask, unsigned bit, unsigned *flag)
 {
     bool diff = false;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x)
-        diff |= a[w] != b[w];
+        diff |= ((a[w] ^ b[w]) & (w == nw - 1 ? last_mask : 0xffffffffu)) != 0u;
     if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
@@ -817,9 +817,10 @@ void state_differs(const double *staged, const int32_t *perm, int64_t n, const f
     k_state_differs<<<grid_of(n), 256, 0, st>>>(staged, perm, n, hi, lo, stride, d64, bit, flag);
 }
 
-void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, unsigned bit, unsigned *flag, cudaStream_t st)
+void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, uint32_t last_mask, unsigned bit, unsigned *flag,
+                  cudaStream_t st)
 {
-    k_words_differ<<<grid_of(nw), 256, 0, st>>>(a, b, nw, bit, flag);
+    k_words_differ<<<grid_of(nw), 256, 0, st>>>(a, b, nw, last_mask, bit, flag);
 }
 
 void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cudaStream_t st)

@@ -55,7 +55,9 @@ void from_caller(const double *in, const int32_t *perm, int64_t n, dbl4 *out, cu
 void state_differs(const double *staged, const int32_t *perm, int64_t n, const float4 *hi, const float4 *lo,
                    int stride, const dbl4 *d64, unsigned bit, unsigned *flag, cudaStream_t st);
 // *flag |= bit when the nw words of a and b differ
-void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, unsigned bit, unsigned *flag, cudaStream_t st);
+// flag |= bit when the words differ (the last word only in the bits of last_mask)
+void words_differ(const uint32_t *a, const uint32_t *b, int64_t nw, uint32_t last_mask, unsigned bit, unsigned *flag,
+                  cudaStream_t st);
 // *flag |= bit when any of the m doubles at a is not finite
 void check_finite(const double *a, int64_t m, unsigned bit, unsigned *flag, cudaStream_t st);
 void split_hilo(const dbl4 *u, int64_t n, float4 *hi, float4 *lo, cudaStream_t st);

@@ -1415,10 +1415,17 @@ __global__ void __launch_bounds__(STEP_THREADS, PD_MINB_TILED) k_step_tiled(cons
 }
 
 // First half of a chunk's first step: v += dt/2 a; u^{n+1} = u^n + dt v; walls move.
+// The drift's displacement bound (dt times the largest |v|) enters the contact
+// list's bookkeeping as every fused step's drift does, by the last block: a list
+// carried over from the previous call is checked against it before the forces use
+// it (the rebuild that follows a drift otherwise resets it).  256 threads a block.
 template <bool MIXED>
 __global__ void k_drift(const StepParams p)
 {
+    __shared__ float s_m[8];
+    __shared__ bool s_last;
     const double hdt = 0.5 * p.dt;
+    float vm = 0.f;  // largest |v|^2 after the half kick (FP32, as the fused steps keep it)
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (MIXED) {
@@ -1434,6 +1441,7 @@ __global__ void k_drift(const StepParams p)
             p.vl[i] = make_float4(vx.lo, vy.lo, vz.lo, 0.f);
             p.uh_out[REC * i] = make_float4(ux.hi, uy.hi, uz.hi, uh.w);
             p.ul_out[REC * i] = make_float4(ux.lo, uy.lo, uz.lo, ul.w);
+            vm = fmaxf(vm, vx.hi * vx.hi + vy.hi * vy.hi + vz.hi * vz.hi);
         } else {
             dbl4 v = p.v[i];
             const dbl4 a = p.acc[i], u = p.u_in[i];
@@ -1447,12 +1455,34 @@ __global__ void k_drift(const StepParams p)
             un.w = 0.0;
             p.v[i] = v;
             p.u_out[i] = un;
+            vm = fmaxf(vm, __double2float_ru(v.x * v.x + v.y * v.y + v.z * v.z));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int l = 0; l < p.walls.nw; ++l)
             for (int q = 0; q < 3; ++q)
                 p.wall_pos[3 * l + q] = dadd(p.wall_pos[3 * l + q], dmul(p.dt, p.walls.v[l][q]));
+    }
+    if (!p.contact) return;  // uniform: a kernel parameter
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = vm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < 8; ++w) m = fmaxf(m, s_m[w]);
+        if (m > 0.f) atomicMax(p.vmax_bits, __float_as_uint(m));  // non-negative floats order as their bits
+        __threadfence();
+        s_last = atomicAdd(p.counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const double m = (double)__uint_as_float(atomicExch(p.vmax_bits, 0u));
+        const double dsp = *p.disp + p.dt * sqrt(m);
+        *p.disp = dsp;
+        if (2.0 * dsp >= p.skin) *p.stale = 1;
+        *p.counter = 0u;
     }
 }
 
