@@ -335,7 +335,9 @@ pd_status pd_set_state_packed(pd_ctx *ctx, const double *u, const double *v, con
  * (0 = every directed slot gathers its neighbour from global memory, 1 =
  * shared-memory tiles, 2 = each bond once in two passes) and the measured time
  * (ms) of one force evaluation per candidate: ms[0..3] kernel 0 with 4, 8, 16, 32
- * lanes, ms[4..7] kernel 1, ms[8..11] kernel 2 (0 = not run).  Any pointer may be
+ * lanes, ms[4..7] kernel 1, ms[8..11] kernel 2 (0 = not run).  The kernel is the
+ * one with the fastest evaluation; its lane count the smallest within 3% of that
+ * time (a full step's per-node work favours fewer lanes).  Any pointer may be
  * NULL. */
 pd_status pd_tuning(pd_ctx *ctx, int *lanes, int *kernel, double ms[12]);
 

@@ -89,8 +89,12 @@ def test_aggregate_steps_finite_and_tuned(agg):
     sc, ctx = agg
     lanes, kernel, ms = ctx.tuning()
     assert lanes in (4, 8, 16, 32) and kernel in (0, 1, 2)
-    # the chosen candidate is the fastest one measured
-    assert ms[4 * kernel + (4, 8, 16, 32).index(lanes)] == min(t for t in ms if t > 0)
+    # the chosen kernel is the fastest measured, at the fewest lanes within 3% of it
+    best = min(t for t in ms if t > 0)
+    chosen = ms[4 * kernel + (4, 8, 16, 32).index(lanes)]
+    assert min(t for t in ms[4 * kernel:4 * kernel + 4] if t > 0) == best
+    assert chosen <= 1.03 * best
+    assert all(not (0 < ms[4 * kernel + q] <= 1.03 * best) for q in range((4, 8, 16, 32).index(lanes)))
     ctx.set_state(u=np.zeros_like(sc.x), v=sc.v0)
     dt = 0.8 * ctx.stable_dt()
     ctx.step(dt, 50)
