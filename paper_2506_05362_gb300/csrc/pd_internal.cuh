@@ -38,7 +38,6 @@ struct WallSet {
     double v[PD_MAX_WALLS][3];
 };
 
-// Everything the force/update kernels need, passed by value.
 // Mixed-path node records: three float4 slots per node, (x_hi, c V), (u_hi,
 // packed x_lo.xy) and (u_lo, packed x_lo.z), in one of three layouts (all give the
 // same bits):
@@ -64,6 +63,7 @@ __host__ __device__ inline int64_t rec_uh0(int64_t n)
 __host__ __device__ inline int64_t rec_ul0(int64_t n) { return PD_PLANES == 1 ? 2 * n : rec_uh0(n) + 1; }
 __host__ __device__ inline int64_t rec_float4s(int64_t n) { return PD_PLANES == 2 ? rec_uh0(n) + 2 * n : 3 * n; }
 
+// Everything the force/update kernels need, passed by value.
 struct StepParams {
     int64_t n;
     const int64_t *rowptr;
